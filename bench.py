@@ -1,0 +1,395 @@
+#!/usr/bin/env python3
+"""MLUPS benchmark of the fused D2Q37 time step on GB300.
+
+Workload (N = 1): the FP64 Rayleigh-Taylor lattice of 2304 x 8192 sites (37 FP64 populations,
+double-buffered, ~11.2 GB), tau = 0.9, temperature ratio 2, walls top/bottom, periodic in x.
+One bench step = one fused LB time step (pull propagate + collide + wall halo write) over the
+whole lattice. MLUPS = sites x steps / seconds / 1e6 (Table 1's unit).
+
+Printed JSON line (rank 0): value = device-timed MLUPS of K steps with the lattice resident in
+HBM (CUDA events on the library's stream, max over ranks); e2e = the same metric through the C
+ABI from pinned host fields (lb_init upload, K steps, lb_moments download, wall clock);
+roofline of the step kernel; cpu_baseline = the CPU oracle on a bounded sample; forms = the
+FP32-deviation form's MLUPS and relative L2 errors; clocks sampled during the timed region.
+
+Multi-GPU (torchrun): one independent lattice per rank (replicas, weak scaling), no collective on
+the data path; barrier + max-over-ranks timing.
+
+--impl reference times the CPU oracle (the only reference this method has: the paper ships no
+code) on the same metric, rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
+NPOP = 37
+# FP64 arithmetic of the fused step per site, counted from the kernel's formulation
+# (moments 103, forcing 7, shell coefficients 99, rest population 3, pairs incl. r*u 318;
+# FMA = 2 flops).
+FP64_FLOP_PER_SITE = 530
+FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
+FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
+SM_COUNT = 152
+FP64_FLOP_PER_CLK_SM = 4                 # 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh)
+    except OSError:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=None):
+        self.proc = None
+        self.path = None
+        self.gpu_index = gpu_index
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_index is not None:
+            cmd += ["-i", str(self.gpu_index)]
+        try:
+            self.out = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "power_w_median": statistics.median(power), "reasons": sorted(reasons)}
+
+
+def visible_gpu_index(local_rank):
+    cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [s for s in cvd.split(",") if s.strip() != ""]
+    if ids and local_rank < len(ids) and ids[local_rank].strip().isdigit():
+        return int(ids[local_rank])
+    return local_rank
+
+
+# ----------------------------------------------------------------------------------------------
+# CPU oracle timing (cpu_baseline leg and --impl reference)
+# ----------------------------------------------------------------------------------------------
+
+def oracle_mlups(rows, steps, nthreads):
+    """Oracle MLUPS on a band of `rows` rows of the 2304-wide Rayleigh-Taylor workload."""
+    from oracle import oracle as orc
+    from paper_1804_01918_gb300 import inputs
+    st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=0)
+    y0 = LY // 2 - rows // 2
+    sub = [a[y0:y0 + rows] for a in (st.rho, st.ux, st.uy, st.T)]
+    f0 = orc.equilibrium(*sub)
+    t0 = time.perf_counter()
+    orc.run(f0, tau=TAU, nsteps=steps, gy=st.gy, T_top=st.T_top, T_bottom=st.T_bottom,
+            nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return LX * rows * steps / dt / 1e6, dt
+
+
+def cpu_baseline(target_s=15.0):
+    from oracle import oracle as orc
+    nthreads = orc.default_threads()
+    rate, _ = oracle_mlups(64, 1, nthreads)                 # calibration
+    rows = int(max(64, min(LY, rate * 1e6 * target_s / 3 / LX)))
+    steps = 3
+    v, dt = oracle_mlups(rows, steps, nthreads)
+    return {"value": round(v, 3), "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
+            "sample": f"{steps} steps of a {LX}x{rows} band (rows {LY // 2 - rows // 2}.."
+                      f"{LY // 2 + (rows + 1) // 2 - 1}) of the {LX}x{LY} FP64 Rayleigh-Taylor "
+                      f"workload, walls at the band edges, {dt:.1f} s"}
+
+
+def run_reference(args):
+    rank = env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    from oracle import oracle as orc
+    nthreads = orc.default_threads()
+    rate, _ = oracle_mlups(64, 1, nthreads)
+    per_step = 150.0 / max(1, args.steps + args.warmup)
+    rows = int(max(16, min(LY, rate * 1e6 * per_step / LX)))
+    from paper_1804_01918_gb300 import inputs
+    st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=0)
+    y0 = LY // 2 - rows // 2
+    f = orc.equilibrium(*[a[y0:y0 + rows] for a in (st.rho, st.ux, st.uy, st.T)])
+    kw = dict(tau=TAU, gy=st.gy, T_top=st.T_top, T_bottom=st.T_bottom, nthreads=nthreads)
+    f = orc.run(f, nsteps=args.warmup, **kw)
+    t0 = time.perf_counter()
+    orc.run(f, nsteps=args.steps, **kw)
+    dt = time.perf_counter() - t0
+    value = LX * rows * args.steps / dt / 1e6
+    sample = (f"each step a {LX}x{rows} band of the {LX}x{LY} FP64 Rayleigh-Taylor workload "
+              f"(walls at the band edges)")
+    line = {"impl": "reference", "metric": "D2Q37 MLUPS, fused FP64 LB step (propagate+collide+walls)",
+            "value": round(value, 3), "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(1),
+            "cpu_baseline": {"value": round(value, 3), "unit": "MLUPS", "cores": nthreads,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(value, 3), "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def workload_config(world):
+    return {"workload": f"D2Q37 FP64 Rayleigh-Taylor {LX}x{LY} (18.9M sites, ~11.2 GB "
+                        f"double-buffered), tau {TAU}, T ratio 1:{RATIO}, walls top/bottom, "
+                        f"periodic x, fused propagate+collide+walls",
+            "Lx": LX, "Ly": LY, "tau": TAU, "precision": "fp64",
+            "replicas": world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+            "l2": "inputs larger than L2 (5.6 GB read + 5.6 GB written per step vs 129 MB L2)"}
+
+
+# ----------------------------------------------------------------------------------------------
+
+def fp64_probe(lb, torch, stream):
+    """Achieved FP64 FMA rate of the library's probe (TFLOP/s) and the time it took."""
+    blocks, threads, iters = SM_COUNT * 8, 256, 2048
+    out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        lb.probe_fma("fp64", blocks, threads, iters, out, stream)   # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lb.probe_fma("fp64", blocks, threads, iters, out, stream)
+        e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    return blocks * threads * 16 * iters / (ms * 1e-3) / 1e12
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-forms", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    from paper_1804_01918_gb300 import build as pkg_build
+    from paper_1804_01918_gb300 import inputs, lb
+
+    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group(backend="nccl" if torch.cuda.is_available() else "gloo")
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    pkg_build.build()
+
+    st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=rank)
+    stream = torch.cuda.Stream()
+    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream)
+    lat.step(args.warmup)
+    lat.sync()
+    probe_tf = fp64_probe(lb, torch, stream)
+
+    sampler = ClockSampler(visible_gpu_index(local))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(args.steps)
+    e1.record(stream)
+    e1.synchronize()
+    clocks = sampler.stop()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.sync()    # raises on a non-finite state
+    if dist:
+        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    sites = LX * LY
+    value = world * sites * args.steps / (ms * 1e-3) / 1e6
+    kernel_s = ms * 1e-3 / args.steps
+    lat.close()
+    del lat
+
+    # ---- end to end through the C ABI from pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        pin = [torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+               for a in (st.rho, st.ux, st.uy, st.T)]
+        outs = [torch.empty((LY, LX), dtype=torch.float64).pin_memory() for _ in range(4)]
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        lat2 = lb.Lattice(LX, LY, TAU, *pin, gy=st.gy, T_top=st.T_top, T_bottom=st.T_bottom,
+                          stream=stream)
+        lat2.step(args.steps)
+        lat2.moments(out=outs)
+        t1 = time.perf_counter()
+        lat2.close()
+        del lat2
+        dt = t1 - t0
+        if dist:
+            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = float(t.item())
+        e2e = {"value": round(world * sites * args.steps / dt / 1e6, 2), "unit": "MLUPS",
+               "h2d_bytes_per_step": round(4 * 8 * sites / args.steps, 1),
+               "d2h_bytes_per_step": round(4 * 8 * sites / args.steps, 1),
+               "note": "one lb_init upload of rho,u,T (32 B/site) and one lb_moments download "
+                       "(32 B/site) per K-step run, amortised per step"}
+
+    # ---- roofline of the fused FP64 step kernel ----
+    flops = FP64_FLOP_PER_SITE * sites
+    achieved_tf = flops / kernel_s / 1e12
+    peak_tf = SM_COUNT * FP64_FLOP_PER_CLK_SM * 2070e6 / 1e12
+    hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    roofline = {"bound": "alu", "kernel": "step_fp64_kernel", "achieved": round(achieved_tf, 4),
+                "peak": round(peak_tf, 4), "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4),
+                "traffic": None,
+                "peak_note": "FP64 CUDA-core peak derived from unit counts and clocks: 152 SMs x 4 "
+                             "flop/clk/SM x 2070 MHz (the 1.25 TFLOP/s nominal); FMA = 2 flops",
+                "probe_fp64_tflops": round(probe_tf, 4),
+                "algorithmic_flop_per_site": FP64_FLOP_PER_SITE,
+                "hbm_achieved_gbs": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9, 1),
+                "hbm_frac": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9 / hbm, 4),
+                "hbm_peak_gbs": hbm}
+
+    # ---- FP32-deviation form: MLUPS and L2 error against the FP64 path ----
+    forms = None
+    if not args.no_forms and rank == 0:
+        forms = measure_forms(lb, torch, np, st, stream, value / world)
+
+    line = {"metric": "D2Q37 MLUPS, fused FP64 LB step (propagate+collide+walls)",
+            "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded Rayleigh-Taylor fields)", "config": workload_config(world),
+            "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps,
+            "e2e": e2e,
+            "paper_context": {"KNL 7230 flat/quad Global MLUPS 1024x8192": 119,
+                              "P100 Global MLUPS 1024x8192": 232}}
+    if forms:
+        line["forms"] = forms
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def measure_forms(lb, torch, np, st, stream, fp64_mlups):
+    """FP32-deviation form on the same workload: MLUPS (device-timed, 1000 steps) and relative L2
+    error of rho and T against the FP64 path at steps 100, 500, 1000 (the FP64 path is the
+    reference at this size; it matches the CPU oracle to 1e-12 in the tests)."""
+    sites = LX * LY
+    out = {}
+    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32dev")
+    lat.step(10)
+    lat.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(1000)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.sync()
+    lat.close()
+    mlups = sites * 1000 / (ms * 1e-3) / 1e6
+    hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
+    out["fp32dev"] = {"mlups": round(mlups, 1), "speedup_vs_fp64": round(mlups / fp64_mlups, 3),
+                      "hbm_gbs": round(FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9, 1),
+                      "hbm_frac": round(FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9 / hbm, 4)}
+    # accuracy: both precisions from the same initial state, moments at 100/500/1000
+    a = lb.Lattice.from_fields(st, tau=TAU, stream=stream)
+    b = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32dev")
+    done, errs = 0, {}
+    for mark in (100, 500, 1000):
+        a.step(mark - done)
+        b.step(mark - done)
+        done = mark
+        ra, _, _, Ta = a.moments()
+        rb, _, _, Tb = b.moments()
+        errs[str(mark)] = {"rho": float(np.linalg.norm(rb - ra) / np.linalg.norm(ra)),
+                           "T": float(np.linalg.norm(Tb - Ta) / np.linalg.norm(Ta))}
+    a.close()
+    b.close()
+    out["fp32dev"]["rel_l2_vs_fp64"] = errs
+    return out
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,135 @@
+/*
+ * lb_d2q37.h -- C ABI of the GB300 (sm_103a) D2Q37 lattice-Boltzmann time step.
+ *
+ * The method (arXiv 1804.01918, Sec. 3): each site of a regular 2-D lattice holds 37
+ * populations; one time step first propagates them (each population hops up to three sites,
+ * Sec. 3 and Fig. 1) and then collides them (mixing that conserves mass, momentum and energy;
+ * the model obeys the perfect-gas law p = rho T). Propagate is a pull (Sec. 4, Fig. 3 listing):
+ * each population of the new lattice is read from the old lattice at the site displaced by a
+ * per-population offset. The full code also applies the boundary conditions (Table 1, "Global").
+ *
+ * Readings of what the paper leaves to its references (same for every entry point):
+ *   - thermal velocities xi_i = r c_i, r = 1.19697977..., over the 37 lattice vectors with
+ *     |c_x|, |c_y| <= 3 listed by lb_velocity_set();
+ *   - equilibrium: 4th-order Hermite expansion of the Maxwellian in (rho, u, T);
+ *   - collide: BGK with relaxation time tau; gravity g by evaluating the equilibrium at
+ *     u + tau g and T + tau (1 - tau) |g|^2 / 2;
+ *   - x is periodic; below row 0 and above row Ly-1 sit walls: three halo rows per wall hold the
+ *     rest equilibrium at the wall temperature with the density of the mirror interior row;
+ *   - macroscopic output: rho = sum f, rho u = sum f xi, rho (u^2 + 2 T) = sum f xi^2.
+ *
+ * Conventions:
+ *   - Host fields are row-major [Ly][Lx] float64 (x fastest). Populations exchanged with the
+ *     host are plane-major [37][Ly][Lx] float64 in the order of lb_velocity_set().
+ *   - Every function returns an lb_status and never aborts; a NULL pointer, a non-positive size
+ *     or tau <= 0.5 gives LB_ERR_ARG. After LB_ERR_CUDA, lb_last_error() holds the CUDA message.
+ *   - Device memory: either the library allocates it (params.workspace == NULL) or the caller
+ *     passes one block of at least lb_workspace_bytes() bytes, 256-byte aligned, that it owns and
+ *     keeps alive until lb_free() (e.g. a PyTorch tensor). All work is queued on params.stream
+ *     (a cudaStream_t; NULL makes the library create and own a non-blocking stream).
+ *   - A context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef LB_D2Q37_H
+#define LB_D2Q37_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LB_NPOP 37
+
+typedef struct lb_ctx lb_ctx;
+
+typedef enum {
+    LB_OK = 0,
+    LB_ERR_ARG = 1,       /* invalid argument (NULL, size, tau, workspace too small ...) */
+    LB_ERR_ALLOC = 2,     /* device or host allocation failed */
+    LB_ERR_CUDA = 3,      /* a CUDA call failed; see lb_last_error() */
+    LB_ERR_NONFINITE = 4, /* a site produced a non-finite or non-positive density or temperature */
+    LB_ERR_STATE = 5      /* call not valid in the context's current state */
+} lb_status;
+
+typedef enum {
+    LB_FP64 = 0,   /* populations stored and collided in FP64 */
+    LB_FP32DEV = 1 /* populations stored as FP32 deviations f - w; FP32 collide, FP64 moments and
+                      conservation projection */
+} lb_precision;
+
+typedef struct {
+    int Lx, Ly;           /* lattice size; 4 <= Lx, 4 <= Ly, Lx * Ly < 2^31 */
+    double tau;           /* BGK relaxation time, > 0.5 */
+    double gx, gy;        /* gravity (lattice units, per step) */
+    double T_top;         /* wall temperature above row Ly-1 */
+    double T_bottom;      /* wall temperature below row 0 */
+    int y_periodic;       /* 0: walls at top/bottom; 1: periodic in y (no walls) */
+    int precision;        /* lb_precision */
+    void* stream;         /* cudaStream_t or NULL */
+    void* workspace;      /* caller-owned device memory or NULL */
+    size_t workspace_bytes;
+} lb_params;
+
+/* Human-readable name of a status code (static string). */
+const char* lb_status_str(lb_status s);
+
+/* Last CUDA error message recorded by this thread (static per thread; "" if none). */
+const char* lb_last_error(void);
+
+/* The library's population order: cx[37], cy[37] lattice vectors, w[37] weights and the thermal
+ * scale r (xi = r c). Any argument may be NULL. Pure host call. Order: 0 = rest; 1..18 one
+ * vector of each opposite pair; 18 + k is the opposite of k. */
+lb_status lb_velocity_set(int* cx, int* cy, double* w, double* r);
+
+/* Device bytes a context with these parameters needs (both population copies, the host-exchange
+ * staging area and status words). Pure host call; fields other than Lx, Ly, precision ignored.
+ * The two population copies are the double buffer of the Fig. 3 listing (prv/nxt). */
+lb_status lb_workspace_bytes(const lb_params* p, size_t* bytes);
+
+/* Create a context: copy the host fields rho, ux, uy, T ([Ly][Lx] float64, caller-owned) to the
+ * device, set every population to the equilibrium of its site (Sec. 3 model) and write the wall
+ * halos. Synchronous: the host arrays may be reused on return. */
+lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const double* uy,
+                  const double* T, lb_ctx** out);
+
+/* Advance n >= 0 fused time steps: pull propagate (Fig. 3 listing) + collide (Sec. 3) + wall halo
+ * write, one kernel per step, CUDA-graph launched. Asynchronous on the context's stream; a
+ * non-finite state is reported by the next lb_sync / lb_moments / lb_get_populations. */
+lb_status lb_step(lb_ctx* c, int n);
+
+/* Propagate only (no collide): the pull of the Fig. 3 listing, new_i(x, y) =
+ * old_i((x - c_ix) mod Lx, y - c_iy), reading wall halos (or wrapping in y when y_periodic);
+ * halo rows are carried over unchanged. A pure copy: bit-exact. Asynchronous. */
+lb_status lb_propagate(lb_ctx* c);
+
+/* Wait for queued work; returns LB_ERR_NONFINITE (once) if any step since the last check saw a
+ * non-finite or non-positive density/temperature, else LB_OK. */
+lb_status lb_sync(lb_ctx* c);
+
+/* Macroscopic fields of the current populations into caller-owned host arrays [Ly][Lx] float64
+ * (any may be NULL). Synchronous. */
+lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T);
+
+/* Same into caller-owned device arrays of Lx*Ly float64 (any may be NULL). Asynchronous. */
+lb_status lb_moments_device(lb_ctx* c, double* rho, double* ux, double* uy, double* T);
+
+/* Copy the current interior populations to host f[37][Ly][Lx] float64 (FP32DEV contexts return
+ * w + deviation). Synchronous. */
+lb_status lb_get_populations(lb_ctx* c, double* f);
+
+/* Replace the current populations by host f[37][Ly][Lx] float64 and rewrite the wall halos from
+ * them (checkpoint restore). Synchronous. */
+lb_status lb_set_populations(lb_ctx* c, const double* f);
+
+/* Steps taken since lb_init (lb_propagate counts as one). */
+lb_status lb_steps_done(const lb_ctx* c, long long* n);
+
+/* Release the context and, if the library allocated it, its device memory. NULL-safe. */
+void lb_free(lb_ctx* c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_D2Q37_H */

@@ -1,0 +1,30 @@
+/*
+ * lb_probe.h -- device-throughput probe of the D2Q37 library.
+ *
+ * The paper rates collide against the processor's peak floating-point throughput (Sec. 5:
+ * ~1 TFlops sustained, ~30% of the KNL's raw peak). On GB300 the FP64 and FP32 CUDA-core peaks
+ * are not published per part, so the library carries its own probe: a kernel of independent
+ * fused multiply-add chains whose time, measured by the caller with CUDA events, gives the
+ * achievable FMA rate used as the roofline denominator of the ALU-bound step kernels.
+ */
+#ifndef LB_PROBE_H
+#define LB_PROBE_H
+
+#include "lb_d2q37.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Launch blocks x threads threads; each runs 8 independent FMA chains of `iters` steps in FP64
+ * (kind 0) or FP32 (kind 1), i.e. 16 * iters flops per thread, and writes one value per thread
+ * to out (device memory of blocks*threads elements of that type, caller-owned). Asynchronous on
+ * `stream` (cudaStream_t, NULL = legacy default stream). LB_ERR_ARG for non-positive sizes,
+ * threads > 1024 or an unknown kind. */
+lb_status lb_probe_fma(int kind, void* stream, int blocks, int threads, int iters, void* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_PROBE_H */

@@ -1,0 +1,91 @@
+// d2q37_gpu.cuh -- D2Q37 model tables and per-step coefficients of the CUDA path.
+//
+// The model (paper, Sec. 3): 37 populations per site, hopping up to three lattice points, with an
+// equilibrium that yields the perfect-gas law p = rho T. The velocity set, weights and Hermite
+// equilibrium are those of the D2Q37 references the paper cites; this header is the CUDA path's
+// own copy (the CPU oracle keeps a separate one).
+//
+// Population order used on the device and in the C ABI:
+//   0        rest particle
+//   1 .. 18  one vector of each opposite pair, shell by shell
+//   19 .. 36 population 18 + k moves opposite to population k
+// Pairing opposite vectors lets the collide evaluate the even and odd parts of the equilibrium
+// polynomial once per pair (f_eq(+c) and f_eq(-c) differ only in the sign of the odd part).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+namespace lbg {
+
+constexpr int NPOP = 37;
+constexpr int NPAIR = 18;
+constexpr int NSHELL = 8;
+constexpr int HALO = 3;
+constexpr double DIM = 2.0;
+
+// Tables are constexpr functions (usable in host code, device code and constant expressions).
+// Lattice vectors of populations 0..18; 19..36 are their negatives.
+__host__ __device__ constexpr int cxh(int i) {
+    constexpr int t[NPAIR + 1] = {0, 1, 0, 1, 1, 2, 0, 2, 2, 1, 1, 2, 2, 3, 0, 3, 3, 1, 1};
+    return t[i];
+}
+__host__ __device__ constexpr int cyh(int i) {
+    constexpr int t[NPAIR + 1] = {0, 0, 1, 1, -1, 0, 2, 1, -1, 2, -2, 2, -2, 0, 3, 1, -1, 3, -3};
+    return t[i];
+}
+// Shell of populations 0..18 (shell s = |c|-class: (0,0) (1,0) (1,1) (2,0) (2,1) (2,2) (3,0) (3,1)).
+__host__ __device__ constexpr int shellh(int i) {
+    constexpr int t[NPAIR + 1] = {0, 1, 1, 2, 2, 3, 3, 4, 4, 4, 4, 5, 5, 6, 6, 7, 7, 7, 7};
+    return t[i];
+}
+// |c|^2 per shell.
+__host__ __device__ constexpr int shell_c2(int s) {
+    constexpr int t[NSHELL] = {0, 1, 2, 4, 5, 8, 9, 10};
+    return t[s];
+}
+// D2Q37 quadrature weights per shell.
+__host__ __device__ constexpr double shell_w(int s) {
+    constexpr double t[NSHELL] = {
+        0.23315066913235250228650, 0.10730609154221900241246, 0.05766785988879488203006,
+        0.01420821615845075026469, 0.00535304900051377523273, 0.00101193759267357547541,
+        0.00024530102775771734547, 0.00028341425299419821740};
+    return t[s];
+}
+
+__host__ __device__ constexpr int cx_of(int i) { return i <= NPAIR ? cxh(i) : -cxh(i - NPAIR); }
+__host__ __device__ constexpr int cy_of(int i) { return i <= NPAIR ? cyh(i) : -cyh(i - NPAIR); }
+__host__ __device__ constexpr int shell_of(int i) { return i <= NPAIR ? shellh(i) : shellh(i - NPAIR); }
+
+// Per-shell polynomial coefficients of the Hermite equilibrium, written for one pair (+c, -c)
+// with a = xi.u, theta = T - 1, u2 = |u|^2 and X = xi^2 = r^2 |c|^2:
+//   f_eq(+-c) / (w rho) = E(a^2) +- O(a)
+//   E = A0 + A2 a^2 + a^4 / 24,  O = a (B1 + a^2 / 6)
+//   A0 = 1 - u2/2 + u2^2/8 + alpha theta + beta theta u2 + gamma theta^2
+//   A2 = 1/2 - u2/4 + delta theta,  B1 = 1 - u2/2 + eps theta
+// with alpha = (X - D)/2, beta = (D + 2 - X)/4, gamma = (X^2 - 2(D + 2)X + D(D + 2))/8,
+// delta = (X - D - 4)/4, eps = (X - D - 2)/2. This is the same polynomial as the 4th-order
+// expansion, regrouped by powers of a.
+struct ShellCoef {
+    double w, alpha, beta, gamma, delta, eps;
+};
+
+// Everything a step kernel needs, passed by value as a kernel parameter.
+struct StepParams {
+    int Lx, Ly;
+    int y_periodic;
+    int pad0;
+    long long plane;       // elements per population plane, (Ly + 2*HALO) * Lx
+    double r;              // thermal scale, xi = r c
+    double r2;             // r^2
+    double omega;          // 1 / tau
+    double omc;            // 1 - 1/tau
+    double gx, gy;         // gravity
+    double tgx, tgy;       // tau * g
+    double dT_force;       // tau (1 - tau) |g|^2 / D
+    ShellCoef sh[NSHELL];
+    double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population
+    double wall_top[NPOP]; // same at T_top
+};
+
+}  // namespace lbg

@@ -1,0 +1,40 @@
+// kernels.cuh -- launchers of the D2Q37 kernels, called by the C ABI layer (lb_capi.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "d2q37_gpu.cuh"
+
+namespace lbg {
+
+// Threads per block of the site-parallel kernels.
+constexpr int SITE_BLOCK = 128;
+
+// ---- FP64 populations (step_fp64.cu) ----
+cudaError_t launch_step_fp64(const double* src, double* dst, const StepParams& P, int* flag,
+                             cudaStream_t s);
+cudaError_t launch_propagate_fp64(const double* src, double* dst, const StepParams& P,
+                                  cudaStream_t s);
+cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy,
+                             const double* T, double* f, const StepParams& P, cudaStream_t s);
+cudaError_t launch_moments_fp64(const double* f, const StepParams& P, double* rho, double* ux,
+                                double* uy, double* T, cudaStream_t s);
+cudaError_t launch_halo_fp64(double* f, const StepParams& P, cudaStream_t s);
+
+// ---- FP32 deviation populations (step_fp32dev.cu) ----
+cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& P, int* flag,
+                                cudaStream_t s);
+cudaError_t launch_propagate_fp32dev(const float* src, float* dst, const StepParams& P,
+                                     cudaStream_t s);
+cudaError_t launch_init_fp32dev(const double* rho, const double* ux, const double* uy,
+                                const double* T, float* f, const StepParams& P, cudaStream_t s);
+cudaError_t launch_moments_fp32dev(const float* f, const StepParams& P, double* rho, double* ux,
+                                   double* uy, double* T, cudaStream_t s);
+cudaError_t launch_halo_fp32dev(float* f, const StepParams& P, cudaStream_t s);
+// plane i interior: FP64 absolute populations <-> FP32 deviations
+cudaError_t launch_plane_to_dev32(const double* src, float* dst_plane_interior, double w,
+                                  long long n, cudaStream_t s);
+cudaError_t launch_plane_from_dev32(const float* src_plane_interior, double* dst, double w,
+                                    long long n, cudaStream_t s);
+
+}  // namespace lbg

@@ -1,0 +1,451 @@
+// lb_capi.cu -- host runtime behind the C ABI of include/lb_d2q37.h.
+//
+// A context owns: two population copies (double buffer), a staging area for host exchange
+// (4 fields of Lx*Ly doubles, also used plane by plane for population copies), a device status
+// word, the stream, and up to two instantiated CUDA graphs of GRAPH_STEPS fused steps (one per
+// buffer parity), replayed by lb_step so that short lattices are not launch-bound.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "../../include/lb_d2q37.h"
+#include "d2q37_gpu.cuh"
+#include "kernels.cuh"
+
+using namespace lbg;
+
+namespace {
+
+constexpr size_t ALIGN = 256;
+constexpr int GRAPH_STEPS = 16;  // even: a replay returns the state to the same buffer
+
+thread_local char g_last_error[256] = "";
+
+size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+lb_status cuda_fail(cudaError_t e, const char* where) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", where, cudaGetErrorString(e));
+    return LB_ERR_CUDA;
+}
+
+#define LB_CUDA(call)                                   \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call); \
+    } while (0)
+
+struct Layout {
+    size_t esize, plane_elems, buf_bytes, stage_bytes, flag_bytes, total;
+    size_t off_a, off_b, off_stage, off_flag;
+};
+
+bool valid_sizes(int Lx, int Ly) {
+    if (Lx < 4 || Ly < 4) return false;
+    const long long full = (long long)Lx * ((long long)Ly + 2 * HALO);
+    return full < (1ll << 31) - 1;
+}
+
+Layout layout_of(int Lx, int Ly, int precision) {
+    Layout L;
+    L.esize = precision == LB_FP32DEV ? sizeof(float) : sizeof(double);
+    L.plane_elems = (size_t)Lx * ((size_t)Ly + 2 * HALO);
+    L.buf_bytes = align_up(L.plane_elems * NPOP * L.esize);
+    L.stage_bytes = align_up((size_t)4 * Lx * Ly * sizeof(double));
+    L.flag_bytes = ALIGN;
+    L.off_a = 0;
+    L.off_b = L.off_a + L.buf_bytes;
+    L.off_stage = L.off_b + L.buf_bytes;
+    L.off_flag = L.off_stage + L.stage_bytes;
+    L.total = L.off_flag + L.flag_bytes;
+    return L;
+}
+
+// r = 1 / sqrt(sum_i w_i c_ix^2): xi = r c puts the reference temperature at 1.
+double thermal_scale() {
+    double m2 = 0.0;
+    for (int i = 0; i < NPOP; ++i) m2 += shell_w(shell_of(i)) * (double)(cx_of(i) * cx_of(i));
+    return 1.0 / std::sqrt(m2);
+}
+
+void fill_step_params(const lb_params& p, StepParams& sp) {
+    std::memset(&sp, 0, sizeof sp);
+    sp.Lx = p.Lx;
+    sp.Ly = p.Ly;
+    sp.y_periodic = p.y_periodic ? 1 : 0;
+    sp.plane = (long long)p.Lx * ((long long)p.Ly + 2 * HALO);
+    const double r = thermal_scale();
+    sp.r = r;
+    sp.r2 = r * r;
+    sp.omega = 1.0 / p.tau;
+    sp.omc = 1.0 - 1.0 / p.tau;
+    sp.gx = p.gx;
+    sp.gy = p.gy;
+    sp.tgx = p.tau * p.gx;
+    sp.tgy = p.tau * p.gy;
+    sp.dT_force = p.tau * (1.0 - p.tau) * (p.gx * p.gx + p.gy * p.gy) / DIM;
+    for (int s = 0; s < NSHELL; ++s) {
+        const double X = sp.r2 * shell_c2(s);
+        sp.sh[s].w = shell_w(s);
+        sp.sh[s].alpha = (X - DIM) / 2.0;
+        sp.sh[s].beta = (DIM + 2.0 - X) / 4.0;
+        sp.sh[s].gamma = (X * X - 2.0 * (DIM + 2.0) * X + DIM * (DIM + 2.0)) / 8.0;
+        sp.sh[s].delta = (X - DIM - 4.0) / 4.0;
+        sp.sh[s].eps = (X - DIM - 2.0) / 2.0;
+    }
+    // rest equilibrium per unit density: w (1 + alpha theta + gamma theta^2) at u = 0
+    for (int i = 0; i < NPOP; ++i) {
+        const ShellCoef& c = sp.sh[shell_of(i)];
+        const double tb = p.T_bottom - 1.0, tt = p.T_top - 1.0;
+        sp.wall_bot[i] = c.w * (1.0 + c.alpha * tb + c.gamma * tb * tb);
+        sp.wall_top[i] = c.w * (1.0 + c.alpha * tt + c.gamma * tt * tt);
+    }
+}
+
+lb_status check_params(const lb_params* p) {
+    if (!p) return LB_ERR_ARG;
+    if (!valid_sizes(p->Lx, p->Ly)) return LB_ERR_ARG;
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LB_ERR_ARG;
+    if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return LB_ERR_ARG;
+    if (!(p->T_top > 0.0) || !(p->T_bottom > 0.0) || !std::isfinite(p->T_top) ||
+        !std::isfinite(p->T_bottom))
+        return LB_ERR_ARG;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV) return LB_ERR_ARG;
+    return LB_OK;
+}
+
+}  // namespace
+
+struct lb_ctx {
+    lb_params p;
+    StepParams sp;
+    Layout L;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char* ws = nullptr;
+    bool own_ws = false;
+    void* buf[2] = {nullptr, nullptr};
+    int cur = 0;
+    double* stage = nullptr;
+    int* flag = nullptr;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    long long steps = 0;
+};
+
+namespace {
+
+lb_status launch_one_step(lb_ctx* c) {
+    cudaError_t e;
+    if (c->p.precision == LB_FP64)
+        e = launch_step_fp64((const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1], c->sp,
+                             c->flag, c->stream);
+    else
+        e = launch_step_fp32dev((const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1], c->sp,
+                                c->flag, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "step kernel launch");
+    c->cur ^= 1;
+    c->steps += 1;
+    return LB_OK;
+}
+
+// Capture GRAPH_STEPS fused steps starting from buffer parity `par` into c->graph[par].
+bool capture_graph(lb_ctx* c, int par) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(c->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone)
+        return false;
+    if (cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    const int saved_cur = c->cur;
+    const long long saved_steps = c->steps;
+    c->cur = par;
+    bool ok = true;
+    for (int k = 0; k < GRAPH_STEPS && ok; ++k) ok = launch_one_step(c) == LB_OK;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(c->stream, &g);
+    c->cur = saved_cur;
+    c->steps = saved_steps;
+    if (!ok || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    c->graph[par] = ex;
+    return true;
+}
+
+lb_status read_flag(lb_ctx* c) {
+    int h = 0;
+    LB_CUDA(cudaMemcpyAsync(&h, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    if (h) {
+        LB_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
+        LB_CUDA(cudaStreamSynchronize(c->stream));
+        return LB_ERR_NONFINITE;
+    }
+    return LB_OK;
+}
+
+lb_status launch_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    cudaError_t e;
+    if (c->p.precision == LB_FP64)
+        e = launch_moments_fp64((const double*)c->buf[c->cur], c->sp, rho, ux, uy, T, c->stream);
+    else
+        e = launch_moments_fp32dev((const float*)c->buf[c->cur], c->sp, rho, ux, uy, T, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "moments kernel launch");
+    return LB_OK;
+}
+
+lb_status rewrite_halos(lb_ctx* c) {
+    if (c->p.y_periodic) return LB_OK;
+    cudaError_t e = c->p.precision == LB_FP64
+                        ? launch_halo_fp64((double*)c->buf[c->cur], c->sp, c->stream)
+                        : launch_halo_fp32dev((float*)c->buf[c->cur], c->sp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "halo kernel launch");
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* lb_status_str(lb_status s) {
+    switch (s) {
+        case LB_OK: return "ok";
+        case LB_ERR_ARG: return "invalid argument";
+        case LB_ERR_ALLOC: return "allocation failed";
+        case LB_ERR_CUDA: return "CUDA error";
+        case LB_ERR_NONFINITE: return "non-finite or non-positive density/temperature";
+        case LB_ERR_STATE: return "invalid state";
+    }
+    return "unknown status";
+}
+
+const char* lb_last_error(void) { return g_last_error; }
+
+lb_status lb_velocity_set(int* cx, int* cy, double* w, double* r) {
+    for (int i = 0; i < NPOP; ++i) {
+        if (cx) cx[i] = cx_of(i);
+        if (cy) cy[i] = cy_of(i);
+        if (w) w[i] = shell_w(shell_of(i));
+    }
+    if (r) *r = thermal_scale();
+    return LB_OK;
+}
+
+lb_status lb_workspace_bytes(const lb_params* p, size_t* bytes) {
+    if (!p || !bytes || !valid_sizes(p->Lx, p->Ly)) return LB_ERR_ARG;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV) return LB_ERR_ARG;
+    *bytes = layout_of(p->Lx, p->Ly, p->precision).total;
+    return LB_OK;
+}
+
+void lb_free(lb_ctx* c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    if (c->own_ws && c->ws) cudaFree(c->ws);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const double* uy,
+                  const double* T, lb_ctx** out) {
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    lb_status st = check_params(p);
+    if (st != LB_OK) return st;
+    if (!rho || !ux || !uy || !T) return LB_ERR_ARG;
+    const Layout L = layout_of(p->Lx, p->Ly, p->precision);
+    if (p->workspace) {
+        if (p->workspace_bytes < L.total || ((uintptr_t)p->workspace % ALIGN) != 0) return LB_ERR_ARG;
+    }
+    lb_ctx* c = new (std::nothrow) lb_ctx();
+    if (!c) return LB_ERR_ALLOC;
+    c->p = *p;
+    c->L = L;
+    fill_step_params(*p, c->sp);
+    if (p->stream) {
+        c->stream = (cudaStream_t)p->stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete c;
+            return cuda_fail(e, "cudaStreamCreateWithFlags");
+        }
+        c->own_stream = true;
+    }
+    if (p->workspace) {
+        c->ws = (char*)p->workspace;
+    } else {
+        cudaError_t e = cudaMalloc((void**)&c->ws, L.total);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            c->ws = nullptr;
+            lb_free(c);
+            std::snprintf(g_last_error, sizeof g_last_error, "cudaMalloc(%zu): %s", L.total,
+                          cudaGetErrorString(e));
+            return LB_ERR_ALLOC;
+        }
+        c->own_ws = true;
+    }
+    c->buf[0] = c->ws + L.off_a;
+    c->buf[1] = c->ws + L.off_b;
+    c->stage = (double*)(c->ws + L.off_stage);
+    c->flag = (int*)(c->ws + L.off_flag);
+
+    const size_t n = (size_t)p->Lx * p->Ly;
+    lb_status rs = LB_OK;
+    do {
+        cudaError_t e = cudaSuccess;
+        const double* src[4] = {rho, ux, uy, T};
+        for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+            e = cudaMemcpyAsync(c->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice,
+                                c->stream);
+        }
+        if (e != cudaSuccess) { rs = cuda_fail(e, "cudaMemcpyAsync(fields)"); break; }
+        e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream);
+        if (e != cudaSuccess) { rs = cuda_fail(e, "cudaMemsetAsync(flag)"); break; }
+        if (p->precision == LB_FP64)
+            e = launch_init_fp64(c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n,
+                                 (double*)c->buf[0], c->sp, c->stream);
+        else
+            e = launch_init_fp32dev(c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n,
+                                    (float*)c->buf[0], c->sp, c->stream);
+        if (e != cudaSuccess) { rs = cuda_fail(e, "init kernel launch"); break; }
+        e = cudaStreamSynchronize(c->stream);
+        if (e != cudaSuccess) { rs = cuda_fail(e, "cudaStreamSynchronize(init)"); break; }
+    } while (0);
+    if (rs != LB_OK) {
+        lb_free(c);
+        return rs;
+    }
+    *out = c;
+    return LB_OK;
+}
+
+lb_status lb_step(lb_ctx* c, int n) {
+    if (!c || n < 0) return LB_ERR_ARG;
+    while (n >= GRAPH_STEPS && !c->graph_failed) {
+        const int par = c->cur;
+        if (!c->graph[par] && !capture_graph(c, par)) {
+            c->graph_failed = true;
+            break;
+        }
+        LB_CUDA(cudaGraphLaunch(c->graph[par], c->stream));
+        c->steps += GRAPH_STEPS;
+        n -= GRAPH_STEPS;
+    }
+    for (; n > 0; --n) {
+        lb_status st = launch_one_step(c);
+        if (st != LB_OK) return st;
+    }
+    return LB_OK;
+}
+
+lb_status lb_propagate(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    cudaError_t e = c->p.precision == LB_FP64
+                        ? launch_propagate_fp64((const double*)c->buf[c->cur],
+                                                (double*)c->buf[c->cur ^ 1], c->sp, c->stream)
+                        : launch_propagate_fp32dev((const float*)c->buf[c->cur],
+                                                   (float*)c->buf[c->cur ^ 1], c->sp, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "propagate kernel launch");
+    c->cur ^= 1;
+    c->steps += 1;
+    return LB_OK;
+}
+
+lb_status lb_sync(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return read_flag(c);
+}
+
+lb_status lb_moments_device(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    if (!c) return LB_ERR_ARG;
+    const size_t n = (size_t)c->p.Lx * c->p.Ly;
+    return launch_moments(c, rho ? rho : c->stage, ux ? ux : c->stage + n,
+                          uy ? uy : c->stage + 2 * n, T ? T : c->stage + 3 * n);
+}
+
+lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    if (!c) return LB_ERR_ARG;
+    const size_t n = (size_t)c->p.Lx * c->p.Ly;
+    lb_status st = launch_moments(c, c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n);
+    if (st != LB_OK) return st;
+    double* dst[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        if (dst[k])
+            LB_CUDA(cudaMemcpyAsync(dst[k], c->stage + k * n, n * sizeof(double),
+                                    cudaMemcpyDeviceToHost, c->stream));
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return read_flag(c);
+}
+
+lb_status lb_get_populations(lb_ctx* c, double* f) {
+    if (!c || !f) return LB_ERR_ARG;
+    const size_t n = (size_t)c->p.Lx * c->p.Ly;
+    const size_t skip = (size_t)HALO * c->p.Lx;
+    for (int i = 0; i < NPOP; ++i) {
+        if (c->p.precision == LB_FP64) {
+            const double* src = (const double*)c->buf[c->cur] + (size_t)i * c->sp.plane + skip;
+            LB_CUDA(cudaMemcpyAsync(f + i * n, src, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+        } else {
+            const float* src = (const float*)c->buf[c->cur] + (size_t)i * c->sp.plane + skip;
+            cudaError_t e = launch_plane_from_dev32(src, c->stage, shell_w(shell_of(i)), (long long)n,
+                                                    c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "plane conversion launch");
+            LB_CUDA(cudaMemcpyAsync(f + i * n, c->stage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                    c->stream));
+            LB_CUDA(cudaStreamSynchronize(c->stream));  // the staging plane is reused
+        }
+    }
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return read_flag(c);
+}
+
+lb_status lb_set_populations(lb_ctx* c, const double* f) {
+    if (!c || !f) return LB_ERR_ARG;
+    const size_t n = (size_t)c->p.Lx * c->p.Ly;
+    const size_t skip = (size_t)HALO * c->p.Lx;
+    for (int i = 0; i < NPOP; ++i) {
+        if (c->p.precision == LB_FP64) {
+            double* dst = (double*)c->buf[c->cur] + (size_t)i * c->sp.plane + skip;
+            LB_CUDA(cudaMemcpyAsync(dst, f + i * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream));
+        } else {
+            float* dst = (float*)c->buf[c->cur] + (size_t)i * c->sp.plane + skip;
+            LB_CUDA(cudaMemcpyAsync(c->stage, f + i * n, n * sizeof(double), cudaMemcpyHostToDevice,
+                                    c->stream));
+            cudaError_t e = launch_plane_to_dev32(c->stage, dst, shell_w(shell_of(i)), (long long)n,
+                                                  c->stream);
+            if (e != cudaSuccess) return cuda_fail(e, "plane conversion launch");
+        }
+    }
+    lb_status st = rewrite_halos(c);
+    if (st != LB_OK) return st;
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    return LB_OK;
+}
+
+lb_status lb_steps_done(const lb_ctx* c, long long* n) {
+    if (!c || !n) return LB_ERR_ARG;
+    *n = c->steps;
+    return LB_OK;
+}
+
+}  // extern "C"

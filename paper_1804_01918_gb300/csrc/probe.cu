@@ -1,0 +1,35 @@
+// probe.cu -- FMA-throughput probe (roofline denominator of the ALU-bound kernels).
+#include <cuda_runtime.h>
+
+#include <cstdio>
+
+#include "../../include/lb_probe.h"
+
+namespace {
+
+template <typename T>
+__global__ void fma_chains_kernel(T* __restrict__ out, int iters, T m, T a) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    T x0 = (T)(t & 7), x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+    T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+    for (int k = 0; k < iters; ++k) {
+        x0 = x0 * m + a; x1 = x1 * m + a; x2 = x2 * m + a; x3 = x3 * m + a;
+        x4 = x4 * m + a; x5 = x5 * m + a; x6 = x6 * m + a; x7 = x7 * m + a;
+    }
+    out[t] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
+}  // namespace
+
+extern "C" lb_status lb_probe_fma(int kind, void* stream, int blocks, int threads, int iters,
+                                  void* out) {
+    if (blocks <= 0 || threads <= 0 || threads > 1024 || iters <= 0 || !out) return LB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (kind == 0)
+        fma_chains_kernel<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.9999999, 1e-7);
+    else if (kind == 1)
+        fma_chains_kernel<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.9999f, 1e-4f);
+    else
+        return LB_ERR_ARG;
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}

@@ -1,0 +1,356 @@
+// step_fp64.cu -- FP64 D2Q37 kernels: fused time step, stand-alone propagate, init, moments, halos.
+//
+// Layout in HBM (structure of arrays, Sec. 4 / Fig. 2 "SoA"): f[i][y + HALO][x], x fastest,
+// plane pitch (Ly + 2*HALO) * Lx doubles, three halo rows below row 0 and above row Ly-1 that
+// hold the wall populations. Two copies (the prv/nxt double buffer of the Fig. 3 listing).
+//
+// The fused step (one thread per site; a warp covers 32 consecutive x of one row):
+//   1. pull: f_i(x, y) = src_i((x - c_ix) mod Lx, y - c_iy) (Fig. 3 listing: read at an offset);
+//      every source element is read by exactly one destination site, so a warp's 37 loads are
+//      37 coalesced row segments, shifted by at most 3 elements;
+//   2. collide (Sec. 3): moments from bins of equal c_x / equal c_y, shifted Hermite equilibrium
+//      evaluated once per opposite pair (even/odd split), BGK relaxation;
+//   3. store to dst with evict-first hints (write-once stream; GPU stores do no read-for-ownership,
+//      the effect the paper gets from non-temporal stores, Sec. 4);
+//   4. threads of rows 0..2 and Ly-3..Ly-1 also write the wall halo rows of dst.
+// On GB300 this kernel is bound by the FP64 pipe (about 380 FP64 operations per site against 592
+// bytes of traffic), so the code minimises FP64 operations; index math is integer-only.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "d2q37_gpu.cuh"
+#include "kernels.cuh"
+
+namespace lbg {
+
+namespace {
+
+__device__ __forceinline__ long long plane_off(int i, long long plane) { return (long long)i * plane; }
+
+// Source index of population i for destination site (x, y) under the pull.
+template <int I>
+__device__ __forceinline__ int pull_index(int x, int y, int Lx, int Ly, int y_periodic) {
+    constexpr int cx = cx_of(I);
+    constexpr int cy = cy_of(I);
+    int xs = x - cx;
+    if (cx > 0) {
+        if (xs < 0) xs += Lx;
+    } else if (cx < 0) {
+        if (xs >= Lx) xs -= Lx;
+    }
+    int ys = y - cy;
+    if (y_periodic) {
+        if (cy > 0) {
+            if (ys < 0) ys += Ly;
+        } else if (cy < 0) {
+            if (ys >= Ly) ys -= Ly;
+        }
+    }
+    return (ys + HALO) * Lx + xs;
+}
+
+// True unless v is a positive finite double (integer test on the bit pattern).
+__device__ __forceinline__ bool bad_positive(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
+}
+
+template <int I>
+struct PullAll {
+    __device__ __forceinline__ static void run(const double* __restrict__ src, double* f, int x,
+                                               int y, int Lx, int Ly, int yp, long long plane) {
+        PullAll<I - 1>::run(src, f, x, y, Lx, Ly, yp, plane);
+        f[I] = __ldg(src + plane_off(I, plane) + pull_index<I>(x, y, Lx, Ly, yp));
+    }
+};
+template <>
+struct PullAll<-1> {
+    __device__ __forceinline__ static void run(const double*, double*, int, int, int, int, int,
+                                               long long) {}
+};
+
+struct SiteMoments {
+    double rho, ux, uy, T;
+};
+
+// rho, u, T of one site from bins of equal c_x and equal c_y:
+//   rho = sum f, rho u = r sum f c, rho (u^2 + D T) = r^2 sum f |c|^2.
+__device__ __forceinline__ SiteMoments site_moments(const double* f, double r, double r2) {
+    double sx[7], sy[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        sx[k] = 0.0;
+        sy[k] = 0.0;
+    }
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        sx[cx_of(i) + 3] += f[i];
+        sy[cy_of(i) + 3] += f[i];
+    }
+    const double px1 = sx[4] + sx[2], px2 = sx[5] + sx[1], px3 = sx[6] + sx[0];
+    const double mx1 = sx[4] - sx[2], mx2 = sx[5] - sx[1], mx3 = sx[6] - sx[0];
+    const double py1 = sy[4] + sy[2], py2 = sy[5] + sy[1], py3 = sy[6] + sy[0];
+    const double my1 = sy[4] - sy[2], my2 = sy[5] - sy[1], my3 = sy[6] - sy[0];
+    const double rho = sx[3] + px1 + px2 + px3;
+    const double jx = fma(3.0, mx3, fma(2.0, mx2, mx1));
+    const double jy = fma(3.0, my3, fma(2.0, my2, my1));
+    const double ex = fma(9.0, px3, fma(4.0, px2, px1));
+    const double ey = fma(9.0, py3, fma(4.0, py2, py1));
+    const double inv = 1.0 / rho;
+    const double rinv = r * inv;
+    SiteMoments m;
+    m.rho = rho;
+    m.ux = jx * rinv;
+    m.uy = jy * rinv;
+    const double u2 = m.ux * m.ux + m.uy * m.uy;
+    m.T = 0.5 * fma(r2 * inv, ex + ey, -u2);
+    return m;
+}
+
+// Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S toward the equilibrium.
+template <int I>
+__device__ __forceinline__ void relax_pair(const double* f, double* __restrict__ dst, long long dsto,
+                                           long long plane, double urx, double ury,
+                                           const double* A0, const double* A2, const double* B1,
+                                           const double* W, double omc) {
+    constexpr int S = shellh(I);
+    constexpr double cx = (double)cxh(I);
+    constexpr double cy = (double)cyh(I);
+    double a;
+    if (cyh(I) == 0)
+        a = cx * urx;
+    else if (cxh(I) == 0)
+        a = cy * ury;
+    else
+        a = fma(cx, urx, cy * ury);
+    const double a2 = a * a;
+    const double e = fma(a2, fma(a2, 1.0 / 24.0, A2[S]), A0[S]);
+    const double o = a * fma(a2, 1.0 / 6.0, B1[S]);
+    const double we = W[S] * e;
+    const double wo = W[S] * o;
+    __stcs(dst + plane_off(I, plane) + dsto, fma(omc, f[I], we + wo));
+    __stcs(dst + plane_off(I + NPAIR, plane) + dsto, fma(omc, f[I + NPAIR], we - wo));
+}
+
+template <int I>
+struct RelaxAll {
+    __device__ __forceinline__ static void run(const double* f, double* __restrict__ dst,
+                                               long long dsto, long long plane, double urx,
+                                               double ury, const double* A0, const double* A2,
+                                               const double* B1, const double* W, double omc) {
+        RelaxAll<I - 1>::run(f, dst, dsto, plane, urx, ury, A0, A2, B1, W, omc);
+        relax_pair<I>(f, dst, dsto, plane, urx, ury, A0, A2, B1, W, omc);
+    }
+};
+template <>
+struct RelaxAll<0> {
+    __device__ __forceinline__ static void run(const double*, double*, long long, long long, double,
+                                               double, const double*, const double*, const double*,
+                                               const double*, double) {}
+};
+
+// Per-shell coefficients of the equilibrium at (theta, u2) scaled by prefactor W_s = wscale w_s.
+__device__ __forceinline__ void shell_coefficients(const StepParams& P, double th, double u2,
+                                                   double wscale, double* A0, double* A2,
+                                                   double* B1, double* W) {
+    const double a00 = fma(u2, fma(u2, 0.125, -0.5), 1.0);
+    const double a20 = fma(u2, -0.25, 0.5);
+    const double b10 = fma(u2, -0.5, 1.0);
+    const double thu2 = th * u2;
+    const double th2 = th * th;
+#pragma unroll
+    for (int s = 0; s < NSHELL; ++s) {
+        A0[s] = fma(P.sh[s].gamma, th2, fma(P.sh[s].beta, thu2, fma(P.sh[s].alpha, th, a00)));
+        A2[s] = fma(P.sh[s].delta, th, a20);
+        B1[s] = fma(P.sh[s].eps, th, b10);
+        W[s] = wscale * P.sh[s].w;
+    }
+}
+
+__global__ void __launch_bounds__(SITE_BLOCK)
+step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P,
+                 int* __restrict__ flag) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= Lx * Ly) return;
+    const int y = site / Lx;
+    const int x = site - y * Lx;
+    const long long plane = P.plane;
+
+    double f[NPOP];
+    PullAll<NPOP - 1>::run(src, f, x, y, Lx, Ly, P.y_periodic, plane);
+
+    const SiteMoments m = site_moments(f, P.r, P.r2);
+    if (bad_positive(m.rho) || bad_positive(m.T)) atomicOr(flag, 1);
+
+    // forcing: equilibrium at u + tau g, T + tau (1 - tau) |g|^2 / D
+    const double uxs = m.ux + P.tgx;
+    const double uys = m.uy + P.tgy;
+    const double th = (m.T + P.dT_force) - 1.0;
+    const double u2 = uxs * uxs + uys * uys;
+    double A0[NSHELL], A2[NSHELL], B1[NSHELL], W[NSHELL];
+    shell_coefficients(P, th, u2, m.rho * P.omega, A0, A2, B1, W);
+
+    const long long dsto = (long long)(y + HALO) * Lx + x;
+    __stcs(dst + dsto, fma(P.omc, f[0], W[0] * A0[0]));
+    RelaxAll<NPAIR>::run(f, dst, dsto, plane, P.r * uxs, P.r * uys, A0, A2, B1, W, P.omc);
+
+    if (!P.y_periodic) {
+        // wall halo rows of dst from this row's density (collide conserves it)
+        if (y < HALO) {
+            const long long o = (long long)(HALO - 1 - y) * Lx + x;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) __stcs(dst + plane_off(i, plane) + o, m.rho * P.wall_bot[i]);
+        }
+        if (y >= Ly - HALO) {
+            const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) __stcs(dst + plane_off(i, plane) + o, m.rho * P.wall_top[i]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(SITE_BLOCK)
+propagate_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= Lx * Ly) return;
+    const int y = site / Lx;
+    const int x = site - y * Lx;
+    const long long plane = P.plane;
+    double f[NPOP];
+    PullAll<NPOP - 1>::run(src, f, x, y, Lx, Ly, P.y_periodic, plane);
+    const long long dsto = (long long)(y + HALO) * Lx + x;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) dst[plane_off(i, plane) + dsto] = f[i];
+    if (y < HALO) {  // carry the halo rows over unchanged
+        const long long ob = (long long)y * Lx + x;
+        const long long ot = (long long)(Ly + HALO + y) * Lx + x;
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) {
+            dst[plane_off(i, plane) + ob] = src[plane_off(i, plane) + ob];
+            dst[plane_off(i, plane) + ot] = src[plane_off(i, plane) + ot];
+        }
+    }
+}
+
+// Full (unshifted) equilibrium of one site into out[37].
+__device__ __forceinline__ void site_equilibrium(const StepParams& P, double rho, double ux,
+                                                 double uy, double T, double* out) {
+    double A0[NSHELL], A2[NSHELL], B1[NSHELL], W[NSHELL];
+    shell_coefficients(P, T - 1.0, ux * ux + uy * uy, rho, A0, A2, B1, W);
+    out[0] = W[0] * A0[0];
+    const double urx = P.r * ux, ury = P.r * uy;
+#pragma unroll
+    for (int i = 1; i <= NPAIR; ++i) {
+        const int s = shellh(i);
+        const double a = cxh(i) * urx + cyh(i) * ury;
+        const double a2 = a * a;
+        const double e = fma(a2, fma(a2, 1.0 / 24.0, A2[s]), A0[s]);
+        const double o = a * fma(a2, 1.0 / 6.0, B1[s]);
+        out[i] = W[s] * (e + o);
+        out[i + NPAIR] = W[s] * (e - o);
+    }
+}
+
+__global__ void __launch_bounds__(SITE_BLOCK)
+init_fp64_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
+                 const double* __restrict__ uy, const double* __restrict__ T,
+                 double* __restrict__ f, const StepParams P) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= Lx * Ly) return;
+    const int y = site / Lx;
+    const int x = site - y * Lx;
+    double fe[NPOP];
+    site_equilibrium(P, rho[site], ux[site], uy[site], T[site], fe);
+    const long long o = (long long)(y + HALO) * Lx + x;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) f[plane_off(i, P.plane) + o] = fe[i];
+}
+
+// Wall halos of f from the current interior rows: halo row -1-k <- rho(x, k) * wall_bot,
+// halo row Ly+k <- rho(x, Ly-1-k) * wall_top, k = 0, 1, 2.
+__global__ void halo_fp64_kernel(double* __restrict__ f, const StepParams P) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= HALO * Lx) return;
+    const int k = t / Lx;
+    const int x = t - k * Lx;
+    const long long ib = (long long)(HALO + k) * Lx + x;
+    const long long it = (long long)(HALO + Ly - 1 - k) * Lx + x;
+    double rb = 0.0, rt = 0.0;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        rb += f[plane_off(i, P.plane) + ib];
+        rt += f[plane_off(i, P.plane) + it];
+    }
+    const long long ob = (long long)(HALO - 1 - k) * Lx + x;
+    const long long ot = (long long)(Ly + HALO + k) * Lx + x;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        f[plane_off(i, P.plane) + ob] = rb * P.wall_bot[i];
+        f[plane_off(i, P.plane) + ot] = rt * P.wall_top[i];
+    }
+}
+
+__global__ void __launch_bounds__(SITE_BLOCK)
+moments_fp64_kernel(const double* __restrict__ f, const StepParams P, double* __restrict__ rho,
+                    double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ T) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= Lx * Ly) return;
+    const int y = site / Lx;
+    const int x = site - y * Lx;
+    const long long o = (long long)(y + HALO) * Lx + x;
+    double v[NPOP];
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, P.plane) + o];
+    const SiteMoments m = site_moments(v, P.r, P.r2);
+    rho[site] = m.rho;
+    ux[site] = m.ux;
+    uy[site] = m.uy;
+    T[site] = m.T;
+}
+
+inline int site_blocks(const StepParams& P) {
+    const long long n = (long long)P.Lx * P.Ly;
+    return (int)((n + SITE_BLOCK - 1) / SITE_BLOCK);
+}
+
+}  // namespace
+
+cudaError_t launch_step_fp64(const double* src, double* dst, const StepParams& P, int* flag,
+                             cudaStream_t s) {
+    step_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_propagate_fp64(const double* src, double* dst, const StepParams& P,
+                                  cudaStream_t s) {
+    propagate_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(src, dst, P);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy,
+                             const double* T, double* f, const StepParams& P, cudaStream_t s) {
+    init_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(rho, ux, uy, T, f, P);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess || P.y_periodic) return e;
+    return launch_halo_fp64(f, P, s);
+}
+
+cudaError_t launch_moments_fp64(const double* f, const StepParams& P, double* rho, double* ux,
+                                double* uy, double* T, cudaStream_t s) {
+    moments_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(f, P, rho, ux, uy, T);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_fp64(double* f, const StepParams& P, cudaStream_t s) {
+    const int n = HALO * P.Lx;
+    halo_fp64_kernel<<<(n + 127) / 128, 128, 0, s>>>(f, P);
+    return cudaGetLastError();
+}
+
+}  // namespace lbg

@@ -1,0 +1,260 @@
+"""Python binding of the D2Q37 C ABI (include/lb_d2q37.h): argument marshalling only.
+
+Every step of the time step runs in the CUDA library liblb_d2q37.so; this module only converts
+arguments. PyTorch supplies the device memory (the context workspace is a torch CUDA tensor)
+and the stream (torch's current stream unless one is given). If the library is missing the
+import fails loudly: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+NPOP = 37
+LB_FP64, LB_FP32DEV = 0, 1
+
+_STATUS = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_ALLOC", 3: "LB_ERR_CUDA",
+           4: "LB_ERR_NONFINITE", 5: "LB_ERR_STATE"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblb_d2q37.so")
+
+
+class LBError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = f"{where}: {_STATUS.get(status, status)}"
+        if status == 3:
+            msg += f" ({last_error()})"
+        super().__init__(msg)
+
+
+class NonFiniteError(LBError):
+    pass
+
+
+class lb_params(C.Structure):
+    _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("tau", C.c_double), ("gx", C.c_double),
+                ("gy", C.c_double), ("T_top", C.c_double), ("T_bottom", C.c_double),
+                ("y_periodic", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
+                ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """The loaded CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing: build it with "
+                              "`python -c 'import __graft_entry__ as g; g.build()'`")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, ip = C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_int)
+        L.lb_status_str.restype = C.c_char_p
+        L.lb_status_str.argtypes = [C.c_int]
+        L.lb_last_error.restype = C.c_char_p
+        L.lb_velocity_set.argtypes = [ip, ip, dp, dp]
+        L.lb_workspace_bytes.argtypes = [C.POINTER(lb_params), C.POINTER(C.c_size_t)]
+        L.lb_init.argtypes = [C.POINTER(lb_params), vp, vp, vp, vp, C.POINTER(vp)]
+        L.lb_step.argtypes = [vp, C.c_int]
+        L.lb_propagate.argtypes = [vp]
+        L.lb_sync.argtypes = [vp]
+        L.lb_moments.argtypes = [vp, vp, vp, vp, vp]
+        L.lb_moments_device.argtypes = [vp, vp, vp, vp, vp]
+        L.lb_get_populations.argtypes = [vp, vp]
+        L.lb_set_populations.argtypes = [vp, vp]
+        L.lb_steps_done.argtypes = [vp, C.POINTER(C.c_longlong)]
+        L.lb_free.argtypes = [vp]
+        L.lb_free.restype = None
+        L.lb_probe_fma.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp]
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().lb_last_error().decode()
+
+
+def check(status: int, where: str) -> None:
+    if status == 4:
+        raise NonFiniteError(status, where)
+    if status != 0:
+        raise LBError(status, where)
+
+
+def velocity_set():
+    """(cx[37], cy[37], w[37], r) in the library's population order."""
+    cx = np.zeros(NPOP, np.int32)
+    cy = np.zeros(NPOP, np.int32)
+    w = np.zeros(NPOP, np.float64)
+    r = C.c_double()
+    check(lib().lb_velocity_set(cx.ctypes.data_as(C.POINTER(C.c_int)),
+                                cy.ctypes.data_as(C.POINTER(C.c_int)),
+                                w.ctypes.data_as(C.POINTER(C.c_double)), C.byref(r)),
+          "lb_velocity_set")
+    return cx, cy, w, r.value
+
+
+def _precision_code(p) -> int:
+    if p in (LB_FP64, "fp64", "f64"):
+        return LB_FP64
+    if p in (LB_FP32DEV, "fp32dev", "fp32"):
+        return LB_FP32DEV
+    raise ValueError(f"unknown precision {p!r}")
+
+
+def make_params(Lx, Ly, tau, gx=0.0, gy=0.0, T_top=1.0, T_bottom=1.0, y_periodic=False,
+                precision=LB_FP64, stream=None, workspace=0, workspace_bytes=0) -> lb_params:
+    return lb_params(int(Lx), int(Ly), float(tau), float(gx), float(gy), float(T_top),
+                     float(T_bottom), int(bool(y_periodic)), _precision_code(precision),
+                     stream, workspace, workspace_bytes)
+
+
+def workspace_bytes(Lx, Ly, precision=LB_FP64) -> int:
+    p = make_params(Lx, Ly, 1.0, precision=precision)
+    n = C.c_size_t()
+    check(lib().lb_workspace_bytes(C.byref(p), C.byref(n)), "lb_workspace_bytes")
+    return n.value
+
+
+def _ptr(a) -> int:
+    """Address of a C-contiguous numpy array or a torch tensor."""
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+def _host_f64(a, shape):
+    if hasattr(a, "data_ptr"):
+        assert a.dtype.__str__() == "torch.float64" and a.is_contiguous() and tuple(a.shape) == shape
+        return a
+    arr = np.ascontiguousarray(a, dtype=np.float64)
+    if arr.shape != shape:
+        arr = np.ascontiguousarray(np.broadcast_to(arr, shape))
+    return arr
+
+
+@dataclass
+class Lattice:
+    """One D2Q37 lattice on the GPU (wraps an lb_ctx).
+
+    fields: host arrays (rho, ux, uy, T), each [Ly][Lx] float64 (numpy or pinned torch tensors).
+    The workspace is a torch uint8 CUDA tensor unless ``own_memory`` asks the library to allocate.
+    Work runs on ``stream`` (a torch.cuda.Stream; a new one if None); torch work that reads the
+    outputs of moments_device must run on, or wait for, that stream.
+    """
+
+    Lx: int
+    Ly: int
+    tau: float
+    rho: object
+    ux: object
+    uy: object
+    T: object
+    gx: float = 0.0
+    gy: float = 0.0
+    T_top: float = 1.0
+    T_bottom: float = 1.0
+    y_periodic: bool = False
+    precision: object = LB_FP64
+    stream: object = None
+    own_memory: bool = False
+
+    def __post_init__(self):
+        import torch
+        self._ctx = C.c_void_p()
+        shape = (self.Ly, self.Lx)
+        fields = [_host_f64(v, shape) for v in (self.rho, self.ux, self.uy, self.T)]
+        prec = _precision_code(self.precision)
+        if self.stream is None:
+            # a stream of its own: the legacy default stream cannot be captured into a CUDA graph
+            self.stream = torch.cuda.Stream()
+        sh = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else self.stream
+        nbytes = workspace_bytes(self.Lx, self.Ly, prec)
+        self._ws = None
+        ws_ptr = 0
+        if not self.own_memory:
+            self._ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            ws_ptr = self._ws.data_ptr()
+        self._params = make_params(self.Lx, self.Ly, self.tau, self.gx, self.gy, self.T_top,
+                                   self.T_bottom, self.y_periodic, prec, sh, ws_ptr,
+                                   nbytes if ws_ptr else 0)
+        check(lib().lb_init(C.byref(self._params), *[_ptr(f) for f in fields], C.byref(self._ctx)),
+              "lb_init")
+        self.rho = self.ux = self.uy = self.T = None  # the context holds its own copy
+
+    @classmethod
+    def from_fields(cls, fields, tau, **kw):
+        """Build from an inputs.RTFields (walls and gravity taken from it)."""
+        kw.setdefault("gy", fields.gy)
+        kw.setdefault("T_top", fields.T_top)
+        kw.setdefault("T_bottom", fields.T_bottom)
+        Ly, Lx = fields.rho.shape
+        return cls(Lx, Ly, tau, fields.rho, fields.ux, fields.uy, fields.T, **kw)
+
+    @property
+    def sites(self) -> int:
+        return self.Lx * self.Ly
+
+    def step(self, n: int = 1) -> None:
+        check(lib().lb_step(self._ctx, int(n)), "lb_step")
+
+    def propagate(self) -> None:
+        check(lib().lb_propagate(self._ctx), "lb_propagate")
+
+    def sync(self) -> None:
+        check(lib().lb_sync(self._ctx), "lb_sync")
+
+    def moments(self, out=None):
+        """(rho, ux, uy, T) as host float64 arrays [Ly][Lx] (or into the given host buffers)."""
+        if out is None:
+            out = tuple(np.empty((self.Ly, self.Lx), np.float64) for _ in range(4))
+        check(lib().lb_moments(self._ctx, *[_ptr(o) if o is not None else None for o in out]),
+              "lb_moments")
+        return out
+
+    def moments_device(self, out):
+        """Write (rho, ux, uy, T) into 4 torch float64 CUDA tensors of Lx*Ly elements (async)."""
+        check(lib().lb_moments_device(self._ctx, *[o.data_ptr() if o is not None else None for o in out]),
+              "lb_moments_device")
+        return out
+
+    def get_populations(self) -> np.ndarray:
+        f = np.empty((NPOP, self.Ly, self.Lx), np.float64)
+        check(lib().lb_get_populations(self._ctx, f.ctypes.data), "lb_get_populations")
+        return f
+
+    def set_populations(self, f) -> None:
+        f = np.ascontiguousarray(f, dtype=np.float64)
+        assert f.shape == (NPOP, self.Ly, self.Lx)
+        check(lib().lb_set_populations(self._ctx, f.ctypes.data), "lb_set_populations")
+
+    @property
+    def steps_done(self) -> int:
+        n = C.c_longlong()
+        check(lib().lb_steps_done(self._ctx, C.byref(n)), "lb_steps_done")
+        return n.value
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().lb_free(self._ctx)
+            self._ctx = C.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def probe_fma(kind: str, blocks: int, threads: int, iters: int, out, stream=None) -> None:
+    """Launch the FMA-throughput probe (kind 'fp64' or 'fp32') into the torch tensor `out`."""
+    k = {"fp64": 0, "fp32": 1}[kind]
+    sh = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    check(lib().lb_probe_fma(k, sh, blocks, threads, iters, out.data_ptr()), "lb_probe_fma")

@@ -1,0 +1,203 @@
+"""GPU parity of the FP64 path (through the C ABI) against the CPU oracle.
+
+Bar: propagate bit-exact (a pure copy, Fig. 3 listing); the fused FP64 step within 1e-12
+relative per population after 100 steps (the oracle and the kernel sum in different orders and
+the kernel fuses multiply-adds, so results agree to rounding, not bit for bit).
+"""
+import numpy as np
+import pytest
+
+from paper_1804_01918_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-12
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_01918_gb300 import build, lb
+    build.build()
+    return lb
+
+
+def gpu_to_oracle(L, orc, f_planes):
+    cx, cy, _, _ = L.velocity_set()
+    return orc.from_planes(f_planes, cx, cy)
+
+
+def oracle_to_gpu(L, orc, f_site):
+    cx, cy, _, _ = L.velocity_set()
+    return orc.to_planes(f_site, cx, cy)
+
+
+def rel_err(a, b):
+    return float(np.max(np.abs(a - b) / np.abs(b)))
+
+
+def test_init_is_the_equilibrium(L, orc):
+    st = inputs.rayleigh_taylor(64, 256, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    f = gpu_to_oracle(L, orc, lat.get_populations())
+    assert rel_err(f, orc.init_fields(st)) < 1e-14
+
+
+@pytest.mark.parametrize("Lx,Ly", [(11, 9), (64, 256), (70, 50)])
+def test_propagate_is_bit_exact_periodic(L, orc, Lx, Ly):
+    rng = np.random.default_rng(Lx * 1000 + Ly)
+    st = inputs.random_state(Lx, Ly, seed=1)
+    lat = L.Lattice.from_fields(st, tau=0.9, y_periodic=True)
+    f0 = rng.uniform(0.0, 1.0, (37, Ly, Lx))
+    lat.set_populations(f0)
+    lat.propagate()
+    got = lat.get_populations()
+    src = np.zeros((Ly + 6, Lx, 37))
+    src[3:Ly + 3] = gpu_to_oracle(L, orc, f0)
+    want = oracle_to_gpu(L, orc, orc.propagate(src, Lx, Ly, y_periodic=True))
+    assert np.array_equal(got, want)
+
+
+def test_propagate_with_walls_bit_exact_away_from_walls(L, orc):
+    """Rows 3..Ly-4 read no halo row: bit-exact. Rows next to a wall read halo values that both
+    sides computed as a rest equilibrium (rounding-level agreement)."""
+    Lx, Ly = 40, 30
+    rng = np.random.default_rng(5)
+    st = inputs.random_state(Lx, Ly, seed=2)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    f0 = orc.equilibrium(st.rho, st.ux, st.uy, st.T) * (1 + 0.01 * rng.uniform(-1, 1, (Ly, Lx, 37)))
+    lat.set_populations(oracle_to_gpu(L, orc, f0))
+    lat.propagate()
+    got = gpu_to_oracle(L, orc, lat.get_populations())
+    want = orc.propagate(orc.with_walls(f0, st.T_top, st.T_bottom), Lx, Ly, y_periodic=False)
+    assert np.array_equal(got[3:Ly - 3], want[3:Ly - 3])
+    assert rel_err(got, want) < 1e-14
+
+
+@pytest.mark.parametrize("Lx,Ly,steps", [(64, 256, 100), (70, 50, 100), (13, 11, 30)])
+def test_fused_step_matches_oracle_rayleigh_taylor(L, orc, Lx, Ly, steps):
+    st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    lat.step(steps)
+    got = gpu_to_oracle(L, orc, lat.get_populations())
+    want = orc.run(orc.init_fields(st), tau=0.9, nsteps=steps, gy=st.gy, T_top=st.T_top,
+                   T_bottom=st.T_bottom)
+    assert rel_err(got, want) <= TOL
+
+
+def test_fused_step_matches_oracle_random_state_strong_gravity(L, orc):
+    """Far-from-equilibrium start, strong gravity along both axes, walls at unequal temperature."""
+    Lx, Ly = 33, 40
+    st = inputs.random_state(Lx, Ly, seed=9)
+    lat = L.Lattice.from_fields(st, tau=0.7, gx=1e-3, gy=-2e-3)
+    lat.step(40)
+    got = gpu_to_oracle(L, orc, lat.get_populations())
+    want = orc.run(orc.init_fields(st), tau=0.7, nsteps=40, gx=1e-3, gy=-2e-3,
+                   T_top=st.T_top, T_bottom=st.T_bottom)
+    assert rel_err(got, want) <= TOL
+
+
+def test_moments_match_oracle(L, orc):
+    st = inputs.rayleigh_taylor(64, 256, R=2.0, seed=3)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    lat.step(7)
+    rho, ux, uy, T = lat.moments()
+    f = gpu_to_oracle(L, orc, lat.get_populations())
+    orho, oux, ouy, oT = orc.moments(f)
+    assert rel_err(rho, orho) < 1e-14 and rel_err(T, oT) < 1e-14
+    assert np.max(np.abs(ux - oux)) < 1e-15 and np.max(np.abs(uy - ouy)) < 1e-15
+
+
+def test_graph_replay_equals_single_launches(L):
+    st = inputs.rayleigh_taylor(64, 64, R=2.0, seed=4)
+    a = L.Lattice.from_fields(st, tau=0.9)
+    b = L.Lattice.from_fields(st, tau=0.9)
+    a.step(37)                 # two 16-step graph replays + 5 single launches
+    for _ in range(37):
+        b.step(1)
+    assert a.steps_done == b.steps_done == 37
+    assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+def test_checkpoint_resume_is_bit_identical(L):
+    st = inputs.random_state(48, 40, seed=6)
+    a = L.Lattice.from_fields(st, tau=0.8, y_periodic=True)
+    a.step(20)
+    b = L.Lattice.from_fields(st, tau=0.8, y_periodic=True)
+    b.step(9)
+    snap = b.get_populations()
+    c = L.Lattice.from_fields(st, tau=0.8, y_periodic=True, own_memory=True)
+    c.set_populations(snap)
+    c.step(11)
+    assert np.array_equal(a.get_populations(), c.get_populations())
+
+
+def test_library_owned_memory_and_stream(L, orc):
+    st = inputs.rayleigh_taylor(32, 64, R=2.0, seed=1)
+    lat = L.Lattice.from_fields(st, tau=0.9, own_memory=True, stream=0)
+    lat.step(5)
+    got = gpu_to_oracle(L, orc, lat.get_populations())
+    want = orc.run(orc.init_fields(st), tau=0.9, nsteps=5, gy=st.gy, T_top=st.T_top,
+                   T_bottom=st.T_bottom)
+    assert rel_err(got, want) <= TOL
+
+
+def test_nonfinite_state_is_reported(L):
+    """A NaN planted on the host is flagged by the step kernel and reported once by lb_sync."""
+    st = inputs.rayleigh_taylor(32, 32, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    f = lat.get_populations()
+    f[5, 10, 7] = np.nan
+    lat.set_populations(f)
+    lat.step(1)
+    with pytest.raises(L.NonFiniteError):
+        lat.sync()
+    lat.sync()  # the flag was cleared
+
+
+def test_rest_state_with_walls_stays_at_rest(L):
+    cx, cy, w, r = L.velocity_set()
+    Lx, Ly = 40, 24
+    lat = L.Lattice(Lx, Ly, 0.9, np.ones((Ly, Lx)), np.zeros((Ly, Lx)), np.zeros((Ly, Lx)),
+                    np.ones((Ly, Lx)))
+    lat.step(100)
+    f = lat.get_populations()
+    assert np.max(np.abs(f - w[:, None, None])) < 1e-14
+
+
+def _window_oracle(orc, st, x0, y0, n, half, tau):
+    """Oracle populations at (x0, y0) after n steps computed on a window of the lattice around it.
+    Wrong values enter a window from its cut edges at <= 3 sites per step, so the centre of a
+    window with half-width >= 3 (n + 1) is exact. Windows wrap in x and stop at real walls."""
+    Ly, Lx = st.rho.shape
+    xs = np.arange(x0 - half, x0 + half + 1) % Lx
+    ylo, yhi = max(0, y0 - half), min(Ly, y0 + half + 1)
+    sub = [a[ylo:yhi][:, xs] for a in (st.rho, st.ux, st.uy, st.T)]
+    f0 = orc.equilibrium(*sub)
+    out = orc.run(f0, tau=tau, nsteps=n, gy=st.gy, T_top=st.T_top, T_bottom=st.T_bottom, nthreads=1)
+    return out[y0 - ylo, half]
+
+
+def test_full_size_2304x8192_sampled_sites_match_oracle(L, orc):
+    """The bench workload (2304 x 8192, FP64, RT initial state) in the bench's launch
+    configuration; sampled sites -- including the x wrap and both walls -- against the oracle
+    run on windows around them."""
+    Lx, Ly, n, tau = 2304, 8192, 4, 0.9
+    st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=tau)
+    lat.step(n)
+    f = lat.get_populations()
+    cx, cy, _, _ = L.velocity_set()
+    perm = orc.order_map(cx, cy)
+    half = 3 * (n + 1)
+    rng = np.random.default_rng(0)
+    samples = [(0, 0), (Lx - 1, Ly - 1), (1, 2), (Lx - 2, Ly - 3), (1151, 4095), (5, Ly // 2)]
+    samples += [(int(rng.integers(Lx)), int(rng.integers(Ly))) for _ in range(10)]
+    for (x0, y0) in samples:
+        want = _window_oracle(orc, st, x0, y0, n, half, tau)
+        got = f[:, y0, x0]
+        got_o = np.empty(37)
+        got_o[perm] = got
+        assert rel_err(got_o, want) <= TOL, (x0, y0)
