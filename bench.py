@@ -146,16 +146,21 @@ def oracle_mlups(rows, steps, nthreads):
 
 
 def cpu_baseline(target_s=15.0):
+    """The oracle on the same workload, as many whole steps as fit ~target_s of CPU time (a
+    band of rows instead when even one full step would take longer)."""
     from oracle import oracle as orc
     nthreads = orc.default_threads()
     rate, _ = oracle_mlups(64, 1, nthreads)                 # calibration
-    rows = int(max(64, min(LY, rate * 1e6 * target_s / 3 / LX)))
-    steps = 3
+    full_step_s = LX * LY / (rate * 1e6)
+    if full_step_s <= target_s:
+        rows, steps = LY, int(max(1, min(50, round(target_s / full_step_s))))
+    else:
+        rows, steps = int(max(64, LY * target_s / full_step_s)), 1
     v, dt = oracle_mlups(rows, steps, nthreads)
+    what = "the whole lattice" if rows == LY else f"a {LX}x{rows} band (walls at the band edges) of"
     return {"value": round(v, 3), "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
-            "sample": f"{steps} steps of a {LX}x{rows} band (rows {LY // 2 - rows // 2}.."
-                      f"{LY // 2 + (rows + 1) // 2 - 1}) of the {LX}x{LY} FP64 Rayleigh-Taylor "
-                      f"workload, walls at the band edges, {dt:.1f} s"}
+            "sample": f"{steps} steps of {what} the {LX}x{LY} FP64 Rayleigh-Taylor workload, "
+                      f"{dt:.1f} s of CPU time"}
 
 
 def run_reference(args):
@@ -227,7 +232,13 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--lattice", default=None,
+                    help="LXxLY of a smaller case for profiling (default: the 2304x8192 workload)")
+    ap.add_argument("--precision", choices=["fp64", "fp32dev"], default="fp64")
     args = ap.parse_args()
+    if args.lattice:
+        global LX, LY
+        LX, LY = (int(v) for v in args.lattice.lower().split("x"))
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
@@ -251,7 +262,7 @@ def main():
 
     st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=rank)
     stream = torch.cuda.Stream()
-    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream)
+    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision=args.precision)
     lat.step(args.warmup)
     lat.sync()
     probe_tf = fp64_probe(lb, torch, stream)

@@ -21,221 +21,19 @@
 
 #include "d2q37_gpu.cuh"
 #include "kernels.cuh"
+#include "site_fp32dev.cuh"
 
 namespace lbg {
 
 namespace {
 
-__device__ __forceinline__ long long poff(int i, long long plane) { return (long long)i * plane; }
-
-template <int I>
-__device__ __forceinline__ int pull_index32(int x, int y, int Lx, int Ly, int y_periodic) {
-    constexpr int cx = cx_of(I);
-    constexpr int cy = cy_of(I);
-    int xs = x - cx;
-    if (cx > 0) {
-        if (xs < 0) xs += Lx;
-    } else if (cx < 0) {
-        if (xs >= Lx) xs -= Lx;
-    }
-    int ys = y - cy;
-    if (y_periodic) {
-        if (cy > 0) {
-            if (ys < 0) ys += Ly;
-        } else if (cy < 0) {
-            if (ys >= Ly) ys -= Ly;
-        }
-    }
-    return (ys + HALO) * Lx + xs;
-}
-
-template <int I>
-struct Pull32 {
-    __device__ __forceinline__ static void run(const float* __restrict__ src, float* d, int x, int y,
-                                               int Lx, int Ly, int yp, long long plane) {
-        Pull32<I - 1>::run(src, d, x, y, Lx, Ly, yp, plane);
-        d[I] = __ldg(src + poff(I, plane) + pull_index32<I>(x, y, Lx, Ly, yp));
-    }
-};
-template <>
-struct Pull32<-1> {
-    __device__ __forceinline__ static void run(const float*, float*, int, int, int, int, int, long long) {}
-};
-
-__device__ __forceinline__ bool bad_positive64(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    return (b - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
-}
-
-// FP64 sums of FP32 deviations: s0 = sum d, sx = sum d c_x, sy = sum d c_y, se = sum d |c|^2.
-struct DevSums {
-    double s0, sx, sy, se;
-};
-
-__device__ __forceinline__ DevSums dev_sums(const float* d) {
-    double bx[7], by[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        bx[k] = 0.0;
-        by[k] = 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        const double v = (double)d[i];
-        bx[cx_of(i) + 3] += v;
-        by[cy_of(i) + 3] += v;
-    }
-    const double px1 = bx[4] + bx[2], px2 = bx[5] + bx[1], px3 = bx[6] + bx[0];
-    const double py1 = by[4] + by[2], py2 = by[5] + by[1], py3 = by[6] + by[0];
-    DevSums s;
-    s.s0 = bx[3] + px1 + px2 + px3;
-    s.sx = fma(3.0, bx[6] - bx[0], fma(2.0, bx[5] - bx[1], bx[4] - bx[2]));
-    s.sy = fma(3.0, by[6] - by[0], fma(2.0, by[5] - by[1], by[4] - by[2]));
-    s.se = fma(9.0, px3, fma(4.0, px2, px1)) + fma(9.0, py3, fma(4.0, py2, py1));
-    return s;
-}
-
-struct Macro {
-    double rho, ux, uy, T;
-};
-
-__device__ __forceinline__ Macro macro_of(const DevSums& s, double r, double r2) {
-    Macro m;
-    m.rho = 1.0 + s.s0;
-    const double inv = 1.0 / m.rho;
-    const double rinv = r * inv;
-    m.ux = s.sx * rinv;
-    m.uy = s.sy * rinv;
-    const double u2 = m.ux * m.ux + m.uy * m.uy;
-    // sum f |c|^2 = D / r^2 + se  ->  rho (u^2 + D T) = r^2 sum f |c|^2 = D + r^2 se
-    m.T = 0.5 * (fma(r2, s.se, DIM) * inv - u2);
-    return m;
-}
-
-// FP32 collide of pair I: deviations of the post-collision populations I and I + NPAIR.
-template <int I>
-__device__ __forceinline__ void collide_pair32(float* d, float urx, float ury, const float* A0m1,
-                                               const float* A2, const float* B1, const float* Wd,
-                                               float drho, float omc) {
-    constexpr int S = shellh(I);
-    constexpr float cx = (float)cxh(I);
-    constexpr float cy = (float)cyh(I);
-    float a;
-    if (cyh(I) == 0)
-        a = cx * urx;
-    else if (cxh(I) == 0)
-        a = cy * ury;
-    else
-        a = fmaf(cx, urx, cy * ury);
-    const float a2 = a * a;
-    const float em1 = fmaf(a2, fmaf(a2, 1.0f / 24.0f, A2[S]), A0m1[S]);
-    const float o = a * fmaf(a2, 1.0f / 6.0f, B1[S]);
-    const float pp = em1 + o, pm = em1 - o;
-    // w (rho P - 1) = w (drho (1 + p) + p)
-    const float qp = fmaf(drho, pp, drho + pp);
-    const float qm = fmaf(drho, pm, drho + pm);
-    d[I] = fmaf(omc, d[I], Wd[S] * qp);
-    d[I + NPAIR] = fmaf(omc, d[I + NPAIR], Wd[S] * qm);
-}
-
-template <int I>
-struct Collide32 {
-    __device__ __forceinline__ static void run(float* d, float urx, float ury, const float* A0m1,
-                                               const float* A2, const float* B1, const float* Wd,
-                                               float drho, float omc) {
-        Collide32<I - 1>::run(d, urx, ury, A0m1, A2, B1, Wd, drho, omc);
-        collide_pair32<I>(d, urx, ury, A0m1, A2, B1, Wd, drho, omc);
-    }
-};
-template <>
-struct Collide32<0> {
-    __device__ __forceinline__ static void run(float*, float, float, const float*, const float*,
-                                               const float*, const float*, float, float) {}
-};
-
 __global__ void __launch_bounds__(SITE_BLOCK)
 step_fp32dev_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P,
                     int* __restrict__ flag) {
-    const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
-    if (site >= Lx * Ly) return;
-    const int y = site / Lx;
-    const int x = site - y * Lx;
-    const long long plane = P.plane;
-
-    float d[NPOP];
-    Pull32<NPOP - 1>::run(src, d, x, y, Lx, Ly, P.y_periodic, plane);
-
-    const DevSums pre = dev_sums(d);
-    const Macro m = macro_of(pre, P.r, P.r2);
-    if (bad_positive64(m.rho) || bad_positive64(m.T)) atomicOr(flag, 1);
-
-    // shifted equilibrium (forcing), coefficients in FP32 from FP64 moments
-    const double uxs = m.ux + P.tgx;
-    const double uys = m.uy + P.tgy;
-    const double th = (m.T + P.dT_force) - 1.0;
-    const double u2 = uxs * uxs + uys * uys;
-    const float thf = (float)th, u2f = (float)u2;
-    const float a00m1 = (float)(u2 * fma(u2, 0.125, -0.5));  // (1 - u2/2 + u2^2/8) - 1
-    const float a20 = fmaf(u2f, -0.25f, 0.5f);
-    const float b10 = fmaf(u2f, -0.5f, 1.0f);
-    const float thu2 = thf * u2f, th2 = thf * thf;
-    const float omega = (float)P.omega;
-    float A0m1[NSHELL], A2[NSHELL], B1[NSHELL], Wd[NSHELL];
-#pragma unroll
-    for (int s = 0; s < NSHELL; ++s) {
-        A0m1[s] = fmaf((float)P.sh[s].gamma, th2,
-                       fmaf((float)P.sh[s].beta, thu2, fmaf((float)P.sh[s].alpha, thf, a00m1)));
-        A2[s] = fmaf((float)P.sh[s].delta, thf, a20);
-        B1[s] = fmaf((float)P.sh[s].eps, thf, b10);
-        Wd[s] = omega * (float)P.sh[s].w;
-    }
-    const float drho = (float)pre.s0;
-    const float omc = (float)P.omc;
-    d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
-    Collide32<NPAIR>::run(d, (float)(P.r * uxs), (float)(P.r * uys), A0m1, A2, B1, Wd, drho, omc);
-
-    // FP64 projection onto the exact post-collision moments (c units):
-    //   sum d' = rho - 1,  sum d' c = sum d c + rho g / r,
-    //   sum d' |c|^2 = sum d |c|^2 + rho (2 u.g + |g|^2) / r^2
-    const DevSums post = dev_sums(d);
-    const double gx = P.gx, gy = P.gy;
-    const double rinv = 1.0 / P.r;
-    const double R0 = pre.s0 - post.s0;
-    const double Rx = fma(m.rho * gx, rinv, pre.sx) - post.sx;
-    const double Ry = fma(m.rho * gy, rinv, pre.sy) - post.sy;
-    const double de = m.rho * (2.0 * (m.ux * gx + m.uy * gy) + gx * gx + gy * gy) * (rinv * rinv);
-    const double Re = (pre.se + de) - post.se;
-    // weighted least-norm correction: M diag(w) M^T lambda = R with
-    // M diag(w) M^T = [[1, 2/r^2], [2/r^2, 8/r^4]] (mass/energy block), 1/r^2 (momentum)
-    const double r2 = P.r2;
-    const float l0 = (float)(2.0 * R0 - 0.5 * r2 * Re);
-    const float le = (float)(r2 * (0.25 * r2 * Re - 0.5 * R0));
-    const float lx = (float)(r2 * Rx);
-    const float ly = (float)(r2 * Ry);
-
-    const long long dsto = (long long)(y + HALO) * Lx + x;
-#pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        const float corr = fmaf(le, (float)shell_c2(shell_of(i)),
-                                fmaf(lx, (float)cx_of(i), fmaf(ly, (float)cy_of(i), l0)));
-        __stcs(dst + poff(i, plane) + dsto, fmaf((float)shell_w(shell_of(i)), corr, d[i]));
-    }
-
-    if (!P.y_periodic) {
-        if (y < HALO) {
-            const long long o = (long long)(HALO - 1 - y) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i)
-                __stcs(dst + poff(i, plane) + o, (float)fma(m.rho, P.wall_bot[i], -shell_w(shell_of(i))));
-        }
-        if (y >= Ly - HALO) {
-            const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i)
-                __stcs(dst + poff(i, plane) + o, (float)fma(m.rho, P.wall_top[i], -shell_w(shell_of(i))));
-        }
-    }
+    if (site >= P.Lx * P.Ly) return;
+    const int y = site / P.Lx;
+    fp32dev_site(src, dst, P, site - y * P.Lx, y, flag);
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)

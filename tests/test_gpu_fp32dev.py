@@ -82,9 +82,9 @@ def test_fp32dev_propagate_bit_exact(L):
     f0 = w[:, None, None] + dev.astype(np.float64)
     lat.set_populations(f0)
     lat.propagate()
-    got = lat.get_populations() - w[:, None, None]
+    got = lat.get_populations()          # w + (double) deviation, one rounding
     for i in range(37):
-        want = np.roll(dev[i], shift=(int(cy[i]), int(cx[i])), axis=(0, 1)).astype(np.float64)
+        want = w[i] + np.roll(dev[i], shift=(int(cy[i]), int(cx[i])), axis=(0, 1)).astype(np.float64)
         assert np.array_equal(got[i], want)
 
 
