@@ -128,6 +128,32 @@ lb_status lb_steps_done(const lb_ctx* c, long long* n);
 /* Release the context and, if the library allocated it, its device memory. NULL-safe. */
 void lb_free(lb_ctx* c);
 
+/* ---- Allocation-free macroscopic fields (the paper has no counterpart to this call) ----
+ *
+ * For callers that cannot allocate device memory -- code whose device memory belongs to a host
+ * framework's own allocator, or that runs where cudaMalloc/cudaFree are not allowed -- this call
+ * computes rho, ux, uy, T of one caller-owned population copy without allocating anything: no
+ * cudaMalloc, cudaFree or allocating library routine. Its device staging area is a static array of
+ * 4 x LB_NOALLOC_MAX_SITES doubles (2 MiB) that every GPU which loads the library holds until the
+ * process exits.
+ *
+ *   p:  Lx, Ly, precision and stream are read (other fields ignored); p->stream is a cudaStream_t
+ *       or NULL (legacy default stream). Lx * Ly must not exceed LB_NOALLOC_MAX_SITES, else
+ *       LB_ERR_ARG with the reason in lb_last_error().
+ *   f:  device pointer to one population copy in the library layout: 37 planes of (Ly + 6) x Lx
+ *       elements (3 halo rows each side, x fastest), double for LB_FP64 or FP32 deviations f - w
+ *       for LB_FP32DEV. A context's workspace holds copy A at offset 0 and copy B right after it
+ *       (offset rounded up to 256 bytes); the current copy is A after an even number of steps.
+ *   rho, ux, uy, T: caller-owned host arrays [Ly][Lx] (any may be NULL).
+ * Synchronous (returns after the host arrays are written). The first call on a device looks up
+ * the static array's device address with that device current; make that first call before any
+ * stream capture. All calls share the one array and nothing in it needs clearing (every element
+ * read is written first by the same call), so calls whose GPU work overlaps (other host threads,
+ * other streams) race on it: serialise them. */
+#define LB_NOALLOC_MAX_SITES 65536
+lb_status lb_moments_noalloc(const lb_params* p, const void* f, double* rho, double* ux, double* uy,
+                             double* T);
+
 #ifdef __cplusplus
 }
 #endif

@@ -118,6 +118,14 @@ lb_status check_params(const lb_params* p) {
 
 }  // namespace
 
+namespace lbg {
+// Record the message lb_last_error() returns on this thread (used by the allocation-free entry
+// point, which lives in its own translation unit).
+void set_last_error(const char* msg) {
+    std::snprintf(g_last_error, sizeof g_last_error, "%s", msg);
+}
+}  // namespace lbg
+
 struct lb_ctx {
     lb_params p;
     StepParams sp;

@@ -72,6 +72,7 @@ def lib() -> C.CDLL:
         L.lb_free.argtypes = [vp]
         L.lb_free.restype = None
         L.lb_probe_fma.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp]
+        L.lb_moments_noalloc.argtypes = [C.POINTER(lb_params), vp, vp, vp, vp, vp]
         _lib = L
     return _lib
 
@@ -258,3 +259,14 @@ def probe_fma(kind: str, blocks: int, threads: int, iters: int, out, stream=None
     k = {"fp64": 0, "fp32": 1}[kind]
     sh = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
     check(lib().lb_probe_fma(k, sh, blocks, threads, iters, out.data_ptr()), "lb_probe_fma")
+
+
+def moments_noalloc(Lx: int, Ly: int, f_device_ptr: int, precision=LB_FP64, stream=None):
+    """(rho, ux, uy, T) host arrays of one caller-owned device population copy, computed without
+    any device allocation (lb_moments_noalloc; at most LB_NOALLOC_MAX_SITES = 65536 sites)."""
+    sh = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
+    p = make_params(Lx, Ly, 1.0, precision=precision, stream=sh)
+    out = tuple(np.empty((Ly, Lx), np.float64) for _ in range(4))
+    check(lib().lb_moments_noalloc(C.byref(p), f_device_ptr, *[o.ctypes.data for o in out]),
+          "lb_moments_noalloc")
+    return out
