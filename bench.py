@@ -36,14 +36,38 @@ if ROOT not in sys.path:
 
 LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
 NPOP = 37
-# FP64 arithmetic of the fused step per site, counted from the kernel's formulation
-# (moments 103, forcing 7, shell coefficients 99, rest population 3, pairs incl. r*u 318;
-# FMA = 2 flops).
-FP64_FLOP_PER_SITE = 530
+# FP64 work of the fused step per site in this kernel's formulation: 364 FP64 instructions
+# (191 FMA + 95 add + 78 mul; ncu's opcode counters on step_fp64_kernel agree exactly), i.e.
+# 555 flops with FMA = 2. The FP64 pipe issues one such instruction per lane-slot whatever its
+# kind, so the ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per SM x f_max
+# (the 1.25 TFLOP/s nominal FP64 rate counts an FMA as 2 flops).
+FP64_INST_PER_SITE = 364
+FP64_FLOP_PER_SITE = 555
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 SM_COUNT = 152
-FP64_FLOP_PER_CLK_SM = 4                 # 1.25 TFLOP/s nominal at 2070 MHz over 152 SMs
+FP64_INST_PER_CLK_SM = 2
+SM_MAX_MHZ = 2070.0
+# DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
+# 699.088 MB + 643.803 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# it was taken on (sha256 of step_fp64.cu and d2q37_gpu.cuh below); otherwise reported as null.
+TRAFFIC_FP64 = {"bytes_per_site": (699.088128e6 + 643.802880e6) / 2359296,
+                "sources": {"step_fp64.cu": "5597620c368f5a957c6bc1dd21017f6a2500b86e1444e616a61e45d4151aa438",
+                            "d2q37_gpu.cuh": "4d59013b2b1c32dfb60f905a86920bcb2013740b2740292f71e9236a9fbc8e92"}}
+
+
+def sources_match(table):
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1804_01918_gb300", "csrc")
+    for name, digest in table["sources"].items():
+        try:
+            with open(os.path.join(csrc, name), "rb") as fh:
+                if hashlib.sha256(fh.read()).hexdigest() != digest:
+                    return False
+        except OSError:
+            return False
+    return True
 
 
 def env_int(name, default):
@@ -232,9 +256,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--lattice", default=None,
                     help="LXxLY of a smaller case for profiling (default: the 2304x8192 workload)")
-    ap.add_argument("--precision", choices=["fp64", "fp32dev"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "fp32dev", "fp32split"], default="fp64")
     args = ap.parse_args()
     if args.lattice:
         global LX, LY
@@ -320,31 +345,44 @@ def main():
                "note": "one lb_init upload of rho,u,T (32 B/site) and one lb_moments download "
                        "(32 B/site) per K-step run, amortised per step"}
 
-    # ---- roofline of the fused FP64 step kernel ----
-    flops = FP64_FLOP_PER_SITE * sites
-    achieved_tf = flops / kernel_s / 1e12
-    peak_tf = SM_COUNT * FP64_FLOP_PER_CLK_SM * 2070e6 / 1e12
+    # ---- roofline of the step kernel ----
     hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
-    roofline = {"bound": "alu", "kernel": "step_fp64_kernel", "achieved": round(achieved_tf, 4),
-                "peak": round(peak_tf, 4), "unit": "TFLOP/s", "frac": round(achieved_tf / peak_tf, 4),
-                "traffic": None,
-                "peak_note": "FP64 CUDA-core peak derived from unit counts and clocks: 152 SMs x 4 "
-                             "flop/clk/SM x 2070 MHz (the 1.25 TFLOP/s nominal); FMA = 2 flops",
-                "probe_fp64_tflops": round(probe_tf, 4),
-                "algorithmic_flop_per_site": FP64_FLOP_PER_SITE,
-                "hbm_achieved_gbs": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9, 1),
-                "hbm_frac": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9 / hbm, 4),
-                "hbm_peak_gbs": hbm}
+    if args.precision == "fp64":
+        inst_rate = FP64_INST_PER_SITE * sites / kernel_s / 1e12
+        peak = SM_COUNT * FP64_INST_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        traffic = (round(TRAFFIC_FP64["bytes_per_site"] * sites) if sources_match(TRAFFIC_FP64)
+                   and (LX, LY) == (2304, 8192) else None)
+        roofline = {"bound": "alu", "kernel": "step_fp64_kernel", "achieved": round(inst_rate, 4),
+                    "peak": round(peak, 4), "unit": "T FP64-instructions/s",
+                    "frac": round(inst_rate / peak, 4), "traffic": traffic,
+                    "peak_note": "FP64 pipe: 152 SMs x 2 FP64 instructions (add, mul or FMA) per "
+                                 "clock per SM x 2070 MHz, the recipe's 1.25 TFLOP/s nominal with "
+                                 "FMA = 2 flops; measured by the library's FMA probe below",
+                    "algorithmic_fp64_inst_per_site": FP64_INST_PER_SITE,
+                    "achieved_tflops": round(FP64_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
+                    "peak_tflops": round(2 * peak, 4),
+                    "probe_fp64_tflops": round(probe_tf, 4),
+                    "traffic_note": "ncu dram bytes of a 1152x2048 launch scaled to 2304x8192 by sites",
+                    "hbm_achieved_gbs": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9, 1),
+                    "hbm_frac": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9 / hbm, 4)}
+    else:
+        gbs = FP32DEV_BYTES_PER_SITE * sites / kernel_s / 1e9
+        roofline = {"bound": "hbm", "kernel": f"step_{args.precision}_kernel", "achieved": round(gbs, 1),
+                    "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": None,
+                    "peak_note": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
     # ---- FP32-deviation form: MLUPS and L2 error against the FP64 path ----
     forms = None
     if not args.no_forms and rank == 0:
         forms = measure_forms(lb, torch, np, st, stream, value / world)
+        if not args.no_ensemble:
+            forms["ensemble"] = measure_ensemble(lb, torch, np, inputs, value / world)
 
     line = {"metric": "D2Q37 MLUPS, fused FP64 LB step (propagate+collide+walls)",
             "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic (seeded Rayleigh-Taylor fields)", "config": workload_config(world),
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps,
             "e2e": e2e,
@@ -363,43 +401,85 @@ def main():
 
 
 def measure_forms(lb, torch, np, st, stream, fp64_mlups):
-    """FP32-deviation form on the same workload: MLUPS (device-timed, 1000 steps) and relative L2
-    error of rho and T against the FP64 path at steps 100, 500, 1000 (the FP64 path is the
-    reference at this size; it matches the CPU oracle to 1e-12 in the tests)."""
+    """The FP32-deviation forms on the same workload: MLUPS (device-timed, 1000 steps), HBM
+    roofline fraction, and relative L2 error of rho and T against the FP64 path at steps 100, 500
+    and 1000 (the FP64 path is the reference at this size; it matches the CPU oracle to 1e-12 in
+    the tests, including sampled sites of this very workload)."""
     sites = LX * LY
+    hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
     out = {}
-    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32dev")
-    lat.step(10)
-    lat.sync()
+    for form in ("fp32dev", "fp32split"):
+        lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision=form)
+        lat.step(10)
+        lat.sync()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        lat.step(1000)
+        e1.record(stream)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1)
+        lat.sync()
+        lat.close()
+        mlups = sites * 1000 / (ms * 1e-3) / 1e6
+        gbs = FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9
+        out[form] = {"mlups": round(mlups, 1), "speedup_vs_fp64": round(mlups / fp64_mlups, 3),
+                     "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
+    # accuracy: all precisions from the same initial state, moments at 100/500/1000
+    lats = {form: lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision=form)
+            for form in ("fp64", "fp32dev", "fp32split")}
+    done = 0
+    errs = {"fp32dev": {}, "fp32split": {}}
+    for mark in (100, 500, 1000):
+        for lat in lats.values():
+            lat.step(mark - done)
+        done = mark
+        ra, _, _, Ta = lats["fp64"].moments()
+        for form in ("fp32dev", "fp32split"):
+            rb, _, _, Tb = lats[form].moments()
+            errs[form][str(mark)] = {"rho": float(np.linalg.norm(rb - ra) / np.linalg.norm(ra)),
+                                     "T": float(np.linalg.norm(Tb - Ta) / np.linalg.norm(Ta))}
+    for lat in lats.values():
+        lat.close()
+    for form in ("fp32dev", "fp32split"):
+        out[form]["rel_l2_vs_fp64"] = errs[form]
+    return out
+
+
+def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300):
+    """Batched ensemble: n seed-drawn Rayleigh-Taylor lattices (Lx uniform over multiples of 32 in
+    [128, 1024], Ly = 4 Lx, Atwood in [0.05, 0.5], tau in [0.6, 1.2]), FP32 storage (exact-split
+    accumulation), autotuned tile shape, 100-step CUDA graphs; MLUPS = sum of sites x steps / s."""
+    descs = inputs.ensemble_members(n, seed=seed)
+    specs = []
+    for d in descs:
+        st = inputs.rayleigh_taylor(d["Lx"], d["Ly"], R=d["R"], seed=d["seed"])
+        specs.append({"Lx": d["Lx"], "Ly": d["Ly"], "tau": d["tau"], "gy": st.gy,
+                      "T_top": st.T_top, "T_bottom": st.T_bottom, "rho": st.rho, "ux": st.ux,
+                      "uy": st.uy, "T": st.T})
+    stream = torch.cuda.Stream()
+    ens = lb.Ensemble(specs, precision="fp32split", graph_steps=100, stream=stream)
+    specs = None
+    tx, ty, tune_mlups = ens.autotune(steps=3)
+    ens.step(100)
+    ens.sync()
+    sites = ens.info()["sites"]
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    lat.step(1000)
+    ens.step(steps)
     e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
-    lat.sync()
-    lat.close()
-    mlups = sites * 1000 / (ms * 1e-3) / 1e6
+    ens.sync()
+    info = ens.info()
+    ens.close()
+    mlups = sites * steps / (ms * 1e-3) / 1e6
     hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
-    out["fp32dev"] = {"mlups": round(mlups, 1), "speedup_vs_fp64": round(mlups / fp64_mlups, 3),
-                      "hbm_gbs": round(FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9, 1),
-                      "hbm_frac": round(FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9 / hbm, 4)}
-    # accuracy: both precisions from the same initial state, moments at 100/500/1000
-    a = lb.Lattice.from_fields(st, tau=TAU, stream=stream)
-    b = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32dev")
-    done, errs = 0, {}
-    for mark in (100, 500, 1000):
-        a.step(mark - done)
-        b.step(mark - done)
-        done = mark
-        ra, _, _, Ta = a.moments()
-        rb, _, _, Tb = b.moments()
-        errs[str(mark)] = {"rho": float(np.linalg.norm(rb - ra) / np.linalg.norm(ra)),
-                           "T": float(np.linalg.norm(Tb - Ta) / np.linalg.norm(Ta))}
-    a.close()
-    b.close()
-    out["fp32dev"]["rel_l2_vs_fp64"] = errs
-    return out
+    gbs = FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9
+    return {"members": n, "sites": sites, "steps": steps, "mlups": round(mlups, 1),
+            "speedup_vs_fp64": round(mlups / fp64_mlups, 3), "hbm_gbs": round(gbs, 1),
+            "hbm_frac": round(gbs / hbm, 4), "tile": [tx, ty], "work_items": info["items"],
+            "autotune_best_mlups": round(tune_mlups, 1), "graph_steps": 100,
+            "precision": "fp32split"}
 
 
 if __name__ == "__main__":

@@ -1,0 +1,516 @@
+// ensemble.cu -- batched ensemble of independent D2Q37 lattices in one persistent launch per step.
+//
+// Device data: every member's two FP32-deviation population copies (same layout as a single
+// lattice), a member table (kernel parameters + buffer pointers), a global list of work items
+// (member, x0, y0) covering all members with tile_x x tile_y tiles, a host-exchange staging area
+// sized for the largest member, and a status word.
+//
+// The step kernel is persistent: its grid is the number of co-resident blocks (SMs x blocks per
+// SM), and block b handles work items b, b + grid, b + 2 grid, ... For each item the block copies
+// the member's parameters to shared memory once and its threads run the same per-site update as
+// the single-lattice FP32 kernels. Items are ordered member by member, row band by row band, so
+// the blocks in flight work on neighbouring tiles and the pull's row offsets (up to 3 rows) hit
+// in L2.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lb_ensemble.h"
+#include "d2q37_gpu.cuh"
+#include "kernels.cuh"
+#include "site_fp32dev.cuh"
+
+using namespace lbg;
+
+// Named namespace: nvcc's host stubs for templated kernels cannot name types declared in a second
+// anonymous namespace of the same translation unit.
+namespace lbg {
+namespace ens {
+
+constexpr int ENS_BLOCK = 128;
+constexpr size_t ALIGN = 256;
+
+struct MemberDesc {
+    StepParams P;
+    float* buf[2];
+};
+
+inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
+
+template <bool kSplit>
+__global__ void __launch_bounds__(ENS_BLOCK)
+ensemble_step_kernel(const MemberDesc* __restrict__ members, const int4* __restrict__ items,
+                     int nitems, int tx_log2, int tile_sites, int parity, int* __restrict__ flag) {
+    __shared__ __align__(16) StepParams sP;
+    __shared__ const float* s_src;
+    __shared__ float* s_dst;
+    constexpr int NWORDS = (int)(sizeof(StepParams) / sizeof(unsigned long long));
+    for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
+        const int4 it = items[t];
+        __syncthreads();  // the previous item is finished with sP
+        const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&members[it.x].P);
+        unsigned long long* s = reinterpret_cast<unsigned long long*>(&sP);
+        for (int k = threadIdx.x; k < NWORDS; k += ENS_BLOCK) s[k] = g[k];
+        if (threadIdx.x == 0) {
+            s_src = members[it.x].buf[parity];
+            s_dst = members[it.x].buf[parity ^ 1];
+        }
+        __syncthreads();
+        const int xmask = (1 << tx_log2) - 1;
+        for (int k = threadIdx.x; k < tile_sites; k += ENS_BLOCK) {
+            const int x = it.y + (k & xmask);
+            const int y = it.z + (k >> tx_log2);
+            if (x < sP.Lx && y < sP.Ly) {
+                if (kSplit)
+                    fp32split_site(s_src, s_dst, sP, x, y, flag);
+                else
+                    fp32dev_site(s_src, s_dst, sP, x, y, flag);
+            }
+        }
+    }
+}
+
+static_assert(sizeof(StepParams) % sizeof(unsigned long long) == 0, "StepParams is copied in words");
+
+}  // namespace ens
+}  // namespace lbg
+
+using namespace lbg::ens;
+
+namespace {
+
+int log2_exact(int v) {
+    int k = 0;
+    while ((1 << k) < v) ++k;
+    return (1 << k) == v ? k : -1;
+}
+
+struct Candidate {
+    int tx, ty;
+};
+
+std::vector<Candidate> candidates() {
+    std::vector<Candidate> out;
+    for (int tx : {32, 64, 128, 256})
+        for (int ty : {1, 2, 4, 8, 16})
+            if (tx * ty >= 128 && tx * ty <= 2048) out.push_back({tx, ty});
+    return out;
+}
+
+long long count_items(const std::vector<lb_params>& m, int tx, int ty) {
+    long long n = 0;
+    for (const auto& p : m) n += (long long)((p.Lx + tx - 1) / tx) * ((p.Ly + ty - 1) / ty);
+    return n;
+}
+
+lb_status fail(cudaError_t e, const char* where) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "%s: %s", where, cudaGetErrorString(e));
+    set_last_error(msg);
+    return LB_ERR_CUDA;
+}
+
+#define ENS_CUDA(call)                                       \
+    do {                                                     \
+        cudaError_t e_ = (call);                             \
+        if (e_ != cudaSuccess) return fail(e_, #call);       \
+    } while (0)
+
+}  // namespace
+
+struct lb_ensemble {
+    std::vector<lb_params> params;
+    std::vector<StepParams> sp;
+    std::vector<float*> buf0, buf1;
+    std::vector<size_t> sites;
+    int precision = LB_FP32SPLIT;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    char* ws = nullptr;
+    bool own_ws = false;
+    MemberDesc* d_members = nullptr;
+    int4* d_items = nullptr;
+    long long max_items = 0;
+    int nitems = 0;
+    int tile_x = 64, tile_y = 4;
+    double* stage = nullptr;
+    int* flag = nullptr;
+    int cur = 0;
+    int graph_steps = 100;
+    cudaGraphExec_t graph[2] = {nullptr, nullptr};
+    bool graph_failed = false;
+    int grid = 0;
+    long long total_sites = 0;
+};
+
+namespace {
+
+struct EnsLayout {
+    std::vector<size_t> off_buf;  // per member, copy A; copy B follows at + buf_bytes[k]
+    std::vector<size_t> buf_bytes;
+    size_t off_members, off_items, off_stage, off_flag, total;
+    long long max_items;
+};
+
+EnsLayout ens_layout(const std::vector<lb_params>& m) {
+    EnsLayout L;
+    size_t off = 0;
+    size_t max_sites = 0;
+    for (const auto& p : m) {
+        const size_t plane = (size_t)p.Lx * ((size_t)p.Ly + 2 * HALO);
+        const size_t b = align_up(plane * NPOP * sizeof(float));
+        L.off_buf.push_back(off);
+        L.buf_bytes.push_back(b);
+        off += 2 * b;
+        max_sites = std::max(max_sites, (size_t)p.Lx * p.Ly);
+    }
+    L.max_items = 0;
+    for (const auto& c : candidates()) L.max_items = std::max(L.max_items, count_items(m, c.tx, c.ty));
+    L.off_members = off;
+    off += align_up(m.size() * sizeof(MemberDesc));
+    L.off_items = off;
+    off += align_up((size_t)L.max_items * sizeof(int4));
+    L.off_stage = off;
+    off += align_up(4 * max_sites * sizeof(double));
+    L.off_flag = off;
+    off += ALIGN;
+    L.total = off;
+    return L;
+}
+
+lb_status check_members(int n, const lb_params* m) {
+    if (n < 1 || !m) return LB_ERR_ARG;
+    for (int k = 0; k < n; ++k) {
+        const lb_params& p = m[k];
+        if (p.Lx < 4 || p.Ly < 4 || (long long)p.Lx * ((long long)p.Ly + 2 * HALO) >= (1ll << 31) - 1)
+            return LB_ERR_ARG;
+        if (!(p.tau > 0.5) || !(p.T_top > 0.0) || !(p.T_bottom > 0.0)) return LB_ERR_ARG;
+    }
+    return LB_OK;
+}
+
+int opts_precision(const lb_ensemble_opts* o) {
+    if (!o || o->precision == 0) return LB_FP32SPLIT;
+    return o->precision;
+}
+
+lb_status upload_items(lb_ensemble* e, int tx, int ty) {
+    std::vector<int4> items;
+    items.reserve((size_t)count_items(e->params, tx, ty));
+    for (int k = 0; k < (int)e->params.size(); ++k) {
+        const lb_params& p = e->params[k];
+        for (int y0 = 0; y0 < p.Ly; y0 += ty)
+            for (int x0 = 0; x0 < p.Lx; x0 += tx) items.push_back(make_int4(k, x0, y0, 0));
+    }
+    if ((long long)items.size() > e->max_items) return LB_ERR_STATE;
+    ENS_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(int4),
+                             cudaMemcpyHostToDevice, e->stream));
+    ENS_CUDA(cudaStreamSynchronize(e->stream));
+    e->nitems = (int)items.size();
+    e->tile_x = tx;
+    e->tile_y = ty;
+    for (int k = 0; k < 2; ++k)
+        if (e->graph[k]) {
+            cudaGraphExecDestroy(e->graph[k]);
+            e->graph[k] = nullptr;
+        }
+    e->graph_failed = false;
+    return LB_OK;
+}
+
+cudaError_t launch_ensemble(lb_ensemble* e, int parity) {
+    const int txl = log2_exact(e->tile_x);
+    if (e->precision == LB_FP32SPLIT)
+        ensemble_step_kernel<true><<<e->grid, ENS_BLOCK, 0, e->stream>>>(
+            e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
+    else
+        ensemble_step_kernel<false><<<e->grid, ENS_BLOCK, 0, e->stream>>>(
+            e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
+    return cudaGetLastError();
+}
+
+bool capture(lb_ensemble* e, int par) {
+    cudaStreamCaptureStatus st;
+    if (cudaStreamIsCapturing(e->stream, &st) != cudaSuccess || st != cudaStreamCaptureStatusNone)
+        return false;
+    if (cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    bool ok = true;
+    for (int k = 0; k < e->graph_steps && ok; ++k) ok = launch_ensemble(e, par ^ (k & 1)) == cudaSuccess;
+    cudaGraph_t g = nullptr;
+    const cudaError_t ee = cudaStreamEndCapture(e->stream, &g);
+    if (!ok || ee != cudaSuccess || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return false;
+    }
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t ie = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (ie != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    e->graph[par] = ex;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_ensemble_workspace_bytes(int n, const lb_params* members, const lb_ensemble_opts* o,
+                                      size_t* bytes) {
+    (void)o;
+    if (!bytes || check_members(n, members) != LB_OK) return LB_ERR_ARG;
+    *bytes = ens_layout(std::vector<lb_params>(members, members + n)).total;
+    return LB_OK;
+}
+
+void lb_ensemble_free(lb_ensemble* e) {
+    if (!e) return;
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    for (int k = 0; k < 2; ++k)
+        if (e->graph[k]) cudaGraphExecDestroy(e->graph[k]);
+    if (e->own_ws && e->ws) cudaFree(e->ws);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+    delete e;
+}
+
+lb_status lb_ensemble_init(int n, const lb_params* members, const double* const* rho,
+                           const double* const* ux, const double* const* uy,
+                           const double* const* T, const lb_ensemble_opts* opts,
+                           lb_ensemble** out) {
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    if (check_members(n, members) != LB_OK || !rho || !ux || !uy || !T) return LB_ERR_ARG;
+    for (int k = 0; k < n; ++k)
+        if (!rho[k] || !ux[k] || !uy[k] || !T[k]) return LB_ERR_ARG;
+    const int prec = opts_precision(opts);
+    if (prec != LB_FP32SPLIT && prec != LB_FP32DEV) return LB_ERR_ARG;
+    int gsteps = opts && opts->graph_steps ? opts->graph_steps : 100;
+    if (gsteps < 2 || (gsteps & 1)) return LB_ERR_ARG;
+    int tx = opts && opts->tile_x ? opts->tile_x : 64;
+    int ty = opts && opts->tile_y ? opts->tile_y : 4;
+    if (log2_exact(tx) < 0 || ty < 1 || tx * ty < 32 || tx * ty > 4096) return LB_ERR_ARG;
+
+    std::vector<lb_params> m(members, members + n);
+    for (auto& p : m) p.precision = prec;
+    const EnsLayout L = ens_layout(m);
+    if (count_items(m, tx, ty) > L.max_items) return LB_ERR_ARG;
+    if (opts && opts->workspace &&
+        (opts->workspace_bytes < L.total || ((uintptr_t)opts->workspace % ALIGN) != 0))
+        return LB_ERR_ARG;
+
+    lb_ensemble* e = new (std::nothrow) lb_ensemble();
+    if (!e) return LB_ERR_ALLOC;
+    e->params = m;
+    e->precision = prec;
+    e->graph_steps = gsteps;
+    e->max_items = L.max_items;
+    if (opts && opts->stream) {
+        e->stream = (cudaStream_t)opts->stream;
+    } else {
+        cudaError_t ce = cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking);
+        if (ce != cudaSuccess) {
+            delete e;
+            return fail(ce, "cudaStreamCreateWithFlags");
+        }
+        e->own_stream = true;
+    }
+    if (opts && opts->workspace) {
+        e->ws = (char*)opts->workspace;
+    } else {
+        cudaError_t ce = cudaMalloc((void**)&e->ws, L.total);
+        if (ce != cudaSuccess) {
+            cudaGetLastError();
+            e->ws = nullptr;
+            lb_ensemble_free(e);
+            char msg[128];
+            std::snprintf(msg, sizeof msg, "cudaMalloc(%zu) for the ensemble failed", L.total);
+            set_last_error(msg);
+            return LB_ERR_ALLOC;
+        }
+        e->own_ws = true;
+    }
+    e->d_members = (MemberDesc*)(e->ws + L.off_members);
+    e->d_items = (int4*)(e->ws + L.off_items);
+    e->stage = (double*)(e->ws + L.off_stage);
+    e->flag = (int*)(e->ws + L.off_flag);
+
+    std::vector<MemberDesc> hd(n);
+    for (int k = 0; k < n; ++k) {
+        StepParams sp;
+        fill_step_params(m[k], sp);
+        e->sp.push_back(sp);
+        e->buf0.push_back((float*)(e->ws + L.off_buf[k]));
+        e->buf1.push_back((float*)(e->ws + L.off_buf[k] + L.buf_bytes[k]));
+        e->sites.push_back((size_t)m[k].Lx * m[k].Ly);
+        e->total_sites += (long long)m[k].Lx * m[k].Ly;
+        hd[k].P = sp;
+        hd[k].buf[0] = e->buf0[k];
+        hd[k].buf[1] = e->buf1[k];
+    }
+    lb_status st = LB_OK;
+    do {
+        cudaError_t ce = cudaMemcpyAsync(e->d_members, hd.data(), n * sizeof(MemberDesc),
+                                         cudaMemcpyHostToDevice, e->stream);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(e->flag, 0, sizeof(int), e->stream);
+        for (int k = 0; k < n && ce == cudaSuccess; ++k) {
+            const size_t ns = e->sites[k];
+            const double* src[4] = {rho[k], ux[k], uy[k], T[k]};
+            for (int f = 0; f < 4 && ce == cudaSuccess; ++f)
+                ce = cudaMemcpyAsync(e->stage + f * ns, src[f], ns * sizeof(double),
+                                     cudaMemcpyHostToDevice, e->stream);
+            if (ce == cudaSuccess)
+                ce = launch_init_fp32dev(e->stage, e->stage + ns, e->stage + 2 * ns, e->stage + 3 * ns,
+                                         e->buf0[k], e->sp[k], e->stream);
+            if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);  // staging is reused
+        }
+        if (ce != cudaSuccess) {
+            st = fail(ce, "ensemble initialisation");
+            break;
+        }
+        int per_sm = 0, dev = 0, sms = 0;
+        ce = cudaGetDevice(&dev);
+        if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (ce == cudaSuccess)
+            ce = prec == LB_FP32SPLIT
+                     ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_step_kernel<true>,
+                                                                     ENS_BLOCK, 0)
+                     : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ensemble_step_kernel<false>,
+                                                                     ENS_BLOCK, 0);
+        if (ce != cudaSuccess) {
+            st = fail(ce, "occupancy query");
+            break;
+        }
+        e->grid = std::max(1, per_sm) * std::max(1, sms);
+        st = upload_items(e, tx, ty);
+    } while (0);
+    if (st != LB_OK) {
+        lb_ensemble_free(e);
+        return st;
+    }
+    *out = e;
+    return LB_OK;
+}
+
+lb_status lb_ensemble_step(lb_ensemble* e, int n) {
+    if (!e || n < 0) return LB_ERR_ARG;
+    while (n >= e->graph_steps && !e->graph_failed) {
+        if (!e->graph[e->cur] && !capture(e, e->cur)) {
+            e->graph_failed = true;
+            break;
+        }
+        ENS_CUDA(cudaGraphLaunch(e->graph[e->cur], e->stream));
+        n -= e->graph_steps;  // even: parity unchanged
+    }
+    for (; n > 0; --n) {
+        ENS_CUDA(launch_ensemble(e, e->cur));
+        e->cur ^= 1;
+    }
+    return LB_OK;
+}
+
+lb_status lb_ensemble_sync(lb_ensemble* e) {
+    if (!e) return LB_ERR_ARG;
+    ENS_CUDA(cudaStreamSynchronize(e->stream));
+    int h = 0;
+    ENS_CUDA(cudaMemcpyAsync(&h, e->flag, sizeof(int), cudaMemcpyDeviceToHost, e->stream));
+    ENS_CUDA(cudaStreamSynchronize(e->stream));
+    if (h) {
+        ENS_CUDA(cudaMemsetAsync(e->flag, 0, sizeof(int), e->stream));
+        ENS_CUDA(cudaStreamSynchronize(e->stream));
+        return (h & 2) ? LB_ERR_RANGE : LB_ERR_NONFINITE;
+    }
+    return LB_OK;
+}
+
+lb_status lb_ensemble_autotune(lb_ensemble* e, int steps, int* tile_x, int* tile_y, double* mlups) {
+    if (!e || steps < 1) return LB_ERR_ARG;
+    cudaEvent_t a, b;
+    ENS_CUDA(cudaEventCreate(&a));
+    ENS_CUDA(cudaEventCreate(&b));
+    double best = -1.0;
+    Candidate bestc{e->tile_x, e->tile_y};
+    lb_status st = LB_OK;
+    for (const auto& c : candidates()) {
+        st = upload_items(e, c.tx, c.ty);
+        if (st != LB_OK) break;
+        // trial launches read the current copy and write the other one without swapping
+        cudaError_t ce = launch_ensemble(e, e->cur);
+        if (ce == cudaSuccess) ce = cudaEventRecord(a, e->stream);
+        for (int k = 0; k < steps && ce == cudaSuccess; ++k) ce = launch_ensemble(e, e->cur);
+        if (ce == cudaSuccess) ce = cudaEventRecord(b, e->stream);
+        if (ce == cudaSuccess) ce = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (ce == cudaSuccess) ce = cudaEventElapsedTime(&ms, a, b);
+        if (ce != cudaSuccess) {
+            st = fail(ce, "autotune trial");
+            break;
+        }
+        const double rate = (double)e->total_sites * steps / (ms * 1e-3) / 1e6;
+        if (rate > best) {
+            best = rate;
+            bestc = c;
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st != LB_OK) return st;
+    st = upload_items(e, bestc.tx, bestc.ty);
+    if (st != LB_OK) return st;
+    if (tile_x) *tile_x = bestc.tx;
+    if (tile_y) *tile_y = bestc.ty;
+    if (mlups) *mlups = best;
+    return LB_OK;
+}
+
+lb_status lb_ensemble_info(const lb_ensemble* e, int* tile_x, int* tile_y, int* ntiles,
+                           long long* sites) {
+    if (!e) return LB_ERR_ARG;
+    if (tile_x) *tile_x = e->tile_x;
+    if (tile_y) *tile_y = e->tile_y;
+    if (ntiles) *ntiles = e->nitems;
+    if (sites) *sites = e->total_sites;
+    return LB_OK;
+}
+
+lb_status lb_ensemble_moments(lb_ensemble* e, int k, double* rho, double* ux, double* uy,
+                              double* T) {
+    if (!e || k < 0 || k >= (int)e->params.size()) return LB_ERR_ARG;
+    const size_t n = e->sites[k];
+    const float* cur = e->cur ? e->buf1[k] : e->buf0[k];
+    ENS_CUDA(launch_moments_fp32dev(cur, e->sp[k], e->stage, e->stage + n, e->stage + 2 * n,
+                                    e->stage + 3 * n, e->stream));
+    double* dst[4] = {rho, ux, uy, T};
+    for (int f = 0; f < 4; ++f)
+        if (dst[f])
+            ENS_CUDA(cudaMemcpyAsync(dst[f], e->stage + f * n, n * sizeof(double),
+                                     cudaMemcpyDeviceToHost, e->stream));
+    ENS_CUDA(cudaStreamSynchronize(e->stream));
+    return LB_OK;
+}
+
+lb_status lb_ensemble_get_populations(lb_ensemble* e, int k, double* f) {
+    if (!e || !f || k < 0 || k >= (int)e->params.size()) return LB_ERR_ARG;
+    const size_t n = e->sites[k];
+    const float* cur = e->cur ? e->buf1[k] : e->buf0[k];
+    const size_t skip = (size_t)HALO * e->params[k].Lx;
+    for (int i = 0; i < NPOP; ++i) {
+        ENS_CUDA(launch_plane_from_dev32(cur + (size_t)i * e->sp[k].plane + skip, e->stage,
+                                         shell_w(shell_of(i)), (long long)n, e->stream));
+        ENS_CUDA(cudaMemcpyAsync(f + i * n, e->stage, n * sizeof(double), cudaMemcpyDeviceToHost,
+                                 e->stream));
+        ENS_CUDA(cudaStreamSynchronize(e->stream));
+    }
+    return LB_OK;
+}
+
+}  // extern "C"

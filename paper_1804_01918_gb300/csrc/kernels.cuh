@@ -5,7 +5,14 @@
 
 #include "d2q37_gpu.cuh"
 
+#include "lb_d2q37.h"
+
 namespace lbg {
+
+// ---- host helpers (lb_capi.cu) ----
+double thermal_scale();                                   // r = 1 / sqrt(sum w c_x^2)
+void fill_step_params(const lb_params& p, StepParams& sp);  // per-lattice kernel parameters
+void set_last_error(const char* msg);                     // message returned by lb_last_error()
 
 // Threads per block of the site-parallel kernels.
 constexpr int SITE_BLOCK = 128;
@@ -24,6 +31,9 @@ cudaError_t launch_halo_fp64(double* f, const StepParams& P, cudaStream_t s);
 // ---- FP32 deviation populations (step_fp32dev.cu) ----
 cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& P, int* flag,
                                 cudaStream_t s);
+// same storage, exact-split FP32 accumulation instead of FP64 (site_fp32dev.cuh)
+cudaError_t launch_step_fp32split(const float* src, float* dst, const StepParams& P, int* flag,
+                                  cudaStream_t s);
 cudaError_t launch_propagate_fp32dev(const float* src, float* dst, const StepParams& P,
                                      cudaStream_t s);
 cudaError_t launch_init_fp32dev(const double* rho, const double* ux, const double* uy,

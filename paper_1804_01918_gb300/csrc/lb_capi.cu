@@ -50,7 +50,7 @@ bool valid_sizes(int Lx, int Ly) {
 
 Layout layout_of(int Lx, int Ly, int precision) {
     Layout L;
-    L.esize = precision == LB_FP32DEV ? sizeof(float) : sizeof(double);
+    L.esize = precision == LB_FP64 ? sizeof(double) : sizeof(float);
     L.plane_elems = (size_t)Lx * ((size_t)Ly + 2 * HALO);
     L.buf_bytes = align_up(L.plane_elems * NPOP * L.esize);
     L.stage_bytes = align_up((size_t)4 * Lx * Ly * sizeof(double));
@@ -63,6 +63,22 @@ Layout layout_of(int Lx, int Ly, int precision) {
     return L;
 }
 
+lb_status check_params(const lb_params* p) {
+    if (!p) return LB_ERR_ARG;
+    if (!valid_sizes(p->Lx, p->Ly)) return LB_ERR_ARG;
+    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LB_ERR_ARG;
+    if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return LB_ERR_ARG;
+    if (!(p->T_top > 0.0) || !(p->T_bottom > 0.0) || !std::isfinite(p->T_top) ||
+        !std::isfinite(p->T_bottom))
+        return LB_ERR_ARG;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV && p->precision != LB_FP32SPLIT)
+        return LB_ERR_ARG;
+    return LB_OK;
+}
+
+}  // namespace
+
+namespace lbg {
 // r = 1 / sqrt(sum_i w_i c_ix^2): xi = r c puts the reference temperature at 1.
 double thermal_scale() {
     double m2 = 0.0;
@@ -104,21 +120,6 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
     }
 }
 
-lb_status check_params(const lb_params* p) {
-    if (!p) return LB_ERR_ARG;
-    if (!valid_sizes(p->Lx, p->Ly)) return LB_ERR_ARG;
-    if (!(p->tau > 0.5) || !std::isfinite(p->tau)) return LB_ERR_ARG;
-    if (!std::isfinite(p->gx) || !std::isfinite(p->gy)) return LB_ERR_ARG;
-    if (!(p->T_top > 0.0) || !(p->T_bottom > 0.0) || !std::isfinite(p->T_top) ||
-        !std::isfinite(p->T_bottom))
-        return LB_ERR_ARG;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV) return LB_ERR_ARG;
-    return LB_OK;
-}
-
-}  // namespace
-
-namespace lbg {
 // Record the message lb_last_error() returns on this thread (used by the allocation-free entry
 // point, which lives in its own translation unit).
 void set_last_error(const char* msg) {
@@ -150,6 +151,9 @@ lb_status launch_one_step(lb_ctx* c) {
     if (c->p.precision == LB_FP64)
         e = launch_step_fp64((const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1], c->sp,
                              c->flag, c->stream);
+    else if (c->p.precision == LB_FP32SPLIT)
+        e = launch_step_fp32split((const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1], c->sp,
+                                  c->flag, c->stream);
     else
         e = launch_step_fp32dev((const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1], c->sp,
                                 c->flag, c->stream);
@@ -200,7 +204,7 @@ lb_status read_flag(lb_ctx* c) {
     if (h) {
         LB_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->stream));
         LB_CUDA(cudaStreamSynchronize(c->stream));
-        return LB_ERR_NONFINITE;
+        return (h & 2) ? LB_ERR_RANGE : LB_ERR_NONFINITE;
     }
     return LB_OK;
 }
@@ -236,6 +240,7 @@ const char* lb_status_str(lb_status s) {
         case LB_ERR_CUDA: return "CUDA error";
         case LB_ERR_NONFINITE: return "non-finite or non-positive density/temperature";
         case LB_ERR_STATE: return "invalid state";
+        case LB_ERR_RANGE: return "population deviation outside the exact-split range";
     }
     return "unknown status";
 }
@@ -254,7 +259,8 @@ lb_status lb_velocity_set(int* cx, int* cy, double* w, double* r) {
 
 lb_status lb_workspace_bytes(const lb_params* p, size_t* bytes) {
     if (!p || !bytes || !valid_sizes(p->Lx, p->Ly)) return LB_ERR_ARG;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV) return LB_ERR_ARG;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV && p->precision != LB_FP32SPLIT)
+        return LB_ERR_ARG;
     *bytes = layout_of(p->Lx, p->Ly, p->precision).total;
     return LB_OK;
 }

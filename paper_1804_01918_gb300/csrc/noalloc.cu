@@ -62,7 +62,8 @@ extern "C" lb_status lb_moments_noalloc(const lb_params* p, const void* f, doubl
                                         double* uy, double* T) {
     if (!p || !f) return LB_ERR_ARG;
     if (p->Lx < 4 || p->Ly < 4) return LB_ERR_ARG;
-    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV) return LB_ERR_ARG;
+    if (p->precision != LB_FP64 && p->precision != LB_FP32DEV && p->precision != LB_FP32SPLIT)
+        return LB_ERR_ARG;
     const long long n = (long long)p->Lx * p->Ly;
     if (n > LB_NOALLOC_MAX_SITES) {
         char msg[160];

@@ -223,3 +223,176 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
 }
 
 }  // namespace lbg
+
+namespace lbg {
+namespace split32 {
+
+// Exact three-way split of an FP32 value at fixed quanta (the ExtractScalar error-free
+// transformation of Rump, Ogita and Oishi, "Accurate floating-point summation part I", SIAM J.
+// Sci. Comput. 31, 2008): for |d| < 256,
+//   hi  = (d + B1) - B1, a multiple of 2^-14            (B1 = 1.5 * 2^9,  ulp(B1) = 2^-14)
+//   mid = (r + B2) - B2, r = d - hi, a multiple of 2^-27 (B2 = 1.5 * 2^-4, ulp(B2) = 2^-27)
+//   lo  = r - mid, |lo| <= 2^-28
+// and d = hi + mid + lo exactly. Sums of up to 216 |c|^2-weighted terms of hi (mid) parts stay
+// below 2^24 quanta while |d| < 4 -- so they are exact in FP32 -- and only the lo sums round
+// (error <= ~2e-12 absolute). The same quanta serve the pre- and post-collision sums, so their
+// differences (the projection residuals) are exact in the hi and mid parts as well.
+constexpr float B1 = 768.0f;
+constexpr float B2 = 0.09375f;
+constexpr float RANGE = 4.0f;  // |d| must stay below this for the hi sums to be exact
+
+struct Part {
+    float s0, sx, sy, se;  // sum d, sum c_x d, sum c_y d, sum |c|^2 d (in lattice units)
+};
+
+__device__ __forceinline__ Part combine(const float* bx, const float* by) {
+    const float px1 = bx[4] + bx[2], px2 = bx[5] + bx[1], px3 = bx[6] + bx[0];
+    const float py1 = by[4] + by[2], py2 = by[5] + by[1], py3 = by[6] + by[0];
+    Part p;
+    p.s0 = ((bx[3] + px1) + px2) + px3;
+    p.sx = fmaf(3.0f, bx[6] - bx[0], fmaf(2.0f, bx[5] - bx[1], bx[4] - bx[2]));
+    p.sy = fmaf(3.0f, by[6] - by[0], fmaf(2.0f, by[5] - by[1], by[4] - by[2]));
+    p.se = fmaf(9.0f, px3, fmaf(4.0f, px2, px1)) + fmaf(9.0f, py3, fmaf(4.0f, py2, py1));
+    return p;
+}
+
+// The four moment sums of d[37] as exact hi and mid parts plus a rounded lo part.
+__device__ __forceinline__ void split_sums(const float* d, Part& hi, Part& mid, Part& lo) {
+    float hx[7], hy[7], mx[7], my[7], lx[7], ly[7];
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+        hx[k] = hy[k] = mx[k] = my[k] = lx[k] = ly[k] = 0.0f;
+    }
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        const float h = __fsub_rn(__fadd_rn(d[i], B1), B1);
+        const float r = __fsub_rn(d[i], h);
+        const float m = __fsub_rn(__fadd_rn(r, B2), B2);
+        const float l = __fsub_rn(r, m);
+        const int ix = cx_of(i) + 3, iy = cy_of(i) + 3;
+        hx[ix] += h;
+        hy[iy] += h;
+        mx[ix] += m;
+        my[iy] += m;
+        lx[ix] += l;
+        ly[iy] += l;
+    }
+    hi = combine(hx, hy);
+    mid = combine(mx, my);
+    lo = combine(lx, ly);
+}
+
+template <int I>
+struct MaxAbs {
+    __device__ __forceinline__ static float run(const float* d) {
+        return fmaxf(MaxAbs<I - 1>::run(d), fabsf(d[I]));
+    }
+};
+template <>
+struct MaxAbs<0> {
+    __device__ __forceinline__ static float run(const float* d) { return fabsf(d[0]); }
+};
+
+__device__ __forceinline__ bool bad_positive32(float v) {
+    const unsigned b = __float_as_uint(v);
+    return (b - 1u) >= 0x7F7FFFFFu;
+}
+
+}  // namespace split32
+
+// One fused FP32-deviation step of site (x, y) with exact-split FP32 moment accumulation and an
+// FP32 projection residual (no FP64 arithmetic except on the six wall rows). Flag bits: 1 =
+// non-finite or non-positive density/temperature, 2 = a deviation outside the exact-split range.
+__device__ __forceinline__ void fp32split_site(const float* __restrict__ src, float* __restrict__ dst,
+                                               const StepParams& P, int x, int y,
+                                               int* __restrict__ flag) {
+    using namespace split32;
+    const int Lx = P.Lx, Ly = P.Ly;
+    const long long plane = P.plane;
+
+    float d[NPOP];
+    Pull32<NPOP - 1>::run(src, d, x, y, Lx, Ly, P.y_periodic, plane);
+    const float dmax = MaxAbs<NPOP - 1>::run(d);
+
+    Part h0, m0, l0;
+    split_sums(d, h0, m0, l0);
+    const float s0 = (h0.s0 + m0.s0) + l0.s0;
+    const float sx = (h0.sx + m0.sx) + l0.sx;
+    const float sy = (h0.sy + m0.sy) + l0.sy;
+    const float se = (h0.se + m0.se) + l0.se;
+    const float r = (float)P.r, r2 = (float)P.r2;
+    const float rho = 1.0f + s0;
+    const float inv = 1.0f / rho;
+    const float ux = r * sx * inv, uy = r * sy * inv;
+    // rho (u^2 + D T) = D + r^2 se  (sum w xi^2 = D)
+    const float T = 0.5f * (fmaf(r2, se, 2.0f) * inv - (ux * ux + uy * uy));
+    if (bad_positive32(rho) || bad_positive32(T) || !(dmax < RANGE)) atomicOr(flag, !(dmax < RANGE) ? 2 : 1);
+
+    // shifted equilibrium (forcing) and FP32 collide
+    const float uxs = ux + (float)P.tgx, uys = uy + (float)P.tgy;
+    const float th = (T + (float)P.dT_force) - 1.0f;
+    const float u2 = uxs * uxs + uys * uys;
+    const float a00m1 = u2 * fmaf(u2, 0.125f, -0.5f);
+    const float a20 = fmaf(u2, -0.25f, 0.5f);
+    const float b10 = fmaf(u2, -0.5f, 1.0f);
+    const float thu2 = th * u2, th2 = th * th;
+    const float omega = (float)P.omega;
+    float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], Wd[NSHELL];
+#pragma unroll
+    for (int s = 0; s < NSHELL; ++s) {
+        A0m1[s] = fmaf((float)P.sh[s].gamma, th2,
+                       fmaf((float)P.sh[s].beta, thu2, fmaf((float)P.sh[s].alpha, th, a00m1)));
+        A2[s] = fmaf((float)P.sh[s].delta, th, a20);
+        B1c[s] = fmaf((float)P.sh[s].eps, th, b10);
+        Wd[s] = omega * (float)P.sh[s].w;
+    }
+    const float drho = s0;
+    const float omc = (float)P.omc;
+    d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
+    Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, Wd, drho, omc);
+
+    // projection residual R = target - sums of the FP32 results, target = pre sums + gravity:
+    //   sum d' = sum d,  sum d' c = sum d c + rho g / r,  sum d' |c|^2 = sum d |c|^2 + rho (2 u.g + g^2) / r^2
+    Part h1, m1, l1;
+    split_sums(d, h1, m1, l1);
+    const float gx = (float)P.gx, gy = (float)P.gy;
+    const float rinv = 1.0f / r;
+    const float R0 = (h0.s0 - h1.s0) + ((m0.s0 - m1.s0) + (l0.s0 - l1.s0));
+    const float Rx = (h0.sx - h1.sx) + ((m0.sx - m1.sx) + (l0.sx - l1.sx)) + rho * gx * rinv;
+    const float Ry = (h0.sy - h1.sy) + ((m0.sy - m1.sy) + (l0.sy - l1.sy)) + rho * gy * rinv;
+    const float Re = (h0.se - h1.se) + ((m0.se - m1.se) + (l0.se - l1.se)) +
+                     rho * (2.0f * (ux * gx + uy * gy) + gx * gx + gy * gy) * (rinv * rinv);
+    // weighted least-norm correction d_i += w_i (l0 + lx c_x + ly c_y + le |c|^2)
+    const float lam0 = 2.0f * R0 - 0.5f * r2 * Re;
+    const float lame = r2 * (0.25f * r2 * Re - 0.5f * R0);
+    const float lamx = r2 * Rx, lamy = r2 * Ry;
+
+    const long long dsto = (long long)(y + HALO) * Lx + x;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) {
+        const float corr = fmaf(lame, (float)shell_c2(shell_of(i)),
+                                fmaf(lamx, (float)cx_of(i), fmaf(lamy, (float)cy_of(i), lam0)));
+        __stcs(dst + (long long)i * plane + dsto, fmaf((float)shell_w(shell_of(i)), corr, d[i]));
+    }
+
+    if (!P.y_periodic) {
+        // wall halo deviations rho w_wall - w from the summed density (FP64 on wall rows only)
+        const double rho_d = 1.0 + (double)s0;
+        if (y < HALO) {
+            const long long o = (long long)(HALO - 1 - y) * Lx + x;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i)
+                __stcs(dst + (long long)i * plane + o,
+                       (float)fma(rho_d, P.wall_bot[i], -shell_w(shell_of(i))));
+        }
+        if (y >= Ly - HALO) {
+            const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i)
+                __stcs(dst + (long long)i * plane + o,
+                       (float)fma(rho_d, P.wall_top[i], -shell_w(shell_of(i))));
+        }
+    }
+}
+
+}  // namespace lbg

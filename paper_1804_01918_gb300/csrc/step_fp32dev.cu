@@ -37,6 +37,15 @@ step_fp32dev_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
+step_fp32split_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P,
+                      int* __restrict__ flag) {
+    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= P.Lx * P.Ly) return;
+    const int y = site / P.Lx;
+    fp32split_site(src, dst, P, site - y * P.Lx, y, flag);
+}
+
+__global__ void __launch_bounds__(SITE_BLOCK)
 propagate_fp32dev_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P) {
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
@@ -155,6 +164,12 @@ inline int site_blocks32(const StepParams& P) {
 cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& P, int* flag,
                                 cudaStream_t s) {
     step_fp32dev_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_fp32split(const float* src, float* dst, const StepParams& P, int* flag,
+                                  cudaStream_t s) {
+    step_fp32split_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
     return cudaGetLastError();
 }
 

@@ -14,10 +14,10 @@ from dataclasses import dataclass
 import numpy as np
 
 NPOP = 37
-LB_FP64, LB_FP32DEV = 0, 1
+LB_FP64, LB_FP32DEV, LB_FP32SPLIT = 0, 1, 2
 
 _STATUS = {0: "LB_OK", 1: "LB_ERR_ARG", 2: "LB_ERR_ALLOC", 3: "LB_ERR_CUDA",
-           4: "LB_ERR_NONFINITE", 5: "LB_ERR_STATE"}
+           4: "LB_ERR_NONFINITE", 5: "LB_ERR_STATE", 6: "LB_ERR_RANGE"}
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblb_d2q37.so")
@@ -41,6 +41,12 @@ class lb_params(C.Structure):
                 ("gy", C.c_double), ("T_top", C.c_double), ("T_bottom", C.c_double),
                 ("y_periodic", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
+
+
+class lb_ensemble_opts(C.Structure):
+    _fields_ = [("tile_x", C.c_int), ("tile_y", C.c_int), ("graph_steps", C.c_int),
+                ("precision", C.c_int), ("stream", C.c_void_p), ("workspace", C.c_void_p),
+                ("workspace_bytes", C.c_size_t)]
 
 
 _lib = None
@@ -73,6 +79,21 @@ def lib() -> C.CDLL:
         L.lb_free.restype = None
         L.lb_probe_fma.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp]
         L.lb_moments_noalloc.argtypes = [C.POINTER(lb_params), vp, vp, vp, vp, vp]
+        PP = C.POINTER(C.c_void_p)
+        L.lb_ensemble_workspace_bytes.argtypes = [C.c_int, C.POINTER(lb_params),
+                                                  C.POINTER(lb_ensemble_opts), C.POINTER(C.c_size_t)]
+        L.lb_ensemble_init.argtypes = [C.c_int, C.POINTER(lb_params), PP, PP, PP, PP,
+                                       C.POINTER(lb_ensemble_opts), C.POINTER(vp)]
+        L.lb_ensemble_step.argtypes = [vp, C.c_int]
+        L.lb_ensemble_sync.argtypes = [vp]
+        L.lb_ensemble_autotune.argtypes = [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                           C.POINTER(C.c_double)]
+        L.lb_ensemble_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                       C.POINTER(C.c_int), C.POINTER(C.c_longlong)]
+        L.lb_ensemble_moments.argtypes = [vp, C.c_int, vp, vp, vp, vp]
+        L.lb_ensemble_get_populations.argtypes = [vp, C.c_int, vp]
+        L.lb_ensemble_free.argtypes = [vp]
+        L.lb_ensemble_free.restype = None
         _lib = L
     return _lib
 
@@ -81,9 +102,15 @@ def last_error() -> str:
     return lib().lb_last_error().decode()
 
 
+class RangeError(LBError):
+    pass
+
+
 def check(status: int, where: str) -> None:
     if status == 4:
         raise NonFiniteError(status, where)
+    if status == 6:
+        raise RangeError(status, where)
     if status != 0:
         raise LBError(status, where)
 
@@ -106,6 +133,8 @@ def _precision_code(p) -> int:
         return LB_FP64
     if p in (LB_FP32DEV, "fp32dev", "fp32"):
         return LB_FP32DEV
+    if p in (LB_FP32SPLIT, "fp32split"):
+        return LB_FP32SPLIT
     raise ValueError(f"unknown precision {p!r}")
 
 
@@ -270,3 +299,82 @@ def moments_noalloc(Lx: int, Ly: int, f_device_ptr: int, precision=LB_FP64, stre
     check(lib().lb_moments_noalloc(C.byref(p), f_device_ptr, *[o.ctypes.data for o in out]),
           "lb_moments_noalloc")
     return out
+
+
+class Ensemble:
+    """Independent D2Q37 lattices advanced together by one persistent launch per step
+    (include/lb_ensemble.h). members: list of dicts with Lx, Ly, tau and optional gx, gy, T_top,
+    T_bottom, y_periodic, plus host fields rho, ux, uy, T ([Ly][Lx] float64)."""
+
+    def __init__(self, members, precision="fp32split", tile=(0, 0), graph_steps=0, stream=None):
+        import torch
+        self._ctx = C.c_void_p()
+        n = len(members)
+        self.members = [(int(m["Lx"]), int(m["Ly"])) for m in members]
+        params = (lb_params * n)()
+        keep = []
+        ptrs = [(C.c_void_p * n)() for _ in range(4)]
+        for k, m in enumerate(members):
+            params[k] = make_params(m["Lx"], m["Ly"], m["tau"], m.get("gx", 0.0), m.get("gy", 0.0),
+                                    m.get("T_top", 1.0), m.get("T_bottom", 1.0),
+                                    m.get("y_periodic", False), precision)
+            for j, key in enumerate(("rho", "ux", "uy", "T")):
+                a = _host_f64(m[key], (int(m["Ly"]), int(m["Lx"])))
+                keep.append(a)
+                ptrs[j][k] = _ptr(a)
+        self.stream = torch.cuda.Stream() if stream is None else stream
+        sh = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else self.stream
+        opts = lb_ensemble_opts(int(tile[0]), int(tile[1]), int(graph_steps),
+                                _precision_code(precision), sh, None, 0)
+        nbytes = C.c_size_t()
+        check(lib().lb_ensemble_workspace_bytes(n, params, C.byref(opts), C.byref(nbytes)),
+              "lb_ensemble_workspace_bytes")
+        self._ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
+        opts.workspace = self._ws.data_ptr()
+        opts.workspace_bytes = nbytes.value
+        check(lib().lb_ensemble_init(n, params, *ptrs, C.byref(opts), C.byref(self._ctx)),
+              "lb_ensemble_init")
+
+    def step(self, n: int = 1) -> None:
+        check(lib().lb_ensemble_step(self._ctx, int(n)), "lb_ensemble_step")
+
+    def sync(self) -> None:
+        check(lib().lb_ensemble_sync(self._ctx), "lb_ensemble_sync")
+
+    def autotune(self, steps: int = 5):
+        tx, ty, m = C.c_int(), C.c_int(), C.c_double()
+        check(lib().lb_ensemble_autotune(self._ctx, int(steps), C.byref(tx), C.byref(ty), C.byref(m)),
+              "lb_ensemble_autotune")
+        return tx.value, ty.value, m.value
+
+    def info(self):
+        tx, ty, nt, ns = C.c_int(), C.c_int(), C.c_int(), C.c_longlong()
+        check(lib().lb_ensemble_info(self._ctx, C.byref(tx), C.byref(ty), C.byref(nt), C.byref(ns)),
+              "lb_ensemble_info")
+        return {"tile": (tx.value, ty.value), "items": nt.value, "sites": ns.value}
+
+    def moments(self, k: int):
+        Lx, Ly = self.members[k]
+        out = tuple(np.empty((Ly, Lx), np.float64) for _ in range(4))
+        check(lib().lb_ensemble_moments(self._ctx, k, *[o.ctypes.data for o in out]),
+              "lb_ensemble_moments")
+        return out
+
+    def get_populations(self, k: int) -> np.ndarray:
+        Lx, Ly = self.members[k]
+        f = np.empty((NPOP, Ly, Lx), np.float64)
+        check(lib().lb_ensemble_get_populations(self._ctx, k, f.ctypes.data),
+              "lb_ensemble_get_populations")
+        return f
+
+    def close(self) -> None:
+        if getattr(self, "_ctx", None) and self._ctx.value:
+            lib().lb_ensemble_free(self._ctx)
+            self._ctx = C.c_void_p()
+        self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

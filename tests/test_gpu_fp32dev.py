@@ -1,5 +1,6 @@
-"""GPU checks of the FP32-deviation form (populations stored in FP32 as f - w, FP32 collide, FP64
-moment accumulation and conservation projection) against the FP64 oracle.
+"""GPU checks of the FP32-deviation forms against the FP64 oracle: populations stored in FP32 as
+f - w with an FP32 collide, and the moment sums plus the conservation projection done either in
+FP64 (fp32dev) or by an exact three-way FP32 split (fp32split).
 
 The form is not expected to match FP64 bit for bit; the bar is a stated relative L2 error of the
 density and temperature fields and conservation at the level of FP32 storage rounding.
@@ -30,10 +31,14 @@ def rel_l2(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def test_fp32dev_rayleigh_taylor_l2_error_vs_fp64_oracle(L, orc):
+FORMS = ["fp32dev", "fp32split"]
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_fp32dev_rayleigh_taylor_l2_error_vs_fp64_oracle(L, orc, form):
     Lx, Ly, steps = 64, 256, 100
     st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
-    lat = L.Lattice.from_fields(st, tau=0.9, precision="fp32dev")
+    lat = L.Lattice.from_fields(st, tau=0.9, precision=form)
     lat.step(steps)
     rho, ux, uy, T = lat.moments()
     f = orc.run(orc.init_fields(st), tau=0.9, nsteps=steps, gy=st.gy, T_top=st.T_top,
@@ -41,7 +46,7 @@ def test_fp32dev_rayleigh_taylor_l2_error_vs_fp64_oracle(L, orc):
     orho, oux, ouy, oT = orc.moments(f)
     bound = steps * 37 * 2.0**-24 * 0.35
     e_rho, e_T = rel_l2(rho, orho), rel_l2(T, oT)
-    print(f"fp32dev 64x256 100 steps: rel L2 rho {e_rho:.3e}, T {e_T:.3e} (bound {bound:.1e})")
+    print(f"{form} 64x256 100 steps: rel L2 rho {e_rho:.3e}, T {e_T:.3e} (bound {bound:.1e})")
     assert e_rho < bound and e_T < bound
     # and the FP32 form is far better than plain FP32 storage of absolute populations would be
     assert e_rho < 1e-5 and e_T < 1e-5
@@ -56,10 +61,11 @@ def test_fp32dev_init_and_moments(L, orc):
     assert np.max(np.abs(ux)) < 1e-8
 
 
-def test_fp32dev_conserves_mass_momentum_energy_periodic(L, orc):
+@pytest.mark.parametrize("form", FORMS)
+def test_fp32dev_conserves_mass_momentum_energy_periodic(L, orc, form):
     Lx, Ly = 48, 40
     st = inputs.random_state(Lx, Ly, seed=3, du=0.02, dT=0.1, drho=0.1)
-    lat = L.Lattice.from_fields(st, tau=0.8, y_periodic=True, precision="fp32dev")
+    lat = L.Lattice.from_fields(st, tau=0.8, y_periodic=True, precision=form)
     cx, cy, w, r = L.velocity_set()
     f0 = lat.get_populations()
     lat.step(50)
@@ -88,12 +94,13 @@ def test_fp32dev_propagate_bit_exact(L):
         assert np.array_equal(got[i], want)
 
 
-def test_fp32dev_gravity_momentum_budget(L):
+@pytest.mark.parametrize("form", FORMS)
+def test_fp32dev_gravity_momentum_budget(L, form):
     """Periodic box with gravity: total momentum grows by g x mass per step (the projection
     targets rho u + rho g), to FP32 storage accuracy."""
     Lx, Ly, n, g = 32, 32, 20, -1e-4
     st = inputs.random_state(Lx, Ly, seed=8, du=0.01, dT=0.05, drho=0.05)
-    lat = L.Lattice.from_fields(st, tau=0.9, y_periodic=True, gy=g, precision="fp32dev")
+    lat = L.Lattice.from_fields(st, tau=0.9, y_periodic=True, gy=g, precision=form)
     cx, cy, w, r = L.velocity_set()
     f0 = lat.get_populations()
     lat.step(n)
@@ -102,3 +109,32 @@ def test_fp32dev_gravity_momentum_budget(L):
     jy0 = float(np.tensordot(r * cy, f0, 1).sum())
     jy1 = float(np.tensordot(r * cy, f1, 1).sum())
     assert jy1 - jy0 == pytest.approx(n * g * mass, rel=1e-4)
+
+
+def test_fp32split_one_step_matches_fp64_accumulation(L):
+    """One step from the same stored deviations: the split accumulation and the FP64 accumulation
+    feed the same FP32 collide, so results agree to a few FP32 ulps of the weights."""
+    Lx, Ly = 40, 36
+    st = inputs.random_state(Lx, Ly, seed=11, du=0.03, dT=0.15, drho=0.15)
+    a = L.Lattice.from_fields(st, tau=0.75, gy=-1e-3, precision="fp32dev")
+    b = L.Lattice.from_fields(st, tau=0.75, gy=-1e-3, precision="fp32split")
+    b.set_populations(a.get_populations())
+    a.step(1)
+    b.step(1)
+    cx, cy, w, r = L.velocity_set()
+    fa, fb = a.get_populations(), b.get_populations()
+    assert np.max(np.abs(fa - fb) / w[:, None, None]) < 2.0**-19
+
+
+def test_fp32split_reports_out_of_range_deviation(L):
+    """A deviation |f - w| >= 4 (planted on the host) leaves the exact-split range: the step flags
+    it and lb_sync reports LB_ERR_RANGE once."""
+    st = inputs.rayleigh_taylor(32, 32, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=0.9, precision="fp32split")
+    f = lat.get_populations()
+    f[3, 10, 7] += 6.0
+    lat.set_populations(f)
+    lat.step(1)
+    with pytest.raises(L.RangeError):
+        lat.sync()
+    lat.sync()
