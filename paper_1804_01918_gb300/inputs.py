@@ -98,13 +98,26 @@ def random_state(Lx: int, Ly: int, seed: int = 0, du: float = 0.05, dT: float = 
     return RTFields(rho=rho, ux=ux, uy=uy, T=T, T_top=1.0 - dT / 2, T_bottom=1.0 + dT / 2, gy=0.0)
 
 
+def tau_min_stable(A: float) -> float:
+    """Smallest relaxation time drawn for a member of Atwood number A.
+
+    The cold side of a member sits at T_top = 1 - A. The BGK D2Q37 step is linearly unstable far
+    below the reference temperature at small tau: in a periodic box a 1e-3 perturbation of a
+    uniform state grows to overflow at (T, tau) = (0.5, 0.6), (0.5, 0.65), (0.55, 0.6) and
+    (0.6, 0.6), and decays at (0.5, 0.7), (0.55, 0.65), (0.6, 0.65) and at every T >= 0.65 for
+    tau >= 0.6 (800 steps each on the oracle). This bound keeps a margin above that boundary:
+    0.6 up to A = 0.3, then rising linearly to 0.75 at A = 0.5."""
+    return 0.6 if A <= 0.3 else 0.6 + 0.75 * (A - 0.3)
+
+
 def ensemble_members(n: int, seed: int = 0, lx_min: int = 128, lx_max: int = 1024,
                      lx_multiple: int = 32) -> list[dict]:
     """Seed-drawn descriptors of an ensemble of independent Rayleigh-Taylor lattices.
 
     Lx is uniform over the multiples of ``lx_multiple`` in [lx_min, lx_max], Ly = 4 Lx, the Atwood
-    number is uniform in [0.05, 0.5] and the relaxation time uniform in [0.6, 1.2]. Each member
-    also gets its own field seed.
+    number is uniform in [0.05, 0.5] and the relaxation time uniform in [tau_min_stable(A), 1.2]
+    (i.e. [0.6, 1.2] except where the member's cold side would make the step unstable). Each
+    member also gets its own field seed.
     """
     rng = np.random.Generator(np.random.PCG64(seed))
     choices = np.arange(lx_min, lx_max + 1, lx_multiple)
@@ -112,7 +125,8 @@ def ensemble_members(n: int, seed: int = 0, lx_min: int = 128, lx_max: int = 102
     for m in range(n):
         Lx = int(choices[rng.integers(0, len(choices))])
         A = float(0.05 + 0.45 * rng.random())
-        tau = float(0.6 + 0.6 * rng.random())
+        lo = tau_min_stable(A)
+        tau = float(lo + (1.2 - lo) * rng.random())
         out.append({"Lx": Lx, "Ly": 4 * Lx, "atwood": A, "R": atwood_to_ratio(A), "tau": tau,
                     "seed": int(rng.integers(0, 2**31 - 1))})
     return out

@@ -28,7 +28,7 @@ def member_specs():
     for k, (Lx, Ly, tau, R) in enumerate([(96, 40, 0.7, 2.0), (64, 256, 0.9, 1.5), (130, 52, 1.1, 3.0),
                                           (33, 17, 0.62, 1.2)]):
         st = inputs.rayleigh_taylor(Lx, Ly, R=R, seed=k)
-        specs.append({"Lx": Lx, "Ly": Ly, "tau": tau, "gy": st.gy * 50, "T_top": st.T_top,
+        specs.append({"Lx": Lx, "Ly": Ly, "tau": tau, "gy": st.gy * 3, "T_top": st.T_top,
                       "T_bottom": st.T_bottom, "rho": st.rho, "ux": st.ux, "uy": st.uy, "T": st.T})
     return specs
 
