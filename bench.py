@@ -275,7 +275,8 @@ def main():
     from paper_1804_01918_gb300 import build as pkg_build
     from paper_1804_01918_gb300 import inputs, lb
 
-    rank, world, local = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    from paper_1804_01918_gb300 import replicas
+    rank, world, local = replicas.rank_env()
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -285,7 +286,7 @@ def main():
     torch.cuda.set_device(local)
     pkg_build.build()
 
-    st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=rank)
+    st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=replicas.replica_seed(rank))
     stream = torch.cuda.Stream()
     lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision=args.precision)
     lat.step(args.warmup)
@@ -307,12 +308,9 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     lat.sync()    # raises on a non-finite state
-    if dist:
-        t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(ms, dist, device="cuda")
     sites = LX * LY
-    value = world * sites * args.steps / (ms * 1e-3) / 1e6
+    value = replicas.aggregate_mlups(sites, args.steps, ms, world)
     kernel_s = ms * 1e-3 / args.steps
     lat.close()
     del lat
@@ -334,11 +332,7 @@ def main():
         t1 = time.perf_counter()
         lat2.close()
         del lat2
-        dt = t1 - t0
-        if dist:
-            t = torch.tensor([dt], dtype=torch.float64, device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = float(t.item())
+        dt = replicas.max_over_ranks(t1 - t0, dist, device="cuda")
         e2e = {"value": round(world * sites * args.steps / dt / 1e6, 2), "unit": "MLUPS",
                "h2d_bytes_per_step": round(4 * 8 * sites / args.steps, 1),
                "d2h_bytes_per_step": round(4 * 8 * sites / args.steps, 1),
