@@ -1,0 +1,74 @@
+/*
+ * lb_learned.h -- learned collide for the D2Q37 step (GB300 tensor cores).
+ *
+ * A small MLP (37 -> 128 -> 128 -> 37, GELU) replaces the collide of Sec. 3: it maps the 37
+ * pre-collision FP32 deviations of a site to the collision change, which is added to them and
+ * projected exactly onto the conserved moments (mass, momentum, energy; gravity included). Its
+ * forward and backward products run on tcgen05 tensor cores (BF16 operands, FP32 accumulation)
+ * in hand-written kernels; it is trained on the GPU (Adam) on (pre, post) pairs that the plain
+ * collide of this library produces. In a lattice step, every 32 x 32-site tile whose result
+ * differs from the plain collide by more than bound x max|f_plain| (checked every check_every
+ * steps) is replaced by the plain collide and stays on it until the next check.
+ *
+ * Layouts: sample arrays are [n][37] float32 in the order of lb_velocity_set() (device memory,
+ * caller-owned). Parameters are packed W1[128][37] b1[128] W2[128][128] b2[128] W3[37][128]
+ * b3[37] (float32); normalisation is [4][37]: mean and standard deviation of the inputs, then of
+ * the targets (post - pre).
+ * Conventions as in lb_d2q37.h. Learned steps need an LB_FP32SPLIT context with Lx and Ly
+ * multiples of 32.
+ */
+#ifndef LB_LEARNED_H
+#define LB_LEARNED_H
+
+#include "lb_d2q37.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lb_mlp lb_mlp;
+
+#define LB_MLP_NPARAM 26149
+#define LB_MLP_TILE 128
+
+/* New network on the current device: weights and biases uniform in +-1/sqrt(fan_in) from a
+ * SplitMix64 stream seeded with `seed`, identity normalisation. The library allocates its memory. */
+lb_status lb_mlp_create(uint64_t seed, lb_mlp** out);
+void lb_mlp_free(lb_mlp* net); /* NULL-safe */
+
+/* Host copies of the FP32 parameters (LB_MLP_NPARAM floats) and normalisation (148 floats). */
+lb_status lb_mlp_get_params(const lb_mlp* net, float* params, float* norm);
+/* Replace parameters (and normalisation unless norm is NULL); resets the optimizer state. */
+lb_status lb_mlp_set_params(lb_mlp* net, const float* params, const float* norm);
+
+/* y[n][37] = network(x[n][37]) on normalised inputs (device arrays, n a multiple of 128). */
+lb_status lb_mlp_eval(lb_mlp* net, const float* x, float* y, int n, void* stream);
+
+/* Mean squared error over n samples x 37 outputs of network(x) against normalised targets t, and
+ * its gradient with respect to the packed parameters (host array of LB_MLP_NPARAM floats). */
+lb_status lb_mlp_loss_grad(lb_mlp* net, const float* x, const float* t, int n, double* loss,
+                           float* grad, void* stream);
+
+/* Train on n (pre, post) pairs: sets the normalisation from the data, then `epochs` passes of
+ * shuffled mini-batches (batch a multiple of 128) with Adam (beta 0.9 / 0.999, eps 1e-8, rate lr).
+ * epoch_loss (host, may be NULL) receives each epoch's mean loss. Synchronous. */
+lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long long n, int epochs,
+                       int batch, float lr, uint64_t seed, float* epoch_loss, void* stream);
+
+/* Training pairs from a context's current state (LB_FP32SPLIT): for each of the n site indices
+ * (y * Lx + x, device array) pre = the pulled deviations, post = their plain collide. Async. */
+lb_status lb_collect_pairs(lb_ctx* c, const int* sites, int n, float* pre, float* post);
+
+/* Switch the context's collide to the learned one (net must outlive the setting), or back. */
+lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int check_every);
+lb_status lb_set_collide_plain(lb_ctx* c);
+
+/* Tiles checked and tiles that fell back since the learned collide was set, and the largest
+ * tile residual seen. Synchronous. */
+lb_status lb_learned_stats(lb_ctx* c, long long* checked, long long* fallback, double* max_residual);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LB_LEARNED_H */

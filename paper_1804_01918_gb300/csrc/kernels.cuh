@@ -47,4 +47,16 @@ cudaError_t launch_plane_to_dev32(const double* src, float* dst_plane_interior, 
 cudaError_t launch_plane_from_dev32(const float* src_plane_interior, double* dst, double w,
                                     long long n, cudaStream_t s);
 
+// ---- learned collide (learned.cu) ----
+struct LearnedState;
+lb_status learned_create(const struct lb_mlp* net, int Lx, int Ly, double bound, int check_every,
+                         LearnedState** out);
+void learned_destroy(LearnedState* ls);
+cudaError_t launch_step_learned(const float* src, float* dst, const StepParams& P, LearnedState* ls,
+                                int* flag, cudaStream_t s);
+cudaError_t launch_pairs(const float* src, const StepParams& P, const int* sites, int n, float* pre,
+                         float* post, int* flag, cudaStream_t s);
+lb_status learned_stats(LearnedState* ls, long long* checked, long long* fallback, double* max_res,
+                        cudaStream_t s);
+
 }  // namespace lbg

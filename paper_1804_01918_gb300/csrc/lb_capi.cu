@@ -12,6 +12,7 @@
 #include <new>
 
 #include "../../include/lb_d2q37.h"
+#include "../../include/lb_learned.h"
 #include "d2q37_gpu.cuh"
 #include "kernels.cuh"
 
@@ -142,13 +143,17 @@ struct lb_ctx {
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
     long long steps = 0;
+    LearnedState* learned = nullptr;  // learned collide, when set
 };
 
 namespace {
 
 lb_status launch_one_step(lb_ctx* c) {
     cudaError_t e;
-    if (c->p.precision == LB_FP64)
+    if (c->learned)
+        e = launch_step_learned((const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1], c->sp,
+                                c->learned, c->flag, c->stream);
+    else if (c->p.precision == LB_FP64)
         e = launch_step_fp64((const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1], c->sp,
                              c->flag, c->stream);
     else if (c->p.precision == LB_FP32SPLIT)
@@ -270,6 +275,7 @@ void lb_free(lb_ctx* c) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     for (int k = 0; k < 2; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
+    learned_destroy(c->learned);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -352,7 +358,8 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
 
 lb_status lb_step(lb_ctx* c, int n) {
     if (!c || n < 0) return LB_ERR_ARG;
-    while (n >= GRAPH_STEPS && !c->graph_failed) {
+    // the learned step's check schedule varies from step to step: launch it directly
+    while (n >= GRAPH_STEPS && !c->graph_failed && !c->learned) {
         const int par = c->cur;
         if (!c->graph[par] && !capture_graph(c, par)) {
             c->graph_failed = true;
@@ -454,6 +461,42 @@ lb_status lb_set_populations(lb_ctx* c, const double* f) {
     if (st != LB_OK) return st;
     LB_CUDA(cudaStreamSynchronize(c->stream));
     return LB_OK;
+}
+
+lb_status lb_collect_pairs(lb_ctx* c, const int* sites, int n, float* pre, float* post) {
+    if (!c || !sites || !pre || !post || n < 0) return LB_ERR_ARG;
+    if (c->p.precision != LB_FP32SPLIT) return LB_ERR_STATE;
+    if (n == 0) return LB_OK;
+    cudaError_t e = launch_pairs((const float*)c->buf[c->cur], c->sp, sites, n, pre, post, c->flag,
+                                 c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pairs kernel launch");
+    return LB_OK;
+}
+
+lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int check_every) {
+    if (!c || !net) return LB_ERR_ARG;
+    if (c->p.precision != LB_FP32SPLIT) return LB_ERR_STATE;
+    LearnedState* ls = nullptr;
+    lb_status st = learned_create(net, c->p.Lx, c->p.Ly, bound, check_every, &ls);
+    if (st != LB_OK) return st;
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    learned_destroy(c->learned);
+    c->learned = ls;
+    return LB_OK;
+}
+
+lb_status lb_set_collide_plain(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    learned_destroy(c->learned);
+    c->learned = nullptr;
+    return LB_OK;
+}
+
+lb_status lb_learned_stats(lb_ctx* c, long long* checked, long long* fallback, double* max_residual) {
+    if (!c) return LB_ERR_ARG;
+    if (!c->learned) return LB_ERR_STATE;
+    return learned_stats(c->learned, checked, fallback, max_residual, c->stream);
 }
 
 lb_status lb_steps_done(const lb_ctx* c, long long* n) {

@@ -1,0 +1,1034 @@
+// learned.cu -- learned collide: an MLP trained on the GPU to replace the plain collide, with an
+// exact projection onto the conserved moments and a per-tile fallback to the plain collide.
+//
+// Training data are (pre, post) pairs of FP32 deviations produced by the plain collide of this
+// library (pairs_kernel). The network (mlp_core.cuh) predicts the normalised collision change
+// (post - pre); its forward and backward passes run as tcgen05 BF16 x BF16 -> FP32 products with
+// hand-written epilogues (bias, GELU, GELU derivative, loss gradient), one 128-sample tile per CTA,
+// and Adam updates FP32 master weights and re-packs the BF16 operand images.
+//
+// The learned LB step (step_learned_kernel) is persistent over 32 x 32-site tiles: per tile it
+// pulls the populations, runs the MLP on 8 sub-tiles of 128 sites, adds the predicted change,
+// projects onto the exact post-collision moments, stores, and on check steps also evaluates the
+// plain collide of the same sites: if max |f_learned - f_plain| exceeds bound x max |f_plain| over
+// the tile, the tile is rewritten with the plain collide (the source copy is never modified, so
+// the plain result can always be recomputed) and stays on the plain collide until the next check.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/lb_learned.h"
+#include "d2q37_gpu.cuh"
+#include "kernels.cuh"
+#include "mlp_core.cuh"
+#include "site_fp32dev.cuh"
+
+using namespace lbg;
+using namespace lbg::mlp;
+
+namespace lbg {
+namespace learn {
+
+constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier waits
+constexpr int ERR_TIMEOUT = 8;             // status-word bit: a tensor-core wait gave up
+
+// Device view of a network: FP32 master parameters (for biases), BF16 operand images of the
+// weights, normalisation (mu_x, sd_x, mu_t, sd_t; 37 each).
+struct NetDev {
+    const float* params;
+    const char* w1img;   // [128][48]
+    const char* w2img;   // [128][128]
+    const char* w3img;   // [48][128]
+    const char* w3timg;  // [128][48]
+    const char* w2timg;  // [128][128]
+    const float* norm;   // [4][37]
+};
+
+struct LearnedStats {
+    unsigned long long checked, fallback;
+    unsigned int max_res_bits;  // non-negative float as bits (atomicMax)
+    unsigned int pad;
+};
+
+// ------------------------------------------------------------------------------------------------
+// training pairs: pre = pulled deviations, post = plain (exact-split) collide of them
+// ------------------------------------------------------------------------------------------------
+__global__ void pairs_kernel(const float* __restrict__ src, const StepParams P, const int* __restrict__ sites,
+                             int n, float* __restrict__ pre, float* __restrict__ post, int* __restrict__ flag) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int site = sites[k];
+    if (site < 0 || site >= P.Lx * P.Ly) {
+        atomicOr(flag, 1);
+        return;
+    }
+    const int y = site / P.Lx, x = site - y * P.Lx;
+    float d[NPOP];
+    Pull32<NPOP - 1>::run(src, d, x, y, P.Lx, P.Ly, P.y_periodic, P.plane);
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) pre[(size_t)k * NPOP + i] = d[i];
+    SplitPre s;
+    split_pre(d, P, s, flag);
+    split_collide(d, P, s);
+    split_project(d, P, s);
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) post[(size_t)k * NPOP + i] = d[i];
+}
+
+// Per-population sums (FP64) of pre and of post - pre for the normalisation statistics.
+__global__ void stats_kernel(const float* __restrict__ pre, const float* __restrict__ post, long long n,
+                             double* __restrict__ acc /* [4][37]: sum x, sum x^2, sum t, sum t^2 */) {
+    __shared__ double s[4 * NIN];
+    for (int k = threadIdx.x; k < 4 * NIN; k += blockDim.x) s[k] = 0.0;
+    __syncthreads();
+    double lx[NIN], lx2[NIN], lt[NIN], lt2[NIN];
+    for (int i = 0; i < NIN; ++i) lx[i] = lx2[i] = lt[i] = lt2[i] = 0.0;
+    for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
+        for (int i = 0; i < NIN; ++i) {
+            const double a = pre[r * NIN + i], t = (double)post[r * NIN + i] - (double)pre[r * NIN + i];
+            lx[i] += a;
+            lx2[i] += a * a;
+            lt[i] += t;
+            lt2[i] += t * t;
+        }
+    for (int i = 0; i < NIN; ++i) {
+        atomicAdd(&s[i], lx[i]);
+        atomicAdd(&s[NIN + i], lx2[i]);
+        atomicAdd(&s[2 * NIN + i], lt[i]);
+        atomicAdd(&s[3 * NIN + i], lt2[i]);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < 4 * NIN; k += blockDim.x) atomicAdd(&acc[k], s[k]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// shared-memory plan of the training kernel
+// ------------------------------------------------------------------------------------------------
+constexpr int TR_X = 0;
+constexpr int TR_H1 = TR_X + BYTES_X;      // H1, later dZ1
+constexpr int TR_H2 = TR_H1 + BYTES_H;     // H2, later dZ2
+constexpr int TR_DY = TR_H2 + BYTES_H;
+constexpr int TR_W1 = TR_DY + BYTES_DY;
+constexpr int TR_W2 = TR_W1 + BYTES_W1;
+constexpr int TR_W3 = TR_W2 + BYTES_W2;
+constexpr int TR_W3T = TR_W3 + BYTES_W3;
+constexpr int TR_W2T = TR_W3T + BYTES_W3T;
+constexpr int TR_GB = TR_W2T + BYTES_W2T;  // bias-gradient accumulators db1[128] db2[128] db3[48]
+constexpr int TR_MISC = TR_GB + (HID + HID + NOUTP) * 4;
+constexpr int TR_BYTES = TR_MISC + 64;
+
+// One 128-sample tile: forward, loss, backward; writes this CTA's parameter-gradient partial
+// (packed like the parameters) and adds its loss sum to *loss_acc.
+//   raw = 1: a = pre deviations, b = post deviations (normalised inside);
+//   raw = 0: a = normalised inputs, b = normalised targets.
+__global__ void __launch_bounds__(128, 1)
+mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restrict__ b,
+                 const int* __restrict__ perm, long long base, float inv_count, int raw,
+                 float* __restrict__ partial, double* __restrict__ loss_acc, int* __restrict__ flag) {
+    extern __shared__ __align__(1024) char sm[];
+    const int tid = threadIdx.x, warp = tid >> 5;
+    float* gb = reinterpret_cast<float*>(sm + TR_GB);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TR_MISC);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + TR_MISC + 8);
+    int* abort_flag = reinterpret_cast<int*>(sm + TR_MISC + 12);
+    float* loss_sm = reinterpret_cast<float*>(sm + TR_MISC + 16);
+
+    copy_to_smem(sm + TR_W1, net.w1img, BYTES_W1);
+    copy_to_smem(sm + TR_W2, net.w2img, BYTES_W2);
+    copy_to_smem(sm + TR_W3, net.w3img, BYTES_W3);
+    copy_to_smem(sm + TR_W3T, net.w3timg, BYTES_W3T);
+    copy_to_smem(sm + TR_W2T, net.w2timg, BYTES_W2T);
+    for (int k = tid; k < HID + HID + NOUTP; k += blockDim.x) gb[k] = 0.0f;
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        *abort_flag = 0;
+        *loss_sm = 0.0f;
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+
+    // ---- this thread's sample ----
+    const long long row = perm ? (long long)perm[base + (long long)blockIdx.x * TILE + tid]
+                               : base + (long long)blockIdx.x * TILE + tid;
+    float xn[KIN], tn[NIN];
+    {
+        const float* norm = net.norm;
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) {
+            const float av = a[row * NIN + i], bv = b[row * NIN + i];
+            if (raw) {
+                xn[i] = (av - norm[i]) / norm[NIN + i];
+                tn[i] = ((bv - av) - norm[2 * NIN + i]) / norm[3 * NIN + i];
+            } else {
+                xn[i] = av;
+                tn[i] = bv;
+            }
+        }
+#pragma unroll
+        for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
+#pragma unroll
+        for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(sm + TR_X, tid, k0, KIN, xn + k0);
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = *tslot;
+    uint32_t ph = 0;
+    bool ok = true;
+
+    auto issue_and_wait = [&](int which) {
+        if (tid == 0) {
+            switch (which) {
+                case 0: mma_kmajor(tm + 0, sm + TR_X, sm + TR_W1, KIN, HID); break;
+                case 1: mma_kmajor(tm + 128, sm + TR_H1, sm + TR_W2, HID, HID); break;
+                case 2: mma_kmajor(tm + 256, sm + TR_H2, sm + TR_W3, HID, NOUTP); break;
+                case 3:
+                    mma_kmajor(tm + 384, sm + TR_DY, sm + TR_W3T, NOUTP, HID);        // dH2
+                    mma_mnmajor(tm + 304, sm + TR_H2, HID, sm + TR_DY, NOUTP, NOUTP);  // dW3^T
+                    break;
+                case 4:
+                    mma_kmajor(tm + 384, sm + TR_H2, sm + TR_W2T, HID, HID);          // dH1 (H2 buf = dZ2)
+                    mma_mnmajor(tm + 256, sm + TR_H2, HID, sm + TR_H1, HID, HID);      // dW2
+                    break;
+                case 5: mma_mnmajor(tm + 128, sm + TR_H1, HID, sm + TR_X, KIN, NOUTP); break;  // dW1 (H1 buf = dZ1)
+            }
+            tc::mma_commit(bar);
+        }
+        const bool got = tc::mbar_wait_bounded(bar, ph, WAIT_LIMIT);
+        ph ^= 1u;
+        if (__syncthreads_or(!got)) {
+            ok = false;
+            return;
+        }
+        tc::fence_after_sync();
+    };
+    auto sync_for_mma = [&]() {
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        tc::fence_after_sync();
+    };
+
+    const float* b1 = net.params + OFF_B1;
+    const float* b2 = net.params + OFF_B2;
+    const float* b3 = net.params + OFF_B3;
+    float v[32];
+    do {
+        // ---- forward ----
+        issue_and_wait(0);
+        if (!ok) break;
+        for (int c = 0; c < HID; c += 32) {
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, c), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b1[c + j]);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
+        }
+        sync_for_mma();
+        issue_and_wait(1);
+        if (!ok) break;
+        for (int c = 0; c < HID; c += 32) {
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), v);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b2[c + j]);
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
+        }
+        sync_for_mma();
+        issue_and_wait(2);
+        if (!ok) break;
+        // ---- output, loss and its gradient ----
+        {
+            float yv[NOUTP];
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 256), yv);
+            tc::tmem_ld16(tmem_lane_addr(tm, warp, 288), yv + 32);
+            float dy[NOUTP], lsum = 0.0f;
+#pragma unroll
+            for (int j = 0; j < NOUTP; ++j) {
+                if (j < NOUT) {
+                    const float e = (yv[j] + b3[j]) - tn[j];
+                    lsum += e * e;
+                    dy[j] = 2.0f * e * inv_count;
+                    atomicAdd(&gb[2 * HID + j], dy[j]);
+                } else {
+                    dy[j] = 0.0f;
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NOUTP; j += 8) store_row8(sm + TR_DY, tid, j, NOUTP, dy + j);
+            atomicAdd(loss_sm, lsum);
+        }
+        sync_for_mma();
+        issue_and_wait(3);
+        if (!ok) break;
+        // ---- dZ2 = dH2 * gelu'(z2) into the H2 buffer; dW3^T partial ----
+        for (int c = 0; c < HID; c += 32) {
+            float z[32];
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), z);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                v[j] *= gelu_grad(z[j] + b2[c + j]);
+                atomicAdd(&gb[HID + c + j], v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
+        }
+        {
+            float g[NOUTP];
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 304), g);
+            tc::tmem_ld16(tmem_lane_addr(tm, warp, 336), g + 32);
+            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W3;
+#pragma unroll
+            for (int j = 0; j < NOUT; ++j) out[j * HID + tid] = g[j];  // dW3[j][h], h = this lane
+        }
+        sync_for_mma();
+        issue_and_wait(4);
+        if (!ok) break;
+        // ---- dZ1 = dH1 * gelu'(z1) into the H1 buffer; dW2 partial ----
+        for (int c = 0; c < HID; c += 32) {
+            float z[32];
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, c), z);
+#pragma unroll
+            for (int j = 0; j < 32; ++j) {
+                v[j] *= gelu_grad(z[j] + b1[c + j]);
+                atomicAdd(&gb[c + j], v[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
+        }
+        {
+            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W2 + (size_t)tid * HID;  // row o
+            for (int c = 0; c < HID; c += 32) {
+                tc::tmem_ld32(tmem_lane_addr(tm, warp, 256 + c), v);
+#pragma unroll
+                for (int j = 0; j < 32; j += 4)
+                    *reinterpret_cast<float4*>(out + c + j) = make_float4(v[j], v[j + 1], v[j + 2], v[j + 3]);
+            }
+        }
+        sync_for_mma();
+        issue_and_wait(5);
+        if (!ok) break;
+        {
+            float g[NOUTP];
+            tc::tmem_ld32(tmem_lane_addr(tm, warp, 128), g);
+            tc::tmem_ld16(tmem_lane_addr(tm, warp, 160), g + 32);
+            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W1 + (size_t)tid * NIN;  // row o
+#pragma unroll
+            for (int i = 0; i < NIN; ++i) out[i] = g[i];
+        }
+    } while (0);
+
+    __syncthreads();
+    if (ok) {
+        float* out = partial + (size_t)blockIdx.x * PART_STRIDE;
+        for (int k = tid; k < HID; k += blockDim.x) {
+            out[OFF_B1 + k] = gb[k];
+            out[OFF_B2 + k] = gb[HID + k];
+        }
+        for (int k = tid; k < NOUT; k += blockDim.x) out[OFF_B3 + k] = gb[2 * HID + k];
+        if (tid == 0) atomicAdd(loss_acc, (double)*loss_sm);
+    } else if (tid == 0) {
+        atomicOr(flag, ERR_TIMEOUT);
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tm, 512);
+    if (tid == 0) tc::mbar_inval(bar);
+}
+
+// Sum the per-tile gradient partials, take an Adam step on the FP32 master parameters and
+// re-pack the BF16 operand images. One thread per parameter.
+__global__ void adam_kernel(float* __restrict__ params, float* __restrict__ m, float* __restrict__ vv,
+                            const float* __restrict__ partial, int nparts, float lr, float bc1, float bc2,
+                            int apply, float* __restrict__ grad_out, char* __restrict__ w1img,
+                            char* __restrict__ w2img, char* __restrict__ w3img, char* __restrict__ w3timg,
+                            char* __restrict__ w2timg) {
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= NPARAM) return;
+    float g = 0.0f;
+    for (int c = 0; c < nparts; ++c) g += partial[(size_t)c * PART_STRIDE + p];
+    if (grad_out) grad_out[p] = g;
+    if (!apply) return;
+    const float b1c = 0.9f, b2c = 0.999f;
+    const float mm = b1c * m[p] + (1.0f - b1c) * g;
+    const float vn = b2c * vv[p] + (1.0f - b2c) * g * g;
+    m[p] = mm;
+    vv[p] = vn;
+    const float w = params[p] - lr * (mm / bc1) / (sqrtf(vn / bc2) + 1e-8f);
+    params[p] = w;
+    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+    if (p < OFF_B1) {
+        const int o = (p - OFF_W1) / NIN, i = (p - OFF_W1) % NIN;
+        *reinterpret_cast<__nv_bfloat16*>(w1img + elem_off(o, i, KIN)) = wb;
+    } else if (p >= OFF_W2 && p < OFF_B2) {
+        const int o = (p - OFF_W2) / HID, i = (p - OFF_W2) % HID;
+        *reinterpret_cast<__nv_bfloat16*>(w2img + elem_off(o, i, HID)) = wb;
+        *reinterpret_cast<__nv_bfloat16*>(w2timg + elem_off(i, o, HID)) = wb;
+    } else if (p >= OFF_W3 && p < OFF_B3) {
+        const int j = (p - OFF_W3) / HID, h = (p - OFF_W3) % HID;
+        *reinterpret_cast<__nv_bfloat16*>(w3img + elem_off(j, h, HID)) = wb;
+        *reinterpret_cast<__nv_bfloat16*>(w3timg + elem_off(h, j, NOUTP)) = wb;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// forward only (evaluation and the learned step)
+// ------------------------------------------------------------------------------------------------
+constexpr int FW_X = 0;
+constexpr int FW_H = FW_X + BYTES_X;
+constexpr int FW_W1 = FW_H + BYTES_H;
+constexpr int FW_W2 = FW_W1 + BYTES_W1;
+constexpr int FW_W3 = FW_W2 + BYTES_W2;
+constexpr int FW_RED = FW_W3 + BYTES_W3;   // block reductions (2 x 4 floats)
+constexpr int FW_MISC = FW_RED + 64;
+constexpr int FW_BYTES = FW_MISC + 64;
+
+struct FwdCtx {
+    char* sm;
+    uint64_t* bar;
+    uint32_t tm;
+    uint32_t ph;
+    int tid, warp;
+};
+
+// Network output (normalised, 37 values) of the inputs this thread stored as row tid of the X
+// image (all threads call it together). Returns false if a tensor-core wait gave up.
+__device__ __forceinline__ bool mlp_forward_tile(FwdCtx& f, const NetDev& net, float* y) {
+    const float* b1 = net.params + OFF_B1;
+    const float* b2 = net.params + OFF_B2;
+    const float* b3 = net.params + OFF_B3;
+    float v[32];
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    for (int layer = 0; layer < 3; ++layer) {
+        if (f.tid == 0) {
+            if (layer == 0) mma_kmajor(f.tm + 0, f.sm + FW_X, f.sm + FW_W1, KIN, HID);
+            if (layer == 1) mma_kmajor(f.tm + 128, f.sm + FW_H, f.sm + FW_W2, HID, HID);
+            if (layer == 2) mma_kmajor(f.tm + 0, f.sm + FW_H, f.sm + FW_W3, HID, NOUTP);
+            tc::mma_commit(f.bar);
+        }
+        const bool got = tc::mbar_wait_bounded(f.bar, f.ph, WAIT_LIMIT);
+        f.ph ^= 1u;
+        if (__syncthreads_or(!got)) return false;
+        tc::fence_after_sync();
+        if (layer < 2) {
+            const float* bias = layer == 0 ? b1 : b2;
+            for (int c = 0; c < HID; c += 32) {
+                tc::tmem_ld32(tmem_lane_addr(f.tm, f.warp, (layer == 0 ? 0 : 128) + c), v);
+#pragma unroll
+                for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + bias[c + j]);
+#pragma unroll
+                for (int j = 0; j < 32; j += 8) store_row8(f.sm + FW_H, f.tid, c + j, HID, v + j);
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            tc::fence_after_sync();
+        } else {
+            float yv[NOUTP];
+            tc::tmem_ld32(tmem_lane_addr(f.tm, f.warp, 0), yv);
+            tc::tmem_ld16(tmem_lane_addr(f.tm, f.warp, 32), yv + 32);
+#pragma unroll
+            for (int j = 0; j < NOUT; ++j) y[j] = yv[j] + b3[j];
+            tc::fence_before_sync();
+            __syncthreads();  // TMEM columns 0.. are free for the next tile's first layer
+            tc::fence_after_sync();
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void fwd_setup(FwdCtx& f, const NetDev& net, char* sm) {
+    f.sm = sm;
+    f.tid = threadIdx.x;
+    f.warp = threadIdx.x >> 5;
+    f.bar = reinterpret_cast<uint64_t*>(sm + FW_MISC);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + FW_MISC + 8);
+    copy_to_smem(sm + FW_W1, net.w1img, BYTES_W1);
+    copy_to_smem(sm + FW_W2, net.w2img, BYTES_W2);
+    copy_to_smem(sm + FW_W3, net.w3img, BYTES_W3);
+    if (f.tid == 0) tc::mbar_init(f.bar, 1);
+    if (f.warp == 0) tc::tmem_alloc(tslot, 256);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    f.tm = *tslot;
+    f.ph = 0;
+}
+
+__device__ __forceinline__ void fwd_teardown(FwdCtx& f) {
+    tc::fence_before_sync();
+    __syncthreads();
+    if (f.warp == 0) tc::tmem_dealloc(f.tm, 256);
+    if (f.tid == 0) tc::mbar_inval(f.bar);
+}
+
+// y[n][37] = network(x[n][37]) on normalised inputs; n a multiple of 128; persistent over tiles.
+__global__ void __launch_bounds__(128)
+mlp_eval_kernel(NetDev net, const float* __restrict__ x, float* __restrict__ y, int ntiles, int* __restrict__ flag) {
+    extern __shared__ __align__(1024) char sm[];
+    FwdCtx f;
+    fwd_setup(f, net, sm);
+    for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const long long row = (long long)t * TILE + f.tid;
+        float xn[KIN];
+#pragma unroll
+        for (int i = 0; i < NIN; ++i) xn[i] = x[row * NIN + i];
+#pragma unroll
+        for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
+#pragma unroll
+        for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(sm + FW_X, f.tid, k0, KIN, xn + k0);
+        float out[NOUT];
+        if (!mlp_forward_tile(f, net, out)) {
+            if (f.tid == 0) atomicOr(flag, ERR_TIMEOUT);
+            break;
+        }
+#pragma unroll
+        for (int j = 0; j < NOUT; ++j) y[row * NOUT + j] = out[j];
+    }
+    fwd_teardown(f);
+}
+
+// The learned LB step (see the file header). Lx and Ly are multiples of 32.
+__global__ void __launch_bounds__(128)
+step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P, NetDev net,
+                    unsigned char* __restrict__ tile_mode, int check, float bound,
+                    LearnedStats* __restrict__ stats, int* __restrict__ flag) {
+    extern __shared__ __align__(1024) char sm[];
+    FwdCtx f;
+    fwd_setup(f, net, sm);
+    float* red = reinterpret_cast<float*>(sm + FW_RED);
+    const int ntx = P.Lx / 32, ntiles = ntx * (P.Ly / 32);
+    const float* mu_x = net.norm;
+    const float* sd_x = net.norm + NIN;
+    const float* mu_t = net.norm + 2 * NIN;
+    const float* sd_t = net.norm + 3 * NIN;
+    bool alive = true;
+    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
+        const int x0 = (t % ntx) * 32, y0 = (t / ntx) * 32;
+        const int mode = tile_mode[t];
+        const int x = x0 + (f.tid & 31);
+        if (!check && mode) {
+            for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
+            continue;
+        }
+        float rmax = 0.0f, fmax = 0.0f;
+        for (int sub = 0; sub < 8; ++sub) {
+            const int y = y0 + 4 * sub + (f.tid >> 5);
+            float d[NPOP];
+            Pull32<NPOP - 1>::run(src, d, x, y, P.Lx, P.Ly, P.y_periodic, P.plane);
+            SplitPre s;
+            split_pre(d, P, s, flag);
+            float xn[KIN];
+#pragma unroll
+            for (int i = 0; i < NIN; ++i) xn[i] = (d[i] - mu_x[i]) / sd_x[i];
+#pragma unroll
+            for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
+#pragma unroll
+            for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(sm + FW_X, f.tid, k0, KIN, xn + k0);
+            float yv[NOUT];
+            if (!mlp_forward_tile(f, net, yv)) {
+                alive = false;
+                break;
+            }
+            float dl[NPOP];
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) dl[i] = d[i] + fmaf(yv[i], sd_t[i], mu_t[i]);
+            split_project(dl, P, s);
+            if (check) {
+                split_collide(d, P, s);  // d becomes the plain collide's candidate
+                split_project(d, P, s);
+#pragma unroll
+                for (int i = 0; i < NPOP; ++i) {
+                    rmax = fmaxf(rmax, fabsf(dl[i] - d[i]));
+                    fmax = fmaxf(fmax, fabsf((float)shell_w(shell_of(i)) + d[i]));
+                }
+            }
+            split_store(dst, P, x, y, dl, s.s0);
+        }
+        if (!alive) break;
+        if (check) {
+            // block maxima of the residual and of |f_plain|
+            for (int o = 16; o > 0; o >>= 1) {
+                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+                fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+            }
+            if ((f.tid & 31) == 0) {
+                red[f.warp] = rmax;
+                red[4 + f.warp] = fmax;
+            }
+            __syncthreads();
+            const float R = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
+            const float F = fmaxf(fmaxf(red[4], red[5]), fmaxf(red[6], red[7]));
+            __syncthreads();
+            const float res = F > 0.0f ? R / F : R;
+            const int fall = !(res <= bound);
+            if (f.tid == 0) {
+                tile_mode[t] = (unsigned char)fall;
+                atomicAdd(&stats->checked, 1ull);
+                if (fall) atomicAdd(&stats->fallback, 1ull);
+                atomicMax(&stats->max_res_bits, __float_as_uint(res));
+            }
+            if (fall)
+                for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
+        }
+    }
+    if (!alive && f.tid == 0) atomicOr(flag, ERR_TIMEOUT);
+    fwd_teardown(f);
+}
+
+}  // namespace learn
+}  // namespace lbg
+
+using namespace lbg::learn;
+
+// ------------------------------------------------------------------------------------------------
+// host side
+// ------------------------------------------------------------------------------------------------
+struct lb_mlp {
+    char* mem = nullptr;  // one device allocation
+    float* params = nullptr;
+    float* m = nullptr;
+    float* v = nullptr;
+    float* norm = nullptr;
+    char* img[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+    long long adam_steps = 0;
+    NetDev dev() const {
+        NetDev n;
+        n.params = params;
+        n.w1img = img[0];
+        n.w2img = img[1];
+        n.w3img = img[2];
+        n.w3timg = img[3];
+        n.w2timg = img[4];
+        n.norm = norm;
+        return n;
+    }
+};
+
+namespace {
+
+lb_status fail_l(cudaError_t e, const char* where) {
+    char msg[256];
+    std::snprintf(msg, sizeof msg, "%s: %s", where, cudaGetErrorString(e));
+    set_last_error(msg);
+    return LB_ERR_CUDA;
+}
+
+#define L_CUDA(call)                                   \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return fail_l(e_, #call); \
+    } while (0)
+
+constexpr size_t IMG_BYTES[5] = {BYTES_W1, BYTES_W2, BYTES_W3, BYTES_W3T, BYTES_W2T};
+
+// SplitMix64 (Steele, Lea & Flood 2014): counter-based 64-bit generator.
+uint64_t splitmix64(uint64_t& s) {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+double uniform01(uint64_t& s) { return (double)(splitmix64(s) >> 11) * (1.0 / 9007199254740992.0); }
+
+// Pack host FP32 parameters into the BF16 operand images (host copies, then one upload).
+void pack_images(const std::vector<float>& p, std::vector<std::vector<uint16_t>>& img) {
+    auto bf = [](float x) {
+        // round to nearest even on the bit pattern (finite inputs)
+        uint32_t u;
+        std::memcpy(&u, &x, 4);
+        const uint32_t lsb = (u >> 16) & 1u;
+        u += 0x7FFFu + lsb;
+        return (uint16_t)(u >> 16);
+    };
+    for (int k = 0; k < 5; ++k) img[k].assign(IMG_BYTES[k] / 2, 0);
+    for (int o = 0; o < HID; ++o)
+        for (int i = 0; i < NIN; ++i) img[0][elem_off(o, i, KIN) / 2] = bf(p[OFF_W1 + o * NIN + i]);
+    for (int o = 0; o < HID; ++o)
+        for (int i = 0; i < HID; ++i) {
+            img[1][elem_off(o, i, HID) / 2] = bf(p[OFF_W2 + o * HID + i]);
+            img[4][elem_off(i, o, HID) / 2] = bf(p[OFF_W2 + o * HID + i]);
+        }
+    for (int j = 0; j < NOUT; ++j)
+        for (int h = 0; h < HID; ++h) {
+            img[2][elem_off(j, h, HID) / 2] = bf(p[OFF_W3 + j * HID + h]);
+            img[3][elem_off(h, j, NOUTP) / 2] = bf(p[OFF_W3 + j * HID + h]);
+        }
+}
+
+lb_status upload_params(lb_mlp* net, const float* params, const float* norm, cudaStream_t s) {
+    std::vector<float> p(params, params + NPARAM);
+    std::vector<std::vector<uint16_t>> img(5);
+    pack_images(p, img);
+    L_CUDA(cudaMemcpyAsync(net->params, params, NPARAM * sizeof(float), cudaMemcpyHostToDevice, s));
+    if (norm) L_CUDA(cudaMemcpyAsync(net->norm, norm, 4 * NIN * sizeof(float), cudaMemcpyHostToDevice, s));
+    for (int k = 0; k < 5; ++k)
+        L_CUDA(cudaMemcpyAsync(net->img[k], img[k].data(), IMG_BYTES[k], cudaMemcpyHostToDevice, s));
+    L_CUDA(cudaMemsetAsync(net->m, 0, NPARAM * sizeof(float), s));
+    L_CUDA(cudaMemsetAsync(net->v, 0, NPARAM * sizeof(float), s));
+    L_CUDA(cudaStreamSynchronize(s));
+    net->adam_steps = 0;
+    return LB_OK;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+    return std::max(1, n);
+}
+
+lb_status set_smem_limits() {
+    static bool done = false;
+    if (done) return LB_OK;
+    L_CUDA(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES));
+    L_CUDA(cudaFuncSetAttribute(mlp_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
+    L_CUDA(cudaFuncSetAttribute(step_learned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
+    done = true;
+    return LB_OK;
+}
+
+// Run the training kernel on `ntiles` tiles (rows from perm or contiguous) and reduce gradients;
+// apply = take an Adam step. Device scratch: partial [ntiles][NPARAM], loss accumulator, flag.
+lb_status train_batch(lb_mlp* net, const float* a, const float* b, const int* perm, long long base,
+                      int ntiles, int raw, float lr, int apply, float* partial, double* loss_acc,
+                      int* flag, float* grad_out, cudaStream_t s) {
+    const float inv_count = 1.0f / ((float)ntiles * TILE * NOUT);
+    mlp_train_kernel<<<ntiles, TILE, TR_BYTES, s>>>(net->dev(), a, b, perm, base, inv_count, raw, partial,
+                                                    loss_acc, flag);
+    L_CUDA(cudaGetLastError());
+    float bc1 = 1.0f, bc2 = 1.0f;
+    if (apply) {
+        net->adam_steps += 1;
+        bc1 = 1.0f - std::pow(0.9f, (float)net->adam_steps);
+        bc2 = 1.0f - std::pow(0.999f, (float)net->adam_steps);
+    }
+    adam_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(net->params, net->m, net->v, partial, ntiles, lr, bc1,
+                                                     bc2, apply, grad_out, net->img[0], net->img[1], net->img[2],
+                                                     net->img[3], net->img[4]);
+    L_CUDA(cudaGetLastError());
+    return LB_OK;
+}
+
+struct Scratch {
+    char* mem = nullptr;
+    float* partial = nullptr;
+    double* loss = nullptr;
+    int* flag = nullptr;
+    float* grad = nullptr;
+    ~Scratch() {
+        if (mem) cudaFree(mem);
+    }
+    lb_status alloc(int ntiles) {
+        const size_t pb = ((size_t)ntiles * PART_STRIDE * sizeof(float) + 255) / 256 * 256;
+        const size_t gb = ((size_t)NPARAM * sizeof(float) + 255) / 256 * 256;
+        cudaError_t e = cudaMalloc((void**)&mem, pb + gb + 256);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            mem = nullptr;
+            set_last_error("MLP training scratch allocation failed");
+            return LB_ERR_ALLOC;
+        }
+        partial = (float*)mem;
+        grad = (float*)(mem + pb);
+        loss = (double*)(mem + pb + gb);
+        flag = (int*)(mem + pb + gb + 64);
+        return LB_OK;
+    }
+};
+
+lb_status check_flag(int* dflag, cudaStream_t s) {
+    int h = 0;
+    L_CUDA(cudaMemcpyAsync(&h, dflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+    L_CUDA(cudaStreamSynchronize(s));
+    if (h & ERR_TIMEOUT) {
+        set_last_error("a tensor-core completion wait gave up (MLP kernel)");
+        return LB_ERR_CUDA;
+    }
+    if (h & 2) return LB_ERR_RANGE;
+    if (h) return LB_ERR_NONFINITE;
+    return LB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lb_status lb_mlp_create(uint64_t seed, lb_mlp** out) {
+    if (!out) return LB_ERR_ARG;
+    *out = nullptr;
+    lb_mlp* net = new (std::nothrow) lb_mlp();
+    if (!net) return LB_ERR_ALLOC;
+    size_t total = 3 * ((NPARAM * sizeof(float) + 255) / 256 * 256) + 1024;
+    for (int k = 0; k < 5; ++k) total += IMG_BYTES[k];
+    cudaError_t e = cudaMalloc((void**)&net->mem, total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete net;
+        set_last_error("MLP allocation failed");
+        return LB_ERR_ALLOC;
+    }
+    char* p = net->mem;
+    const size_t pbytes = (NPARAM * sizeof(float) + 255) / 256 * 256;
+    net->params = (float*)p;
+    p += pbytes;
+    net->m = (float*)p;
+    p += pbytes;
+    net->v = (float*)p;
+    p += pbytes;
+    net->norm = (float*)p;
+    p += 1024;
+    for (int k = 0; k < 5; ++k) {
+        net->img[k] = p;
+        p += IMG_BYTES[k];
+    }
+    // PyTorch-style default initialisation: weights and biases uniform in +-1/sqrt(fan_in)
+    std::vector<float> w(NPARAM);
+    uint64_t s = seed ^ 0x5D3F2A1B9C8E7F60ull;
+    auto fill = [&](int off, int count, int fan_in) {
+        const double a = 1.0 / std::sqrt((double)fan_in);
+        for (int k = 0; k < count; ++k) w[off + k] = (float)((2.0 * uniform01(s) - 1.0) * a);
+    };
+    fill(OFF_W1, HID * NIN, NIN);
+    fill(OFF_B1, HID, NIN);
+    fill(OFF_W2, HID * HID, HID);
+    fill(OFF_B2, HID, HID);
+    fill(OFF_W3, NOUT * HID, HID);
+    fill(OFF_B3, NOUT, HID);
+    std::vector<float> norm(4 * NIN, 0.0f);
+    for (int i = 0; i < NIN; ++i) norm[NIN + i] = norm[3 * NIN + i] = 1.0f;
+    lb_status st = set_smem_limits();
+    if (st == LB_OK) st = upload_params(net, w.data(), norm.data(), 0);
+    if (st != LB_OK) {
+        lb_mlp_free(net);
+        return st;
+    }
+    *out = net;
+    return LB_OK;
+}
+
+void lb_mlp_free(lb_mlp* net) {
+    if (!net) return;
+    cudaDeviceSynchronize();
+    if (net->mem) cudaFree(net->mem);
+    delete net;
+}
+
+lb_status lb_mlp_get_params(const lb_mlp* net, float* params, float* norm) {
+    if (!net) return LB_ERR_ARG;
+    if (params) L_CUDA(cudaMemcpy(params, net->params, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    if (norm) L_CUDA(cudaMemcpy(norm, net->norm, 4 * NIN * sizeof(float), cudaMemcpyDeviceToHost));
+    return LB_OK;
+}
+
+lb_status lb_mlp_set_params(lb_mlp* net, const float* params, const float* norm) {
+    if (!net || !params) return LB_ERR_ARG;
+    return upload_params(net, params, norm, 0);
+}
+
+lb_status lb_mlp_eval(lb_mlp* net, const float* x, float* y, int n, void* stream) {
+    if (!net || !x || !y || n <= 0 || n % TILE) return LB_ERR_ARG;
+    lb_status st = set_smem_limits();
+    if (st != LB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch sc;
+    st = sc.alloc(1);
+    if (st != LB_OK) return st;
+    L_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int), s));
+    const int ntiles = n / TILE;
+    const int grid = std::min(ntiles, 2 * sm_count());
+    mlp_eval_kernel<<<grid, TILE, FW_BYTES, s>>>(net->dev(), x, y, ntiles, sc.flag);
+    L_CUDA(cudaGetLastError());
+    return check_flag(sc.flag, s);
+}
+
+lb_status lb_mlp_loss_grad(lb_mlp* net, const float* x, const float* t, int n, double* loss, float* grad,
+                           void* stream) {
+    if (!net || !x || !t || n <= 0 || n % TILE) return LB_ERR_ARG;
+    lb_status st = set_smem_limits();
+    if (st != LB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ntiles = n / TILE;
+    Scratch sc;
+    st = sc.alloc(ntiles);
+    if (st != LB_OK) return st;
+    L_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int), s));
+    L_CUDA(cudaMemsetAsync(sc.loss, 0, sizeof(double), s));
+    st = train_batch(net, x, t, nullptr, 0, ntiles, 0, 0.0f, 0, sc.partial, sc.loss, sc.flag, sc.grad, s);
+    if (st != LB_OK) return st;
+    st = check_flag(sc.flag, s);
+    if (st != LB_OK) return st;
+    double l = 0.0;
+    L_CUDA(cudaMemcpy(&l, sc.loss, sizeof(double), cudaMemcpyDeviceToHost));
+    if (loss) *loss = l / ((double)n * NOUT);
+    if (grad) L_CUDA(cudaMemcpy(grad, sc.grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    return LB_OK;
+}
+
+lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long long n, int epochs, int batch,
+                       float lr, uint64_t seed, float* epoch_loss, void* stream) {
+    if (!net || !pre || !post || n < batch || epochs < 1 || batch < TILE || batch % TILE || !(lr > 0.0f))
+        return LB_ERR_ARG;
+    if (n > (1ll << 31) - 1) return LB_ERR_ARG;
+    lb_status st = set_smem_limits();
+    if (st != LB_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int ntiles = batch / TILE;
+    Scratch sc;
+    st = sc.alloc(ntiles);
+    if (st != LB_OK) return st;
+    // normalisation statistics from the data (FP64 sums on the device)
+    {
+        double* acc = nullptr;
+        L_CUDA(cudaMalloc((void**)&acc, 4 * NIN * sizeof(double)));
+        cudaMemsetAsync(acc, 0, 4 * NIN * sizeof(double), s);
+        stats_kernel<<<4 * sm_count(), 256, 0, s>>>(pre, post, n, acc);
+        std::vector<double> h(4 * NIN);
+        cudaError_t e = cudaMemcpyAsync(h.data(), acc, 4 * NIN * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        cudaFree(acc);
+        if (e != cudaSuccess) return fail_l(e, "normalisation statistics");
+        std::vector<float> norm(4 * NIN);
+        for (int i = 0; i < NIN; ++i) {
+            const double mx = h[i] / n, vx = std::max(0.0, h[NIN + i] / n - mx * mx);
+            const double mt = h[2 * NIN + i] / n, vt = std::max(0.0, h[3 * NIN + i] / n - mt * mt);
+            norm[i] = (float)mx;
+            norm[NIN + i] = (float)(vx > 0.0 ? std::sqrt(vx) : 1.0);
+            norm[2 * NIN + i] = (float)mt;
+            norm[3 * NIN + i] = (float)(vt > 0.0 ? std::sqrt(vt) : 1.0);
+        }
+        L_CUDA(cudaMemcpyAsync(net->norm, norm.data(), 4 * NIN * sizeof(float), cudaMemcpyHostToDevice, s));
+    }
+    int* dperm = nullptr;
+    L_CUDA(cudaMalloc((void**)&dperm, (size_t)n * sizeof(int)));
+    std::vector<int> perm((size_t)n);
+    const long long nb = n / batch;
+    uint64_t rs = seed;
+    for (int ep = 0; ep < epochs && st == LB_OK; ++ep) {
+        for (long long k = 0; k < n; ++k) perm[k] = (int)k;
+        for (long long k = n - 1; k > 0; --k) {  // Fisher-Yates
+            const long long j = (long long)(splitmix64(rs) % (uint64_t)(k + 1));
+            std::swap(perm[k], perm[j]);
+        }
+        cudaError_t e = cudaMemcpyAsync(dperm, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc.loss, 0, sizeof(double), s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(sc.flag, 0, sizeof(int), s);
+        if (e != cudaSuccess) {
+            st = fail_l(e, "epoch setup");
+            break;
+        }
+        for (long long bi = 0; bi < nb && st == LB_OK; ++bi)
+            st = train_batch(net, pre, post, dperm, bi * batch, ntiles, 1, lr, 1, sc.partial, sc.loss, sc.flag,
+                             nullptr, s);
+        if (st != LB_OK) break;
+        st = check_flag(sc.flag, s);
+        if (st != LB_OK) break;
+        double l = 0.0;
+        e = cudaMemcpy(&l, sc.loss, sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            st = fail_l(e, "epoch loss");
+            break;
+        }
+        if (epoch_loss) epoch_loss[ep] = (float)(l / ((double)nb * batch * NOUT));
+    }
+    cudaStreamSynchronize(s);
+    cudaFree(dperm);
+    return st;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------------------------------------
+// integration with lb_ctx (lb_capi.cu): launchers used by the C ABI there
+// ------------------------------------------------------------------------------------------------
+namespace lbg {
+
+struct LearnedState {
+    const lb_mlp* net = nullptr;
+    unsigned char* tile_mode = nullptr;
+    LearnedStats* stats = nullptr;
+    char* mem = nullptr;
+    float bound = 1e-4f;
+    int check_every = 1;
+    long long steps = 0;
+};
+
+lb_status learned_create(const lb_mlp* net, int Lx, int Ly, double bound, int check_every, LearnedState** out) {
+    if (!net || !out || Lx % 32 || Ly % 32 || check_every < 1 || !(bound >= 0.0)) return LB_ERR_ARG;
+    lb_status st = set_smem_limits();
+    if (st != LB_OK) return st;
+    LearnedState* ls = new (std::nothrow) LearnedState();
+    if (!ls) return LB_ERR_ALLOC;
+    const size_t ntiles = (size_t)(Lx / 32) * (Ly / 32);
+    cudaError_t e = cudaMalloc((void**)&ls->mem, 256 + (ntiles + 255) / 256 * 256);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        delete ls;
+        set_last_error("learned-collide state allocation failed");
+        return LB_ERR_ALLOC;
+    }
+    ls->stats = (LearnedStats*)ls->mem;
+    ls->tile_mode = (unsigned char*)(ls->mem + 256);
+    e = cudaMemset(ls->mem, 0, 256 + ntiles);
+    if (e != cudaSuccess) {
+        cudaFree(ls->mem);
+        delete ls;
+        return fail_l(e, "cudaMemset(learned state)");
+    }
+    ls->net = net;
+    ls->bound = (float)bound;
+    ls->check_every = check_every;
+    *out = ls;
+    return LB_OK;
+}
+
+void learned_destroy(LearnedState* ls) {
+    if (!ls) return;
+    cudaDeviceSynchronize();
+    if (ls->mem) cudaFree(ls->mem);
+    delete ls;
+}
+
+cudaError_t launch_step_learned(const float* src, float* dst, const StepParams& P, LearnedState* ls, int* flag,
+                                cudaStream_t s) {
+    const int check = (ls->steps % ls->check_every) == 0;
+    ls->steps += 1;
+    const int ntiles = (P.Lx / 32) * (P.Ly / 32);
+    const int grid = std::min(ntiles, 2 * sm_count());
+    step_learned_kernel<<<grid, TILE, FW_BYTES, s>>>(src, dst, P, ls->net->dev(), ls->tile_mode, check, ls->bound,
+                                                     ls->stats, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pairs(const float* src, const StepParams& P, const int* sites, int n, float* pre, float* post,
+                         int* flag, cudaStream_t s) {
+    pairs_kernel<<<(n + 127) / 128, 128, 0, s>>>(src, P, sites, n, pre, post, flag);
+    return cudaGetLastError();
+}
+
+lb_status learned_stats(LearnedState* ls, long long* checked, long long* fallback, double* max_res,
+                        cudaStream_t s) {
+    LearnedStats h;
+    L_CUDA(cudaMemcpyAsync(&h, ls->stats, sizeof h, cudaMemcpyDeviceToHost, s));
+    L_CUDA(cudaStreamSynchronize(s));
+    if (checked) *checked = (long long)h.checked;
+    if (fallback) *fallback = (long long)h.fallback;
+    if (max_res) {
+        float f;
+        std::memcpy(&f, &h.max_res_bits, 4);
+        *max_res = f;
+    }
+    return LB_OK;
+}
+
+}  // namespace lbg

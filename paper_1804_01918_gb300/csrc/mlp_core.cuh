@@ -1,0 +1,116 @@
+// mlp_core.cuh -- the learned collide's MLP (37 -> 128 -> 128 -> 37, GELU) on tcgen05 tensor cores.
+//
+// A CTA handles 128 samples (one per TMEM lane / thread). Activations and weights are BF16 in
+// shared memory in the no-swizzle core-matrix layout of tc_helpers.cuh, always stored
+// "row-major by sample" (rows = samples or output features, 16-byte rows along the reduction
+// dimension); accumulators are FP32 in TMEM.
+//
+//   forward   D1 = X  W1^T  (M 128, N 128, K 48)    z1 = D1 + b1, h1 = gelu(z1)
+//             D2 = H1 W2^T  (M 128, N 128, K 128)   z2 = D2 + b2, h2 = gelu(z2)
+//             D3 = H2 W3^T  (M 128, N 48,  K 128)   y  = D3 + b3 (first 37 columns)
+//   backward  dH2 = dY W3   (B operand W3^T, K 48)  dz2 = dH2 * gelu'(z2)
+//             dH1 = dZ2 W2  (B operand W2^T)        dz1 = dH1 * gelu'(z1)
+//             dW3^T = H2^T dY, dW2 = dZ2^T H1, dW1 = dZ1^T X  (K = the 128 samples; both operands
+//             read MN-major from the same sample-major buffers)
+//
+// Inputs and targets are normalised per population: x = (d_pre - mu_x) / sd_x and the network
+// predicts the collision change t = (d_post - d_pre - mu_t) / sd_t.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include <cstdint>
+
+#include "tc_helpers.cuh"
+
+namespace lbg {
+namespace mlp {
+
+constexpr int NIN = 37;
+constexpr int KIN = 48;    // input features padded to a multiple of 16
+constexpr int HID = 128;
+constexpr int NOUT = 37;
+constexpr int NOUTP = 48;  // outputs padded to a multiple of 16
+constexpr int TILE = 128;  // samples per MMA round
+
+// Parameter packing (FP32): W1[128][37] b1[128] W2[128][128] b2[128] W3[37][128] b3[37]
+constexpr int OFF_W1 = 0;
+constexpr int OFF_B1 = OFF_W1 + HID * NIN;
+constexpr int OFF_W2 = OFF_B1 + HID;
+constexpr int OFF_B2 = OFF_W2 + HID * HID;
+constexpr int OFF_W3 = OFF_B2 + HID;
+constexpr int OFF_B3 = OFF_W3 + NOUT * HID;
+constexpr int NPARAM = OFF_B3 + NOUT;
+// Stride (floats) between per-tile gradient partials: a multiple of 64 so that every row of the
+// W2 block (OFF_W2 and HID are multiples of 4) starts 16-byte aligned for vector stores.
+constexpr int PART_STRIDE = (NPARAM + 63) / 64 * 64;
+static_assert(OFF_W2 % 4 == 0 && HID % 4 == 0, "vector stores of dW2 rows need 16-byte alignment");
+
+// Byte sizes of the BF16 operand images.
+constexpr int BYTES_X = TILE * KIN * 2;      // 12 KB
+constexpr int BYTES_H = TILE * HID * 2;      // 32 KB
+constexpr int BYTES_W1 = HID * KIN * 2;      // [128][48]
+constexpr int BYTES_W2 = HID * HID * 2;      // [128][128]
+constexpr int BYTES_W3 = NOUTP * HID * 2;    // [48][128]
+constexpr int BYTES_W3T = HID * NOUTP * 2;   // [128][48]
+constexpr int BYTES_W2T = HID * HID * 2;     // [128][128]
+constexpr int BYTES_DY = TILE * NOUTP * 2;   // [128][48]
+
+// Byte offset of element (r, k) in a [rows][K] BF16 operand image (K a multiple of 8).
+__host__ __device__ constexpr int elem_off(int r, int k, int K) {
+    return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+    return *reinterpret_cast<const uint32_t*>(&v);
+}
+
+// Store 8 consecutive values (columns k0..k0+7, k0 a multiple of 8) of row r into an image.
+__device__ __forceinline__ void store_row8(char* img, int r, int k0, int K, const float* v) {
+    uint4 q;
+    q.x = pack_bf16x2(v[0], v[1]);
+    q.y = pack_bf16x2(v[2], v[3]);
+    q.z = pack_bf16x2(v[4], v[5]);
+    q.w = pack_bf16x2(v[6], v[7]);
+    *reinterpret_cast<uint4*>(img + elem_off(r, k0, K)) = q;
+}
+
+// D = A[128][K] x B[N][K]^T, both K-major images; issued by one thread.
+__device__ __forceinline__ void mma_kmajor(uint32_t d, const char* A, const char* B, int K, int N) {
+    const uint32_t idesc = tc::idesc_bf16(128, N, 0, 0);
+    const uint32_t sbo = (uint32_t)(K / 8) * 128u;
+    for (int ks = 0; ks < K / 16; ++ks)
+        tc::mma_bf16(d, tc::smem_desc(A + ks * 256, 128u, sbo), tc::smem_desc(B + ks * 256, 128u, sbo),
+                     idesc, ks > 0 ? 1u : 0u);
+}
+
+// D[M=128][N] = sum over the 128 samples s of A[s][m] B[s][n]: A is a [128][FA] sample-major image
+// (FA = 128), B a [128][FB] sample-major image (first N of FB features); both read MN-major.
+__device__ __forceinline__ void mma_mnmajor(uint32_t d, const char* A, int FA, const char* B, int FB, int N) {
+    const uint32_t idesc = tc::idesc_bf16(128, N, 1, 1);
+    const uint32_t lboa = (uint32_t)(FA / 8) * 128u, lbob = (uint32_t)(FB / 8) * 128u;
+    for (int ks = 0; ks < TILE / 16; ++ks)
+        tc::mma_bf16(d, tc::smem_desc(A + ks * 2 * (int)lboa, lboa, 128u),
+                     tc::smem_desc(B + ks * 2 * (int)lbob, lbob, 128u), idesc, ks > 0 ? 1u : 0u);
+}
+
+// TMEM address of this warp's 32 lanes at column col (warp w of a 4-warp group owns lanes 32w..).
+__device__ __forceinline__ uint32_t tmem_lane_addr(uint32_t base, int warp, int col) {
+    return base + ((uint32_t)(32 * (warp & 3)) << 16) + (uint32_t)col;
+}
+
+// Copy nbytes (multiple of 16) from global to shared memory with the whole block.
+__device__ __forceinline__ void copy_to_smem(char* dst, const char* src, int nbytes) {
+    const uint4* s = reinterpret_cast<const uint4*>(src);
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    for (int k = threadIdx.x; k < nbytes / 16; k += blockDim.x) d[k] = __ldg(s + k);
+}
+
+}  // namespace mlp
+}  // namespace lbg

@@ -300,37 +300,40 @@ __device__ __forceinline__ bool bad_positive32(float v) {
 
 }  // namespace split32
 
-// One fused FP32-deviation step of site (x, y) with exact-split FP32 moment accumulation and an
-// FP32 projection residual (no FP64 arithmetic except on the six wall rows). Flag bits: 1 =
-// non-finite or non-positive density/temperature, 2 = a deviation outside the exact-split range.
-__device__ __forceinline__ void fp32split_site(const float* __restrict__ src, float* __restrict__ dst,
-                                               const StepParams& P, int x, int y,
-                                               int* __restrict__ flag) {
+// Pre-collision state of one site for the exact-split path: exact hi/mid sums, rounded lo sums,
+// and the FP32 macroscopic fields derived from them.
+struct SplitPre {
+    split32::Part h, m, l;
+    float s0, rho, ux, uy, T;
+};
+
+// Sums and fields of the pulled deviations d; sets flag bit 1 (non-finite / non-positive density
+// or temperature) or 2 (a deviation outside the exact-split range).
+__device__ __forceinline__ void split_pre(const float* d, const StepParams& P, SplitPre& s,
+                                          int* __restrict__ flag) {
     using namespace split32;
-    const int Lx = P.Lx, Ly = P.Ly;
-    const long long plane = P.plane;
-
-    float d[NPOP];
-    Pull32<NPOP - 1>::run(src, d, x, y, Lx, Ly, P.y_periodic, plane);
     const float dmax = MaxAbs<NPOP - 1>::run(d);
-
-    Part h0, m0, l0;
-    split_sums(d, h0, m0, l0);
-    const float s0 = (h0.s0 + m0.s0) + l0.s0;
-    const float sx = (h0.sx + m0.sx) + l0.sx;
-    const float sy = (h0.sy + m0.sy) + l0.sy;
-    const float se = (h0.se + m0.se) + l0.se;
+    split_sums(d, s.h, s.m, s.l);
+    s.s0 = (s.h.s0 + s.m.s0) + s.l.s0;
+    const float sx = (s.h.sx + s.m.sx) + s.l.sx;
+    const float sy = (s.h.sy + s.m.sy) + s.l.sy;
+    const float se = (s.h.se + s.m.se) + s.l.se;
     const float r = (float)P.r, r2 = (float)P.r2;
-    const float rho = 1.0f + s0;
-    const float inv = 1.0f / rho;
-    const float ux = r * sx * inv, uy = r * sy * inv;
+    s.rho = 1.0f + s.s0;
+    const float inv = 1.0f / s.rho;
+    s.ux = r * sx * inv;
+    s.uy = r * sy * inv;
     // rho (u^2 + D T) = D + r^2 se  (sum w xi^2 = D)
-    const float T = 0.5f * (fmaf(r2, se, 2.0f) * inv - (ux * ux + uy * uy));
-    if (bad_positive32(rho) || bad_positive32(T) || !(dmax < RANGE)) atomicOr(flag, !(dmax < RANGE) ? 2 : 1);
+    s.T = 0.5f * (fmaf(r2, se, 2.0f) * inv - (s.ux * s.ux + s.uy * s.uy));
+    if (bad_positive32(s.rho) || bad_positive32(s.T) || !(dmax < RANGE))
+        atomicOr(flag, !(dmax < RANGE) ? 2 : 1);
+}
 
-    // shifted equilibrium (forcing) and FP32 collide
-    const float uxs = ux + (float)P.tgx, uys = uy + (float)P.tgy;
-    const float th = (T + (float)P.dT_force) - 1.0f;
+// FP32 BGK relaxation of d (in place) toward the shifted Hermite equilibrium of s.
+__device__ __forceinline__ void split_collide(float* d, const StepParams& P, const SplitPre& s) {
+    const float r = (float)P.r;
+    const float uxs = s.ux + (float)P.tgx, uys = s.uy + (float)P.tgy;
+    const float th = (s.T + (float)P.dT_force) - 1.0f;
     const float u2 = uxs * uxs + uys * uys;
     const float a00m1 = u2 * fmaf(u2, 0.125f, -0.5f);
     const float a20 = fmaf(u2, -0.25f, 0.5f);
@@ -339,44 +342,56 @@ __device__ __forceinline__ void fp32split_site(const float* __restrict__ src, fl
     const float omega = (float)P.omega;
     float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], Wd[NSHELL];
 #pragma unroll
-    for (int s = 0; s < NSHELL; ++s) {
-        A0m1[s] = fmaf((float)P.sh[s].gamma, th2,
-                       fmaf((float)P.sh[s].beta, thu2, fmaf((float)P.sh[s].alpha, th, a00m1)));
-        A2[s] = fmaf((float)P.sh[s].delta, th, a20);
-        B1c[s] = fmaf((float)P.sh[s].eps, th, b10);
-        Wd[s] = omega * (float)P.sh[s].w;
+    for (int k = 0; k < NSHELL; ++k) {
+        A0m1[k] = fmaf((float)P.sh[k].gamma, th2,
+                       fmaf((float)P.sh[k].beta, thu2, fmaf((float)P.sh[k].alpha, th, a00m1)));
+        A2[k] = fmaf((float)P.sh[k].delta, th, a20);
+        B1c[k] = fmaf((float)P.sh[k].eps, th, b10);
+        Wd[k] = omega * (float)P.sh[k].w;
     }
-    const float drho = s0;
+    const float drho = s.s0;
     const float omc = (float)P.omc;
     d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
     Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, Wd, drho, omc);
+}
 
-    // projection residual R = target - sums of the FP32 results, target = pre sums + gravity:
-    //   sum d' = sum d,  sum d' c = sum d c + rho g / r,  sum d' |c|^2 = sum d |c|^2 + rho (2 u.g + g^2) / r^2
+// Project candidate post-collision deviations d (in place) onto the exact post-collision moments:
+// sum d' = sum d, sum d' c = sum d c + rho g / r, sum d' |c|^2 = sum d |c|^2 + rho (2 u.g + g^2) / r^2,
+// with the weighted least-norm correction d_i += w_i (l0 + lx c_x + ly c_y + le |c|^2). The
+// residual is formed from exact hi/mid differences (same quanta before and after).
+__device__ __forceinline__ void split_project(float* d, const StepParams& P, const SplitPre& s) {
+    using namespace split32;
     Part h1, m1, l1;
     split_sums(d, h1, m1, l1);
+    const float r = (float)P.r, r2 = (float)P.r2;
     const float gx = (float)P.gx, gy = (float)P.gy;
     const float rinv = 1.0f / r;
-    const float R0 = (h0.s0 - h1.s0) + ((m0.s0 - m1.s0) + (l0.s0 - l1.s0));
-    const float Rx = (h0.sx - h1.sx) + ((m0.sx - m1.sx) + (l0.sx - l1.sx)) + rho * gx * rinv;
-    const float Ry = (h0.sy - h1.sy) + ((m0.sy - m1.sy) + (l0.sy - l1.sy)) + rho * gy * rinv;
-    const float Re = (h0.se - h1.se) + ((m0.se - m1.se) + (l0.se - l1.se)) +
-                     rho * (2.0f * (ux * gx + uy * gy) + gx * gx + gy * gy) * (rinv * rinv);
-    // weighted least-norm correction d_i += w_i (l0 + lx c_x + ly c_y + le |c|^2)
+    const float R0 = (s.h.s0 - h1.s0) + ((s.m.s0 - m1.s0) + (s.l.s0 - l1.s0));
+    const float Rx = (s.h.sx - h1.sx) + ((s.m.sx - m1.sx) + (s.l.sx - l1.sx)) + s.rho * gx * rinv;
+    const float Ry = (s.h.sy - h1.sy) + ((s.m.sy - m1.sy) + (s.l.sy - l1.sy)) + s.rho * gy * rinv;
+    const float Re = (s.h.se - h1.se) + ((s.m.se - m1.se) + (s.l.se - l1.se)) +
+                     s.rho * (2.0f * (s.ux * gx + s.uy * gy) + gx * gx + gy * gy) * (rinv * rinv);
     const float lam0 = 2.0f * R0 - 0.5f * r2 * Re;
     const float lame = r2 * (0.25f * r2 * Re - 0.5f * R0);
     const float lamx = r2 * Rx, lamy = r2 * Ry;
-
-    const long long dsto = (long long)(y + HALO) * Lx + x;
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) {
         const float corr = fmaf(lame, (float)shell_c2(shell_of(i)),
                                 fmaf(lamx, (float)cx_of(i), fmaf(lamy, (float)cy_of(i), lam0)));
-        __stcs(dst + (long long)i * plane + dsto, fmaf((float)shell_w(shell_of(i)), corr, d[i]));
+        d[i] = fmaf((float)shell_w(shell_of(i)), corr, d[i]);
     }
+}
 
+// Store a site's deviations and, on wall rows, the wall halo rows (rest equilibrium at the wall
+// temperature with the summed density; FP64 on the six wall rows only).
+__device__ __forceinline__ void split_store(float* __restrict__ dst, const StepParams& P, int x,
+                                            int y, const float* d, float s0) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const long long plane = P.plane;
+    const long long dsto = (long long)(y + HALO) * Lx + x;
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) __stcs(dst + (long long)i * plane + dsto, d[i]);
     if (!P.y_periodic) {
-        // wall halo deviations rho w_wall - w from the summed density (FP64 on wall rows only)
         const double rho_d = 1.0 + (double)s0;
         if (y < HALO) {
             const long long o = (long long)(HALO - 1 - y) * Lx + x;
@@ -393,6 +408,21 @@ __device__ __forceinline__ void fp32split_site(const float* __restrict__ src, fl
                        (float)fma(rho_d, P.wall_top[i], -shell_w(shell_of(i))));
         }
     }
+}
+
+// One fused FP32-deviation step of site (x, y) with exact-split FP32 moment accumulation and an
+// FP32 projection residual (no FP64 arithmetic except on the six wall rows). Flag bits: 1 =
+// non-finite or non-positive density/temperature, 2 = a deviation outside the exact-split range.
+__device__ __forceinline__ void fp32split_site(const float* __restrict__ src, float* __restrict__ dst,
+                                               const StepParams& P, int x, int y,
+                                               int* __restrict__ flag) {
+    float d[NPOP];
+    Pull32<NPOP - 1>::run(src, d, x, y, P.Lx, P.Ly, P.y_periodic, P.plane);
+    SplitPre s;
+    split_pre(d, P, s, flag);
+    split_collide(d, P, s);
+    split_project(d, P, s);
+    split_store(dst, P, x, y, d, s.s0);
 }
 
 }  // namespace lbg

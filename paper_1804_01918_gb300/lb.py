@@ -94,6 +94,21 @@ def lib() -> C.CDLL:
         L.lb_ensemble_get_populations.argtypes = [vp, C.c_int, vp]
         L.lb_ensemble_free.argtypes = [vp]
         L.lb_ensemble_free.restype = None
+        fp = C.POINTER(C.c_float)
+        L.lb_mlp_create.argtypes = [C.c_uint64, C.POINTER(vp)]
+        L.lb_mlp_free.argtypes = [vp]
+        L.lb_mlp_free.restype = None
+        L.lb_mlp_get_params.argtypes = [vp, vp, vp]
+        L.lb_mlp_set_params.argtypes = [vp, vp, vp]
+        L.lb_mlp_eval.argtypes = [vp, vp, vp, C.c_int, vp]
+        L.lb_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_double), vp, vp]
+        L.lb_mlp_train.argtypes = [vp, vp, vp, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_uint64,
+                                   vp, vp]
+        L.lb_collect_pairs.argtypes = [vp, vp, C.c_int, vp, vp]
+        L.lb_set_collide_learned.argtypes = [vp, vp, C.c_double, C.c_int]
+        L.lb_set_collide_plain.argtypes = [vp]
+        L.lb_learned_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                       C.POINTER(C.c_double)]
         _lib = L
     return _lib
 
@@ -270,11 +285,92 @@ class Lattice:
         check(lib().lb_steps_done(self._ctx, C.byref(n)), "lb_steps_done")
         return n.value
 
+    def collect_pairs(self, sites, pre, post) -> None:
+        """Training pairs of the current state for the given site indices (torch int32 CUDA tensor
+        of y * Lx + x) into torch float32 CUDA tensors pre, post of shape [n, 37] (async)."""
+        n = int(sites.numel())
+        check(lib().lb_collect_pairs(self._ctx, sites.data_ptr(), n, pre.data_ptr(), post.data_ptr()),
+              "lb_collect_pairs")
+
+    def set_collide_learned(self, net, bound: float = 1e-4, check_every: int = 1) -> None:
+        self._net = net  # keep the network alive while it is in use
+        check(lib().lb_set_collide_learned(self._ctx, net._ptr, float(bound), int(check_every)),
+              "lb_set_collide_learned")
+
+    def set_collide_plain(self) -> None:
+        check(lib().lb_set_collide_plain(self._ctx), "lb_set_collide_plain")
+        self._net = None
+
+    def learned_stats(self):
+        a, b, r = C.c_longlong(), C.c_longlong(), C.c_double()
+        check(lib().lb_learned_stats(self._ctx, C.byref(a), C.byref(b), C.byref(r)), "lb_learned_stats")
+        return {"tiles_checked": a.value, "tiles_fallback": b.value, "max_residual": r.value}
+
     def close(self) -> None:
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().lb_free(self._ctx)
             self._ctx = C.c_void_p()
         self._ws = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_NPARAM = 26149
+MLP_TILE = 128
+
+
+class MLP:
+    """The learned collide's network (include/lb_learned.h), device-resident."""
+
+    def __init__(self, seed: int = 0):
+        self._ptr = C.c_void_p()
+        check(lib().lb_mlp_create(C.c_uint64(seed), C.byref(self._ptr)), "lb_mlp_create")
+
+    def get_params(self):
+        p = np.empty(MLP_NPARAM, np.float32)
+        nrm = np.empty((4, 37), np.float32)
+        check(lib().lb_mlp_get_params(self._ptr, p.ctypes.data, nrm.ctypes.data), "lb_mlp_get_params")
+        return p, nrm
+
+    def set_params(self, params, norm=None) -> None:
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == MLP_NPARAM
+        nrm = None if norm is None else np.ascontiguousarray(norm, dtype=np.float32)
+        check(lib().lb_mlp_set_params(self._ptr, p.ctypes.data, None if nrm is None else nrm.ctypes.data),
+              "lb_mlp_set_params")
+
+    def eval(self, x, y, stream=None) -> None:
+        """y = network(x) for torch float32 CUDA tensors [n, 37], n a multiple of 128."""
+        sh = None if stream is None else stream.cuda_stream
+        check(lib().lb_mlp_eval(self._ptr, x.data_ptr(), y.data_ptr(), int(x.shape[0]), sh), "lb_mlp_eval")
+
+    def loss_grad(self, x, t, stream=None):
+        """(loss, gradient[NPARAM]) of the mean squared error on normalised inputs/targets."""
+        sh = None if stream is None else stream.cuda_stream
+        loss = C.c_double()
+        g = np.empty(MLP_NPARAM, np.float32)
+        check(lib().lb_mlp_loss_grad(self._ptr, x.data_ptr(), t.data_ptr(), int(x.shape[0]), C.byref(loss),
+                                     g.ctypes.data, sh), "lb_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, pre, post, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, seed: int = 0,
+              stream=None):
+        """Train on device pairs [n, 37]; returns the per-epoch mean losses."""
+        sh = None if stream is None else stream.cuda_stream
+        losses = np.zeros(epochs, np.float32)
+        check(lib().lb_mlp_train(self._ptr, pre.data_ptr(), post.data_ptr(), int(pre.shape[0]), int(epochs),
+                                 int(batch), float(lr), C.c_uint64(seed), losses.ctypes.data, sh),
+              "lb_mlp_train")
+        return losses
+
+    def close(self) -> None:
+        if getattr(self, "_ptr", None) and self._ptr.value:
+            lib().lb_mlp_free(self._ptr)
+            self._ptr = C.c_void_p()
 
     def __del__(self):
         try:

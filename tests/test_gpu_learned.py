@@ -1,0 +1,164 @@
+"""GPU checks of the learned collide (include/lb_learned.h) against the CPU oracle MLP.
+
+The network's products run on tcgen05 tensor cores with BF16 operands and FP32 accumulation; the
+oracle mirrors the BF16 rounding points in FP64, so remaining differences come from FP32 vs FP64
+accumulation, FP32 GELU and rare BF16 rounding flips of hidden activations: the bar is 1e-2
+relative per output or gradient block.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+from paper_1804_01918_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+BLOCKS = [("W1", 0, 4736), ("b1", 4736, 4864), ("W2", 4864, 21248), ("b2", 21248, 21376),
+          ("W3", 21376, 26112), ("b3", 26112, 26149)]
+
+
+@pytest.fixture(scope="module")
+def L():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1804_01918_gb300 import build, lb
+    build.build()
+    return lb
+
+
+def dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).cuda()
+
+
+def test_forward_matches_oracle(L):
+    import torch
+    rng = np.random.default_rng(0)
+    p = omlp.init_params(3, scale=2.0).astype(np.float32)
+    net = L.MLP(seed=0)
+    net.set_params(p)
+    x = rng.standard_normal((384, 37)).astype(np.float32)
+    X = dev(x)
+    Y = torch.empty_like(X)
+    net.eval(X, Y)
+    torch.cuda.synchronize()
+    y = Y.cpu().numpy().astype(np.float64)
+    yref, _ = omlp.forward(p.astype(np.float64), x.astype(np.float64), bf16=True)
+    err = np.abs(y - yref) / np.abs(yref).max()
+    assert err.max() < 1e-2 and err.mean() < 1e-3, (err.max(), err.mean())
+    net.close()
+
+
+def test_gradients_match_oracle(L):
+    rng = np.random.default_rng(1)
+    p = omlp.init_params(5, scale=2.0).astype(np.float32)
+    net = L.MLP(seed=0)
+    net.set_params(p)
+    x = rng.standard_normal((256, 37)).astype(np.float32)
+    t = (0.5 * rng.standard_normal((256, 37))).astype(np.float32)
+    loss, g = net.loss_grad(dev(x), dev(t))
+    lref, gref = omlp.loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), bf16=True)
+    assert loss == pytest.approx(lref, rel=1e-3)
+    for name, a, b in BLOCKS:
+        rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
+        assert rel < 1e-2, (name, rel)
+    net.close()
+
+
+def collect_pairs(L, Lx=64, Ly=256, steps=24, every=3, seed=0, tau=0.9, R=2.0):
+    """Pairs (pre, post) of all sites of a Rayleigh-Taylor lattice every `every` steps."""
+    import torch
+    st = inputs.rayleigh_taylor(Lx, Ly, R=R, seed=seed)
+    lat = L.Lattice.from_fields(st, tau=tau, precision="fp32split")
+    n = Lx * Ly
+    sites = torch.arange(n, dtype=torch.int32, device="cuda")
+    pre, post = [], []
+    for k in range(steps // every):
+        a = torch.empty((n, 37), dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        with torch.cuda.stream(lat.stream):
+            lat.collect_pairs(sites, a, b)
+        lat.step(every)
+        pre.append(a)
+        post.append(b)
+    lat.sync()
+    lat.close()
+    return torch.cat(pre), torch.cat(post)
+
+
+def test_training_reduces_loss(L):
+    pre, post = collect_pairs(L)
+    net = L.MLP(seed=1)
+    losses = net.train(pre, post, epochs=4, batch=2048, lr=1e-3, seed=0)
+    assert np.all(np.isfinite(losses))
+    assert losses[-1] < 0.25 * losses[0], losses
+    net.close()
+
+
+def test_bound_zero_falls_back_everywhere_and_equals_plain(L):
+    st = inputs.rayleigh_taylor(64, 128, R=2.0, seed=2)
+    net = L.MLP(seed=2)
+    a = L.Lattice.from_fields(st, tau=0.9, precision="fp32split")
+    b = L.Lattice.from_fields(st, tau=0.9, precision="fp32split")
+    a.set_collide_learned(net, bound=0.0)
+    a.step(5)
+    b.step(5)
+    assert np.array_equal(a.get_populations(), b.get_populations())
+    s = a.learned_stats()
+    assert s["tiles_checked"] == 5 * (64 // 32) * (128 // 32) == s["tiles_fallback"]
+    a.close()
+    b.close()
+    net.close()
+
+
+def test_learned_step_keeps_conserved_moments(L):
+    """No fallback (infinite bound): the projection alone keeps mass, momentum and energy."""
+    Lx, Ly = 64, 64
+    st = inputs.random_state(Lx, Ly, seed=4, du=0.02, dT=0.1, drho=0.1)
+    pre, post = collect_pairs(L, Lx=64, Ly=64, steps=12, every=2)
+    net = L.MLP(seed=3)
+    net.train(pre, post, epochs=2, batch=1024)
+    lat = L.Lattice.from_fields(st, tau=0.8, y_periodic=True, precision="fp32split")
+    lat.set_collide_learned(net, bound=1e30)
+    cx, cy, w, r = L.velocity_set()
+    f0 = lat.get_populations()
+    lat.step(10)
+    f1 = lat.get_populations()
+    assert lat.learned_stats()["tiles_fallback"] == 0
+    xi2 = (r * cx) ** 2 + (r * cy) ** 2
+    for weight, scale in ((np.ones(37), 1.0), (r * cx, 1.0), (r * cy, 1.0), (xi2, 2.0)):
+        A = float(np.tensordot(weight, f0, 1).sum())
+        B = float(np.tensordot(weight, f1, 1).sum())
+        assert abs(A - B) <= 1e-7 * scale * Lx * Ly
+    lat.close()
+    net.close()
+
+
+def test_learned_collide_gain_report(L, orc):
+    """What the trained network gains: accuracy against the FP64 oracle and the fraction of tiles
+    it handles (the rest fall back to the plain collide), at the bound 1e-4."""
+    import time
+
+    import torch
+    pre, post = collect_pairs(L, steps=60, every=2)
+    net = L.MLP(seed=5)
+    losses = net.train(pre, post, epochs=6, batch=4096)
+    Lx, Ly, n = 64, 256, 40
+    st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=7)
+    lat = L.Lattice.from_fields(st, tau=0.9, precision="fp32split")
+    lat.set_collide_learned(net, bound=1e-4)
+    lat.step(n)
+    rho, _, _, T = lat.moments()
+    stats = lat.learned_stats()
+    f = orc.run(orc.init_fields(st), tau=0.9, nsteps=n, gy=st.gy, T_top=st.T_top, T_bottom=st.T_bottom)
+    orho, _, _, oT = orc.moments(f)
+    e_rho = np.linalg.norm(rho - orho) / np.linalg.norm(orho)
+    e_T = np.linalg.norm(T - oT) / np.linalg.norm(oT)
+    frac = 1.0 - stats["tiles_fallback"] / max(1, stats["tiles_checked"])
+    print(f"learned collide: final loss {losses[-1]:.3e}, tiles kept learned {frac:.3f}, "
+          f"max residual {stats['max_residual']:.2e}, rel L2 rho {e_rho:.2e} T {e_T:.2e}")
+    # every kept tile is within 1e-4 of the plain collide per step
+    assert e_rho < n * 1e-4 and e_T < n * 1e-4
+    lat.close()
+    net.close()
