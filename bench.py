@@ -257,6 +257,7 @@ def main():
     ap.add_argument("--no-forms", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-learned", action="store_true")
     ap.add_argument("--lattice", default=None,
                     help="LXxLY of a smaller case for profiling (default: the 2304x8192 workload)")
     ap.add_argument("--precision", choices=["fp64", "fp32dev", "fp32split"], default="fp64")
@@ -369,6 +370,14 @@ def main():
     forms = None
     if not args.no_forms and rank == 0:
         forms = measure_forms(lb, torch, np, st, stream, value / world)
+        net = None
+        if not args.no_learned:
+            forms["learned"], net = measure_learned(lb, torch, np, inputs, st, stream,
+                                                    forms["fp32split"]["mlups"])
+        for form, e in measure_accuracy(lb, np, st, stream, learned_net=net).items():
+            forms[form]["rel_l2_vs_fp64"] = e
+        if net is not None:
+            net.close()
         if not args.no_ensemble:
             forms["ensemble"] = measure_ensemble(lb, torch, np, inputs, value / world)
 
@@ -395,10 +404,8 @@ def main():
 
 
 def measure_forms(lb, torch, np, st, stream, fp64_mlups):
-    """The FP32-deviation forms on the same workload: MLUPS (device-timed, 1000 steps), HBM
-    roofline fraction, and relative L2 error of rho and T against the FP64 path at steps 100, 500
-    and 1000 (the FP64 path is the reference at this size; it matches the CPU oracle to 1e-12 in
-    the tests, including sampled sites of this very workload)."""
+    """MLUPS (device-timed, 1000 steps) and HBM fraction of both FP32-deviation forms on the bench
+    workload."""
     sites = LX * LY
     hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
     out = {}
@@ -418,30 +425,121 @@ def measure_forms(lb, torch, np, st, stream, fp64_mlups):
         gbs = FP32DEV_BYTES_PER_SITE * mlups * 1e6 / 1e9
         out[form] = {"mlups": round(mlups, 1), "speedup_vs_fp64": round(mlups / fp64_mlups, 3),
                      "hbm_gbs": round(gbs, 1), "hbm_frac": round(gbs / hbm, 4)}
-    # accuracy: all precisions from the same initial state, moments at 100/500/1000
+    return out
+
+
+def measure_accuracy(lb, np, st, stream, learned_net=None):
+    """Relative L2 error of rho and T of the FP32 forms (and of the learned collide) against the
+    FP64 path at steps 100, 500 and 1000, all from the same initial state. The FP64 path is the
+    reference at this size: it matches the CPU oracle to 1e-12 in the tests, including sampled
+    sites of this very workload."""
     lats = {form: lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision=form)
             for form in ("fp64", "fp32dev", "fp32split")}
+    compared = ["fp32dev", "fp32split"]
+    if learned_net is not None:
+        lats["learned"] = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32split")
+        lats["learned"].set_collide_learned(learned_net, bound=1e-4, check_every=1)
+        compared.append("learned")
     done = 0
-    errs = {"fp32dev": {}, "fp32split": {}}
+    errs = {form: {} for form in compared}
     for mark in (100, 500, 1000):
         for lat in lats.values():
             lat.step(mark - done)
         done = mark
         ra, _, _, Ta = lats["fp64"].moments()
-        for form in ("fp32dev", "fp32split"):
+        for form in compared:
             rb, _, _, Tb = lats[form].moments()
             errs[form][str(mark)] = {"rho": float(np.linalg.norm(rb - ra) / np.linalg.norm(ra)),
                                      "T": float(np.linalg.norm(Tb - Ta) / np.linalg.norm(Ta))}
     for lat in lats.values():
         lat.close()
-    for form in ("fp32dev", "fp32split"):
-        out[form]["rel_l2_vs_fp64"] = errs[form]
-    return out
+    return errs
+
+
+def collect_training_pairs(lb, torch, np, inputs, total=10_000_000, seed=0):
+    """(pre, post) FP32-deviation pairs from the plain collide, as configured: every site of the
+    64x256 Rayleigh-Taylor run at each of its 100 steps (1.64 M pairs), and the rest sampled at
+    random sites of the 2304x8192 run every 100 of its 1000 steps (FP32 storage, exact-split
+    accumulation)."""
+    pre, post = [], []
+    st1 = inputs.rayleigh_taylor(64, 256, R=RATIO, seed=seed)
+    lat = lb.Lattice.from_fields(st1, tau=TAU, precision="fp32split")
+    sites = torch.arange(64 * 256, dtype=torch.int32, device="cuda")
+    for _ in range(100):
+        a = torch.empty((sites.numel(), NPOP), dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        with torch.cuda.stream(lat.stream):
+            lat.collect_pairs(sites, a, b)
+        lat.step(1)
+        pre.append(a)
+        post.append(b)
+    lat.sync()
+    lat.close()
+    remaining = total - sum(a.shape[0] for a in pre)
+    st3 = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=seed + 1)
+    lat = lb.Lattice.from_fields(st3, tau=TAU, precision="fp32split")
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    per = remaining // 10
+    for k in range(10):
+        m = per if k < 9 else remaining - 9 * per
+        idx = torch.randint(0, LX * LY, (m,), dtype=torch.int32, device="cuda", generator=gen)
+        a = torch.empty((m, NPOP), dtype=torch.float32, device="cuda")
+        b = torch.empty_like(a)
+        torch.cuda.current_stream().synchronize()
+        with torch.cuda.stream(lat.stream):
+            lat.collect_pairs(idx, a, b)
+        lat.step(100)
+        pre.append(a)
+        post.append(b)
+    lat.sync()
+    lat.close()
+    return torch.cat(pre), torch.cat(post)
+
+
+def measure_learned(lb, torch, np, inputs, st, stream, fp32split_mlups, epochs=20, steps=1000):
+    """Learned collide at the bench size: train the MLP (20 epochs, batch 4096, Adam 1e-3) on 10 M
+    pairs, then run the learned LB step (bound 1e-4 per 32x32 tile, checked every step) and report
+    its MLUPS, the fraction of tiles kept on the network and its error against the FP64 path."""
+    t0 = time.perf_counter()
+    pre, post = collect_training_pairs(lb, torch, np, inputs)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = lb.MLP(seed=0)
+    t0 = time.perf_counter()
+    losses = net.train(pre, post, epochs=epochs, batch=4096, lr=1e-3, seed=0)
+    t_train = time.perf_counter() - t0
+    npairs = int(pre.shape[0])
+    del pre, post
+    torch.cuda.empty_cache()
+    sites = LX * LY
+    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32split")
+    lat.set_collide_learned(net, bound=1e-4, check_every=1)
+    lat.step(10)
+    lat.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1)
+    lat.sync()
+    stats = lat.learned_stats()
+    lat.close()
+    mlups = sites * steps / (ms * 1e-3) / 1e6
+    kept = 1.0 - stats["tiles_fallback"] / max(1, stats["tiles_checked"])
+    out = {"mlups": round(mlups, 1), "speedup_vs_fp32split": round(mlups / fp32split_mlups, 3),
+           "tiles_kept_learned": round(kept, 4), "max_tile_residual": stats["max_residual"],
+           "bound": 1e-4, "check_every": 1, "train_pairs": npairs, "epochs": epochs,
+           "final_loss": float(losses[-1]), "first_epoch_loss": float(losses[0]),
+           "train_s": round(t_train, 1), "pair_generation_s": round(t_data, 1),
+           "train_samples_per_s": round(npairs * epochs / t_train, 0)}
+    return out, net
 
 
 def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300):
     """Batched ensemble: n seed-drawn Rayleigh-Taylor lattices (Lx uniform over multiples of 32 in
-    [128, 1024], Ly = 4 Lx, Atwood in [0.05, 0.5], tau in [0.6, 1.2]), FP32 storage (exact-split
+    [128, 1024], Ly = 4 Lx, Atwood in [0.05, 0.5], tau in [tau_min(A), 1.2]), FP32 storage (exact-split
     accumulation), autotuned tile shape, 100-step CUDA graphs; MLUPS = sum of sites x steps / s."""
     descs = inputs.ensemble_members(n, seed=seed)
     specs = []
