@@ -258,6 +258,11 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-learned", action="store_true")
+    ap.add_argument("--only", choices=["ensemble", "learned"], default=None,
+                    help="run only this form (profiling): the ensemble or the learned step")
+    ap.add_argument("--members", type=int, default=64, help="ensemble members (with --only ensemble)")
+    ap.add_argument("--pairs", type=int, default=10_000_000, help="training pairs (with --only learned)")
+    ap.add_argument("--epochs", type=int, default=20, help="training epochs (with --only learned)")
     ap.add_argument("--lattice", default=None,
                     help="LXxLY of a smaller case for profiling (default: the 2304x8192 workload)")
     ap.add_argument("--precision", choices=["fp64", "fp32dev", "fp32split"], default="fp64")
@@ -269,6 +274,8 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.only:
+        return run_only(args)
 
     import numpy as np
     import torch
@@ -403,6 +410,25 @@ def main():
     return 0
 
 
+def run_only(args):
+    """One form alone, for profiling: prints its measurement as one JSON line."""
+    import numpy as np
+    import torch
+
+    from paper_1804_01918_gb300 import build as pkg_build
+    from paper_1804_01918_gb300 import inputs, lb
+    pkg_build.build()
+    if args.only == "ensemble":
+        out = measure_ensemble(lb, torch, np, inputs, 1.0, n=args.members, steps=args.steps)
+    else:
+        st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=0)
+        out, net = measure_learned(lb, torch, np, inputs, st, torch.cuda.Stream(), 1.0,
+                                   epochs=args.epochs, steps=args.steps, pairs=args.pairs)
+        net.close()
+    print(json.dumps({"only": args.only, "config": {"Lx": LX, "Ly": LY}, **out}), flush=True)
+    return 0
+
+
 def measure_forms(lb, torch, np, st, stream, fp64_mlups):
     """MLUPS (device-timed, 1000 steps) and HBM fraction of both FP32-deviation forms on the bench
     workload."""
@@ -475,7 +501,7 @@ def collect_training_pairs(lb, torch, np, inputs, total=10_000_000, seed=0):
         post.append(b)
     lat.sync()
     lat.close()
-    remaining = total - sum(a.shape[0] for a in pre)
+    remaining = max(1280, total - sum(a.shape[0] for a in pre))
     st3 = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=seed + 1)
     lat = lb.Lattice.from_fields(st3, tau=TAU, precision="fp32split")
     gen = torch.Generator(device="cuda")
@@ -497,12 +523,13 @@ def collect_training_pairs(lb, torch, np, inputs, total=10_000_000, seed=0):
     return torch.cat(pre), torch.cat(post)
 
 
-def measure_learned(lb, torch, np, inputs, st, stream, fp32split_mlups, epochs=20, steps=1000):
+def measure_learned(lb, torch, np, inputs, st, stream, fp32split_mlups, epochs=20, steps=1000,
+                    pairs=10_000_000):
     """Learned collide at the bench size: train the MLP (20 epochs, batch 4096, Adam 1e-3) on 10 M
     pairs, then run the learned LB step (bound 1e-4 per 32x32 tile, checked every step) and report
     its MLUPS, the fraction of tiles kept on the network and its error against the FP64 path."""
     t0 = time.perf_counter()
-    pre, post = collect_training_pairs(lb, torch, np, inputs)
+    pre, post = collect_training_pairs(lb, torch, np, inputs, total=pairs)
     torch.cuda.synchronize()
     t_data = time.perf_counter() - t0
     net = lb.MLP(seed=0)

@@ -68,6 +68,9 @@ __host__ __device__ constexpr int shell_of(int i) { return i <= NPAIR ? shellh(i
 // expansion, regrouped by powers of a.
 struct ShellCoef {
     double w, alpha, beta, gamma, delta, eps;
+    // the same coefficients times w (and w/24, w/6): the FP64 step folds the prefactor
+    // w rho / tau into each shell's coefficients so that a pair costs one multiply and 7 FMAs
+    double aw, bw, gw, dw, ew, w24, w6;
 };
 
 // Everything a step kernel needs, passed by value as a kernel parameter.

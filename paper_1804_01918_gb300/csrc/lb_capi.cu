@@ -111,6 +111,13 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh[s].gamma = (X * X - 2.0 * (DIM + 2.0) * X + DIM * (DIM + 2.0)) / 8.0;
         sp.sh[s].delta = (X - DIM - 4.0) / 4.0;
         sp.sh[s].eps = (X - DIM - 2.0) / 2.0;
+        sp.sh[s].aw = sp.sh[s].alpha * sp.sh[s].w;
+        sp.sh[s].bw = sp.sh[s].beta * sp.sh[s].w;
+        sp.sh[s].gw = sp.sh[s].gamma * sp.sh[s].w;
+        sp.sh[s].dw = sp.sh[s].delta * sp.sh[s].w;
+        sp.sh[s].ew = sp.sh[s].eps * sp.sh[s].w;
+        sp.sh[s].w24 = sp.sh[s].w / 24.0;
+        sp.sh[s].w6 = sp.sh[s].w / 6.0;
     }
     // rest equilibrium per unit density: w (1 + alpha theta + gamma theta^2) at u = 0
     for (int i = 0; i < NPOP; ++i) {

@@ -108,12 +108,15 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
     return m;
 }
 
-// Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S toward the equilibrium.
+// Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S. With the prefactor
+// W = w rho / tau folded into the shell coefficients (WA0 = W A0, WA2 = W A2, WB1 = W B1,
+// W24 = W / 24, W6 = W / 6):  W E = WA0 + a^2 (WA2 + a^2 W24),  W O = a (WB1 + a^2 W6),
+// W f_eq(+-c) = W E +- W O, and f' = (1 - 1/tau) f + W f_eq -- one multiply (a^2) and 7 FMAs.
 template <int I>
 __device__ __forceinline__ void relax_pair(const double* f, double* __restrict__ dst, long long dsto,
                                            long long plane, double urx, double ury,
-                                           const double* A0, const double* A2, const double* B1,
-                                           const double* W, double omc) {
+                                           const double* WA0, const double* WA2, const double* WB1,
+                                           const double* W24, const double* W6, double omc) {
     constexpr int S = shellh(I);
     constexpr double cx = (double)cxh(I);
     constexpr double cy = (double)cyh(I);
@@ -125,29 +128,30 @@ __device__ __forceinline__ void relax_pair(const double* f, double* __restrict__
     else
         a = fma(cx, urx, cy * ury);
     const double a2 = a * a;
-    const double e = fma(a2, fma(a2, 1.0 / 24.0, A2[S]), A0[S]);
-    const double o = a * fma(a2, 1.0 / 6.0, B1[S]);
-    const double we = W[S] * e;
-    const double wo = W[S] * o;
-    __stcs(dst + plane_off(I, plane) + dsto, fma(omc, f[I], we + wo));
-    __stcs(dst + plane_off(I + NPAIR, plane) + dsto, fma(omc, f[I + NPAIR], we - wo));
+    const double we = fma(a2, fma(a2, W24[S], WA2[S]), WA0[S]);
+    const double q = fma(a2, W6[S], WB1[S]);
+    const double gp = fma(a, q, we);
+    const double gm = fma(-a, q, we);
+    __stcs(dst + plane_off(I, plane) + dsto, fma(omc, f[I], gp));
+    __stcs(dst + plane_off(I + NPAIR, plane) + dsto, fma(omc, f[I + NPAIR], gm));
 }
 
 template <int I>
 struct RelaxAll {
     __device__ __forceinline__ static void run(const double* f, double* __restrict__ dst,
                                                long long dsto, long long plane, double urx,
-                                               double ury, const double* A0, const double* A2,
-                                               const double* B1, const double* W, double omc) {
-        RelaxAll<I - 1>::run(f, dst, dsto, plane, urx, ury, A0, A2, B1, W, omc);
-        relax_pair<I>(f, dst, dsto, plane, urx, ury, A0, A2, B1, W, omc);
+                                               double ury, const double* WA0, const double* WA2,
+                                               const double* WB1, const double* W24, const double* W6,
+                                               double omc) {
+        RelaxAll<I - 1>::run(f, dst, dsto, plane, urx, ury, WA0, WA2, WB1, W24, W6, omc);
+        relax_pair<I>(f, dst, dsto, plane, urx, ury, WA0, WA2, WB1, W24, W6, omc);
     }
 };
 template <>
 struct RelaxAll<0> {
     __device__ __forceinline__ static void run(const double*, double*, long long, long long, double,
                                                double, const double*, const double*, const double*,
-                                               const double*, double) {}
+                                               const double*, const double*, double) {}
 };
 
 // Per-shell coefficients of the equilibrium at (theta, u2) scaled by prefactor W_s = wscale w_s.
@@ -165,6 +169,27 @@ __device__ __forceinline__ void shell_coefficients(const StepParams& P, double t
         A2[s] = fma(P.sh[s].delta, th, a20);
         B1[s] = fma(P.sh[s].eps, th, b10);
         W[s] = wscale * P.sh[s].w;
+    }
+}
+
+// The same coefficients already multiplied by W_s = rw w_s, from site quantities scaled by rw:
+//   W A0 = w rw a00 + (alpha w) rw theta + (beta w) rw theta u2 + (gamma w) rw theta^2, etc.
+__device__ __forceinline__ void shell_coefficients_scaled(const StepParams& P, double th, double u2,
+                                                          double rw, double* WA0, double* WA2,
+                                                          double* WB1, double* W24, double* W6) {
+    const double r0 = rw * fma(u2, fma(u2, 0.125, -0.5), 1.0);
+    const double r20 = rw * fma(u2, -0.25, 0.5);
+    const double r10 = rw * fma(u2, -0.5, 1.0);
+    const double r1 = rw * th;
+    const double ru = r1 * u2;
+    const double r2 = r1 * th;
+#pragma unroll
+    for (int s = 0; s < NSHELL; ++s) {
+        WA0[s] = fma(P.sh[s].gw, r2, fma(P.sh[s].bw, ru, fma(P.sh[s].aw, r1, P.sh[s].w * r0)));
+        WA2[s] = fma(P.sh[s].dw, r1, P.sh[s].w * r20);
+        WB1[s] = fma(P.sh[s].ew, r1, P.sh[s].w * r10);
+        W24[s] = rw * P.sh[s].w24;
+        W6[s] = rw * P.sh[s].w6;
     }
 }
 
@@ -189,12 +214,12 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
     const double uys = m.uy + P.tgy;
     const double th = (m.T + P.dT_force) - 1.0;
     const double u2 = uxs * uxs + uys * uys;
-    double A0[NSHELL], A2[NSHELL], B1[NSHELL], W[NSHELL];
-    shell_coefficients(P, th, u2, m.rho * P.omega, A0, A2, B1, W);
+    double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], W24[NSHELL], W6[NSHELL];
+    shell_coefficients_scaled(P, th, u2, m.rho * P.omega, WA0, WA2, WB1, W24, W6);
 
     const long long dsto = (long long)(y + HALO) * Lx + x;
-    __stcs(dst + dsto, fma(P.omc, f[0], W[0] * A0[0]));
-    RelaxAll<NPAIR>::run(f, dst, dsto, plane, P.r * uxs, P.r * uys, A0, A2, B1, W, P.omc);
+    __stcs(dst + dsto, fma(P.omc, f[0], WA0[0]));
+    RelaxAll<NPAIR>::run(f, dst, dsto, plane, P.r * uxs, P.r * uys, WA0, WA2, WB1, W24, W6, P.omc);
 
     if (!P.y_periodic) {
         // wall halo rows of dst from this row's density (collide conserves it)
