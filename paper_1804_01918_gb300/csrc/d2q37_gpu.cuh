@@ -73,6 +73,12 @@ struct ShellCoef {
     double aw, bw, gw, dw, ew, w24, w6;
 };
 
+// FP32 copies of the shell coefficients for the FP32 kernels (converting doubles on the device
+// would run on GB300's narrow FP64 pipe).
+struct ShellCoef32 {
+    float w, alpha, beta, gamma, delta, eps;
+};
+
 // Everything a step kernel needs, passed by value as a kernel parameter.
 struct StepParams {
     int Lx, Ly;
@@ -89,6 +95,9 @@ struct StepParams {
     ShellCoef sh[NSHELL];
     double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population
     double wall_top[NPOP]; // same at T_top
+    // FP32 copies of the scalars above and of the shell coefficients
+    float r_f, r2_f, omega_f, omc_f, gx_f, gy_f, tgx_f, tgy_f, dT_force_f, pad_f;
+    ShellCoef32 sh32[NSHELL];
 };
 
 }  // namespace lbg

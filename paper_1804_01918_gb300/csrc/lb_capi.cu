@@ -119,6 +119,23 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh[s].w24 = sp.sh[s].w / 24.0;
         sp.sh[s].w6 = sp.sh[s].w / 6.0;
     }
+    sp.r_f = (float)sp.r;
+    sp.r2_f = (float)sp.r2;
+    sp.omega_f = (float)sp.omega;
+    sp.omc_f = (float)sp.omc;
+    sp.gx_f = (float)sp.gx;
+    sp.gy_f = (float)sp.gy;
+    sp.tgx_f = (float)sp.tgx;
+    sp.tgy_f = (float)sp.tgy;
+    sp.dT_force_f = (float)sp.dT_force;
+    for (int s = 0; s < NSHELL; ++s) {
+        sp.sh32[s].w = (float)sp.sh[s].w;
+        sp.sh32[s].alpha = (float)sp.sh[s].alpha;
+        sp.sh32[s].beta = (float)sp.sh[s].beta;
+        sp.sh32[s].gamma = (float)sp.sh[s].gamma;
+        sp.sh32[s].delta = (float)sp.sh[s].delta;
+        sp.sh32[s].eps = (float)sp.sh[s].eps;
+    }
     // rest equilibrium per unit density: w (1 + alpha theta + gamma theta^2) at u = 0
     for (int i = 0; i < NPOP; ++i) {
         const ShellCoef& c = sp.sh[shell_of(i)];

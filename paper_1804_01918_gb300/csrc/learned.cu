@@ -106,6 +106,24 @@ __global__ void stats_kernel(const float* __restrict__ pre, const float* __restr
     for (int k = threadIdx.x; k < 4 * NIN; k += blockDim.x) atomicAdd(&acc[k], s[k]);
 }
 
+// Column sums over a warp: on return lane L holds the sum over the warp's 32 lanes of their v[L]
+// (v is overwritten). Butterfly transpose-reduce: at the stage of width s, lanes with bit s set
+// keep the upper half of their columns and exchange the lower half, so 31 shuffles suffice.
+__device__ __forceinline__ float warp_column_sums(float* v) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+        const bool upper = (lane & s) != 0;
+#pragma unroll
+        for (int k = 0; k < s; ++k) {
+            const float send = upper ? v[k] : v[k + s];
+            const float keep = upper ? v[k + s] : v[k];
+            v[k] = keep + __shfl_xor_sync(0xffffffffu, send, s);
+        }
+    }
+    return v[0];
+}
+
 // ------------------------------------------------------------------------------------------------
 // shared-memory plan of the training kernel
 // ------------------------------------------------------------------------------------------------
@@ -254,14 +272,23 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
                     const float e = (yv[j] + b3[j]) - tn[j];
                     lsum += e * e;
                     dy[j] = 2.0f * e * inv_count;
-                    atomicAdd(&gb[2 * HID + j], dy[j]);
                 } else {
                     dy[j] = 0.0f;
                 }
             }
 #pragma unroll
             for (int j = 0; j < NOUTP; j += 8) store_row8(sm + TR_DY, tid, j, NOUTP, dy + j);
-            atomicAdd(loss_sm, lsum);
+            // db3: warp column sums, then one shared atomic per column and warp
+            float cs[32];
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cs[j] = dy[j];
+            atomicAdd(&gb[2 * HID + (tid & 31)], warp_column_sums(cs));
+#pragma unroll
+            for (int j = 0; j < 32; ++j) cs[j] = j < NOUTP - 32 ? dy[32 + j] : 0.0f;
+            const float c2 = warp_column_sums(cs);
+            if ((tid & 31) < NOUTP - 32) atomicAdd(&gb[2 * HID + 32 + (tid & 31)], c2);
+            for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if ((tid & 31) == 0) atomicAdd(loss_sm, lsum);
         }
         sync_for_mma();
         issue_and_wait(3);
@@ -272,12 +299,10 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), z);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                v[j] *= gelu_grad(z[j] + b2[c + j]);
-                atomicAdd(&gb[HID + c + j], v[j]);
-            }
+            for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(z[j] + b2[c + j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
+            atomicAdd(&gb[HID + c + (tid & 31)], warp_column_sums(v));
         }
         {
             float g[NOUTP];
@@ -296,12 +321,10 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
             tc::tmem_ld32(tmem_lane_addr(tm, warp, c), z);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                v[j] *= gelu_grad(z[j] + b1[c + j]);
-                atomicAdd(&gb[c + j], v[j]);
-            }
+            for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(z[j] + b1[c + j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
+            atomicAdd(&gb[c + (tid & 31)], warp_column_sums(v));
         }
         {
             float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W2 + (size_t)tid * HID;  // row o

@@ -61,9 +61,23 @@ __host__ __device__ constexpr int elem_off(int r, int k, int K) {
     return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+// erf(x) by the rational approximation of Abramowitz & Stegun, Handbook of Mathematical Functions
+// (1964), eq. 7.1.26: erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2), t = 1 / (1 + p x), x >= 0,
+// |error| <= 1.5e-7, extended to x < 0 by oddness. The activations it feeds are rounded to
+// bfloat16 (relative 4e-3), so this error is invisible; it is several times cheaper than erff.
+__device__ __forceinline__ float erf_as(float x) {
+    const float ax = fabsf(x);
+    const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
+    const float poly =
+        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
+                 0.254829592f);
+    const float e = 1.0f - poly * __expf(-ax * ax);
+    return copysignf(e, x);
+}
+// GELU(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2;  GELU'(z) = Phi(z) + z phi(z).
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {

@@ -164,18 +164,18 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
     const float a20 = fmaf(u2f, -0.25f, 0.5f);
     const float b10 = fmaf(u2f, -0.5f, 1.0f);
     const float thu2 = thf * u2f, th2 = thf * thf;
-    const float omega = (float)P.omega;
+    const float omega = P.omega_f;
     float A0m1[NSHELL], A2[NSHELL], B1[NSHELL], Wd[NSHELL];
 #pragma unroll
     for (int s = 0; s < NSHELL; ++s) {
-        A0m1[s] = fmaf((float)P.sh[s].gamma, th2,
-                       fmaf((float)P.sh[s].beta, thu2, fmaf((float)P.sh[s].alpha, thf, a00m1)));
-        A2[s] = fmaf((float)P.sh[s].delta, thf, a20);
-        B1[s] = fmaf((float)P.sh[s].eps, thf, b10);
-        Wd[s] = omega * (float)P.sh[s].w;
+        A0m1[s] = fmaf(P.sh32[s].gamma, th2,
+                       fmaf(P.sh32[s].beta, thu2, fmaf(P.sh32[s].alpha, thf, a00m1)));
+        A2[s] = fmaf(P.sh32[s].delta, thf, a20);
+        B1[s] = fmaf(P.sh32[s].eps, thf, b10);
+        Wd[s] = omega * P.sh32[s].w;
     }
     const float drho = (float)pre.s0;
-    const float omc = (float)P.omc;
+    const float omc = P.omc_f;
     d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
     Collide32<NPAIR>::run(d, (float)(P.r * uxs), (float)(P.r * uys), A0m1, A2, B1, Wd, drho, omc);
 
@@ -318,7 +318,7 @@ __device__ __forceinline__ void split_pre(const float* d, const StepParams& P, S
     const float sx = (s.h.sx + s.m.sx) + s.l.sx;
     const float sy = (s.h.sy + s.m.sy) + s.l.sy;
     const float se = (s.h.se + s.m.se) + s.l.se;
-    const float r = (float)P.r, r2 = (float)P.r2;
+    const float r = P.r_f, r2 = P.r2_f;
     s.rho = 1.0f + s.s0;
     const float inv = 1.0f / s.rho;
     s.ux = r * sx * inv;
@@ -331,26 +331,26 @@ __device__ __forceinline__ void split_pre(const float* d, const StepParams& P, S
 
 // FP32 BGK relaxation of d (in place) toward the shifted Hermite equilibrium of s.
 __device__ __forceinline__ void split_collide(float* d, const StepParams& P, const SplitPre& s) {
-    const float r = (float)P.r;
-    const float uxs = s.ux + (float)P.tgx, uys = s.uy + (float)P.tgy;
-    const float th = (s.T + (float)P.dT_force) - 1.0f;
+    const float r = P.r_f;
+    const float uxs = s.ux + P.tgx_f, uys = s.uy + P.tgy_f;
+    const float th = (s.T + P.dT_force_f) - 1.0f;
     const float u2 = uxs * uxs + uys * uys;
     const float a00m1 = u2 * fmaf(u2, 0.125f, -0.5f);
     const float a20 = fmaf(u2, -0.25f, 0.5f);
     const float b10 = fmaf(u2, -0.5f, 1.0f);
     const float thu2 = th * u2, th2 = th * th;
-    const float omega = (float)P.omega;
+    const float omega = P.omega_f;
     float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], Wd[NSHELL];
 #pragma unroll
     for (int k = 0; k < NSHELL; ++k) {
-        A0m1[k] = fmaf((float)P.sh[k].gamma, th2,
-                       fmaf((float)P.sh[k].beta, thu2, fmaf((float)P.sh[k].alpha, th, a00m1)));
-        A2[k] = fmaf((float)P.sh[k].delta, th, a20);
-        B1c[k] = fmaf((float)P.sh[k].eps, th, b10);
-        Wd[k] = omega * (float)P.sh[k].w;
+        A0m1[k] = fmaf(P.sh32[k].gamma, th2,
+                       fmaf(P.sh32[k].beta, thu2, fmaf(P.sh32[k].alpha, th, a00m1)));
+        A2[k] = fmaf(P.sh32[k].delta, th, a20);
+        B1c[k] = fmaf(P.sh32[k].eps, th, b10);
+        Wd[k] = omega * P.sh32[k].w;
     }
     const float drho = s.s0;
-    const float omc = (float)P.omc;
+    const float omc = P.omc_f;
     d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
     Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, Wd, drho, omc);
 }
@@ -363,8 +363,8 @@ __device__ __forceinline__ void split_project(float* d, const StepParams& P, con
     using namespace split32;
     Part h1, m1, l1;
     split_sums(d, h1, m1, l1);
-    const float r = (float)P.r, r2 = (float)P.r2;
-    const float gx = (float)P.gx, gy = (float)P.gy;
+    const float r = P.r_f, r2 = P.r2_f;
+    const float gx = P.gx_f, gy = P.gy_f;
     const float rinv = 1.0f / r;
     const float R0 = (s.h.s0 - h1.s0) + ((s.m.s0 - m1.s0) + (s.l.s0 - l1.s0));
     const float Rx = (s.h.sx - h1.sx) + ((s.m.sx - m1.sx) + (s.l.sx - l1.sx)) + s.rho * gx * rinv;
