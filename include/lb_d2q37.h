@@ -50,7 +50,7 @@ typedef enum {
     LB_ERR_CUDA = 3,      /* a CUDA call failed; see lb_last_error() */
     LB_ERR_NONFINITE = 4, /* a site produced a non-finite or non-positive density or temperature */
     LB_ERR_STATE = 5,     /* call not valid in the context's current state */
-    LB_ERR_RANGE = 6      /* LB_FP32SPLIT: a deviation |f - w| reached 4, outside the exact-split
+    LB_ERR_RANGE = 6      /* LB_FP32SPLIT: a deviation |f - w| reached 1, outside the exact-split
                              accumulation range */
 } lb_status;
 
@@ -59,9 +59,10 @@ typedef enum {
     LB_FP32DEV = 1,  /* populations stored as FP32 deviations f - w; FP32 collide, FP64 moment
                         accumulation and FP64 conservation projection */
     LB_FP32SPLIT = 2 /* same storage and FP32 collide; the moment sums and the projection residual
-                        are accumulated by an exact three-way FP32 split (error-free transformation:
-                        hi and mid parts summed exactly, lo parts rounded at ~1e-12) instead of FP64,
-                        whose rate on GB300 is 1/64 of FP32 */
+                        are accumulated by an exact error-free split of each FP32 value into an
+                        integer multiple of 2^-22 (summed exactly in 32-bit integers) and a residual
+                        below 2^-23 (summed in FP32, error ~1e-10) instead of in FP64, whose rate on
+                        GB300 is 1/64 of FP32 */
 } lb_precision;
 
 typedef struct {

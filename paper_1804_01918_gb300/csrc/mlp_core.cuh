@@ -67,7 +67,7 @@ __host__ __device__ constexpr int elem_off(int r, int k, int K) {
 // bfloat16 (relative 4e-3), so this error is invisible; it is several times cheaper than erff.
 __device__ __forceinline__ float erf_as(float x) {
     const float ax = fabsf(x);
-    const float t = __frcp_rn(fmaf(0.3275911f, ax, 1.0f));
+    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));  // argument >= 1: no special cases
     const float poly =
         t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
                  0.254829592f);

@@ -227,59 +227,56 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
 namespace lbg {
 namespace split32 {
 
-// Exact three-way split of an FP32 value at fixed quanta (the ExtractScalar error-free
-// transformation of Rump, Ogita and Oishi, "Accurate floating-point summation part I", SIAM J.
-// Sci. Comput. 31, 2008): for |d| < 256,
-//   hi  = (d + B1) - B1, a multiple of 2^-14            (B1 = 1.5 * 2^9,  ulp(B1) = 2^-14)
-//   mid = (r + B2) - B2, r = d - hi, a multiple of 2^-27 (B2 = 1.5 * 2^-4, ulp(B2) = 2^-27)
-//   lo  = r - mid, |lo| <= 2^-28
-// and d = hi + mid + lo exactly. Sums of up to 216 |c|^2-weighted terms of hi (mid) parts stay
-// below 2^24 quanta while |d| < 4 -- so they are exact in FP32 -- and only the lo sums round
-// (error <= ~2e-12 absolute). The same quanta serve the pre- and post-collision sums, so their
-// differences (the projection residuals) are exact in the hi and mid parts as well.
-constexpr float B1 = 768.0f;
-constexpr float B2 = 0.09375f;
-constexpr float RANGE = 4.0f;  // |d| must stay below this for the hi sums to be exact
+// Exact accumulation of FP32 deviations by an error-free split at a fixed quantum q = 2^-22:
+// for |d| < 1, t = d + 3 lies in [2, 4), where the FP32 spacing is exactly q, so
+//   n = bits(t) - bits(3.0f) = rint(d / q)   (an integer, |n| < 2^22)
+//   r = d - (t - 3)                          (exact, |r| <= q / 2)
+// and d = n q + r exactly (the magic-number split of Rump, Ogita and Oishi's ExtractScalar, read
+// through the bit pattern). The n parts are summed as 32-bit integers -- exactly: |c|^2-weighted
+// sums stay below 216 x 2^22 < 2^31 -- and only the r parts are summed in FP32 (absolute error
+// <= ~6e-11). Pre- and post-collision sums use the same quantum, so their differences (the
+// projection residuals) are exact in the integer parts.
+constexpr float QB = 3.0f;
+constexpr float Q = 2.384185791015625e-07f;  // 2^-22
+constexpr float RANGE = 1.0f;                // |d| must stay below this for the split to be exact
 
 struct Part {
-    float s0, sx, sy, se;  // sum d, sum c_x d, sum c_y d, sum |c|^2 d (in lattice units)
+    int n0, nx, ny, ne;       // integer parts of sum d, sum c_x d, sum c_y d, sum |c|^2 d (units of q)
+    float r0, rx, ry, re;     // rounded sums of the residuals
 };
 
-__device__ __forceinline__ Part combine(const float* bx, const float* by) {
-    const float px1 = bx[4] + bx[2], px2 = bx[5] + bx[1], px3 = bx[6] + bx[0];
-    const float py1 = by[4] + by[2], py2 = by[5] + by[1], py3 = by[6] + by[0];
-    Part p;
-    p.s0 = ((bx[3] + px1) + px2) + px3;
-    p.sx = fmaf(3.0f, bx[6] - bx[0], fmaf(2.0f, bx[5] - bx[1], bx[4] - bx[2]));
-    p.sy = fmaf(3.0f, by[6] - by[0], fmaf(2.0f, by[5] - by[1], by[4] - by[2]));
-    p.se = fmaf(9.0f, px3, fmaf(4.0f, px2, px1)) + fmaf(9.0f, py3, fmaf(4.0f, py2, py1));
-    return p;
-}
-
-// The four moment sums of d[37] as exact hi and mid parts plus a rounded lo part.
-__device__ __forceinline__ void split_sums(const float* d, Part& hi, Part& mid, Part& lo) {
-    float hx[7], hy[7], mx[7], my[7], lx[7], ly[7];
+__device__ __forceinline__ void split_sums(const float* d, Part& p) {
+    int bx[7], by[7];
+    float rx[7], ry[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
-        hx[k] = hy[k] = mx[k] = my[k] = lx[k] = ly[k] = 0.0f;
+        bx[k] = by[k] = 0;
+        rx[k] = ry[k] = 0.0f;
     }
+    const int b3 = __float_as_int(QB);
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) {
-        const float h = __fsub_rn(__fadd_rn(d[i], B1), B1);
-        const float r = __fsub_rn(d[i], h);
-        const float m = __fsub_rn(__fadd_rn(r, B2), B2);
-        const float l = __fsub_rn(r, m);
+        const float t = __fadd_rn(d[i], QB);
+        const float r = __fsub_rn(d[i], __fsub_rn(t, QB));
+        const int n = __float_as_int(t) - b3;
         const int ix = cx_of(i) + 3, iy = cy_of(i) + 3;
-        hx[ix] += h;
-        hy[iy] += h;
-        mx[ix] += m;
-        my[iy] += m;
-        lx[ix] += l;
-        ly[iy] += l;
+        bx[ix] += n;
+        by[iy] += n;
+        rx[ix] += r;
+        ry[iy] += r;
     }
-    hi = combine(hx, hy);
-    mid = combine(mx, my);
-    lo = combine(lx, ly);
+    const int px1 = bx[4] + bx[2], px2 = bx[5] + bx[1], px3 = bx[6] + bx[0];
+    const int py1 = by[4] + by[2], py2 = by[5] + by[1], py3 = by[6] + by[0];
+    p.n0 = ((bx[3] + px1) + px2) + px3;
+    p.nx = 3 * (bx[6] - bx[0]) + 2 * (bx[5] - bx[1]) + (bx[4] - bx[2]);
+    p.ny = 3 * (by[6] - by[0]) + 2 * (by[5] - by[1]) + (by[4] - by[2]);
+    p.ne = (9 * px3 + 4 * px2 + px1) + (9 * py3 + 4 * py2 + py1);
+    const float qx1 = rx[4] + rx[2], qx2 = rx[5] + rx[1], qx3 = rx[6] + rx[0];
+    const float qy1 = ry[4] + ry[2], qy2 = ry[5] + ry[1], qy3 = ry[6] + ry[0];
+    p.r0 = ((rx[3] + qx1) + qx2) + qx3;
+    p.rx = fmaf(3.0f, rx[6] - rx[0], fmaf(2.0f, rx[5] - rx[1], rx[4] - rx[2]));
+    p.ry = fmaf(3.0f, ry[6] - ry[0], fmaf(2.0f, ry[5] - ry[1], ry[4] - ry[2]));
+    p.re = fmaf(9.0f, qx3, fmaf(4.0f, qx2, qx1)) + fmaf(9.0f, qy3, fmaf(4.0f, qy2, qy1));
 }
 
 template <int I>
@@ -303,7 +300,7 @@ __device__ __forceinline__ bool bad_positive32(float v) {
 // Pre-collision state of one site for the exact-split path: exact hi/mid sums, rounded lo sums,
 // and the FP32 macroscopic fields derived from them.
 struct SplitPre {
-    split32::Part h, m, l;
+    split32::Part p;
     float s0, rho, ux, uy, T;
 };
 
@@ -313,11 +310,11 @@ __device__ __forceinline__ void split_pre(const float* d, const StepParams& P, S
                                           int* __restrict__ flag) {
     using namespace split32;
     const float dmax = MaxAbs<NPOP - 1>::run(d);
-    split_sums(d, s.h, s.m, s.l);
-    s.s0 = (s.h.s0 + s.m.s0) + s.l.s0;
-    const float sx = (s.h.sx + s.m.sx) + s.l.sx;
-    const float sy = (s.h.sy + s.m.sy) + s.l.sy;
-    const float se = (s.h.se + s.m.se) + s.l.se;
+    split_sums(d, s.p);
+    s.s0 = fmaf((float)s.p.n0, Q, s.p.r0);
+    const float sx = fmaf((float)s.p.nx, Q, s.p.rx);
+    const float sy = fmaf((float)s.p.ny, Q, s.p.ry);
+    const float se = fmaf((float)s.p.ne, Q, s.p.re);
     const float r = P.r_f, r2 = P.r2_f;
     s.rho = 1.0f + s.s0;
     const float inv = 1.0f / s.rho;
@@ -361,15 +358,16 @@ __device__ __forceinline__ void split_collide(float* d, const StepParams& P, con
 // residual is formed from exact hi/mid differences (same quanta before and after).
 __device__ __forceinline__ void split_project(float* d, const StepParams& P, const SplitPre& s) {
     using namespace split32;
-    Part h1, m1, l1;
-    split_sums(d, h1, m1, l1);
+    Part p1;
+    split_sums(d, p1);
     const float r = P.r_f, r2 = P.r2_f;
     const float gx = P.gx_f, gy = P.gy_f;
     const float rinv = 1.0f / r;
-    const float R0 = (s.h.s0 - h1.s0) + ((s.m.s0 - m1.s0) + (s.l.s0 - l1.s0));
-    const float Rx = (s.h.sx - h1.sx) + ((s.m.sx - m1.sx) + (s.l.sx - l1.sx)) + s.rho * gx * rinv;
-    const float Ry = (s.h.sy - h1.sy) + ((s.m.sy - m1.sy) + (s.l.sy - l1.sy)) + s.rho * gy * rinv;
-    const float Re = (s.h.se - h1.se) + ((s.m.se - m1.se) + (s.l.se - l1.se)) +
+    // integer differences are exact; only the residual sums round
+    const float R0 = fmaf((float)(s.p.n0 - p1.n0), Q, s.p.r0 - p1.r0);
+    const float Rx = fmaf((float)(s.p.nx - p1.nx), Q, s.p.rx - p1.rx) + s.rho * gx * rinv;
+    const float Ry = fmaf((float)(s.p.ny - p1.ny), Q, s.p.ry - p1.ry) + s.rho * gy * rinv;
+    const float Re = fmaf((float)(s.p.ne - p1.ne), Q, s.p.re - p1.re) +
                      s.rho * (2.0f * (s.ux * gx + s.uy * gy) + gx * gx + gy * gy) * (rinv * rinv);
     const float lam0 = 2.0f * R0 - 0.5f * r2 * Re;
     const float lame = r2 * (0.25f * r2 * Re - 0.5f * R0);

@@ -127,7 +127,7 @@ def test_fp32split_one_step_matches_fp64_accumulation(L):
 
 
 def test_fp32split_reports_out_of_range_deviation(L):
-    """A deviation |f - w| >= 4 (planted on the host) leaves the exact-split range: the step flags
+    """A deviation |f - w| >= 1 (planted on the host) leaves the exact-split range: the step flags
     it and lb_sync reports LB_ERR_RANGE once."""
     st = inputs.rayleigh_taylor(32, 32, R=2.0, seed=0)
     lat = L.Lattice.from_fields(st, tau=0.9, precision="fp32split")
