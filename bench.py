@@ -36,13 +36,13 @@ if ROOT not in sys.path:
 
 LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
 NPOP = 37
-# FP64 work of the fused step per site in this kernel's formulation: 364 FP64 instructions
-# (191 FMA + 95 add + 78 mul; ncu's opcode counters on step_fp64_kernel agree exactly), i.e.
-# 555 flops with FMA = 2. The FP64 pipe issues one such instruction per lane-slot whatever its
+# FP64 work of the fused step per site in this kernel's formulation: 359 FP64 instructions
+# (191 FMA + 95 add + 73 mul; ncu's opcode counters on step_fp64_kernel, per site), i.e.
+# 550 flops with FMA = 2. The FP64 pipe issues one such instruction per lane-slot whatever its
 # kind, so the ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per SM x f_max
 # (the 1.25 TFLOP/s nominal FP64 rate counts an FMA as 2 flops).
-FP64_INST_PER_SITE = 364
-FP64_FLOP_PER_SITE = 555
+FP64_INST_PER_SITE = 359
+FP64_FLOP_PER_SITE = 550
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 SM_COUNT = 152
@@ -50,11 +50,11 @@ FP64_INST_PER_CLK_SM = 2
 SM_MAX_MHZ = 2070.0
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 699.088 MB + 643.803 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# 698.642 MB + 644.271 MB for 2359296 sites, scaled per site. Valid only for the kernel source
 # it was taken on (sha256 of step_fp64.cu and d2q37_gpu.cuh below); otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (699.088128e6 + 643.802880e6) / 2359296,
-                "sources": {"step_fp64.cu": "5597620c368f5a957c6bc1dd21017f6a2500b86e1444e616a61e45d4151aa438",
-                            "d2q37_gpu.cuh": "4d59013b2b1c32dfb60f905a86920bcb2013740b2740292f71e9236a9fbc8e92"}}
+TRAFFIC_FP64 = {"bytes_per_site": (698.642176e6 + 644.271360e6) / 2359296,
+                "sources": {"step_fp64.cu": "76b443659be85d70ad400e4077d0a8a430696d9f2a20dd27b3bb805cbb96a075",
+                            "d2q37_gpu.cuh": "4fc41d583a7b75f6a860893613dc2e3f2a7fb7e26d650bc5c1467a5cf947583f"}}
 
 
 def sources_match(table):
