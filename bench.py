@@ -169,21 +169,21 @@ def oracle_mlups(rows, steps, nthreads):
     return LX * rows * steps / dt / 1e6, dt
 
 
-def cpu_baseline(target_s=15.0):
+def cpu_baseline(target_s=20.0):
     """The oracle on the same workload, as many whole steps as fit ~target_s of CPU time (a
     band of rows instead when even one full step would take longer)."""
     from oracle import oracle as orc
     nthreads = orc.default_threads()
-    rate, _ = oracle_mlups(64, 1, nthreads)                 # calibration
+    rate, _ = oracle_mlups(min(LY, 512), 1, nthreads)       # calibration on a 512-row band
     full_step_s = LX * LY / (rate * 1e6)
     if full_step_s <= target_s:
         rows, steps = LY, int(max(1, min(50, round(target_s / full_step_s))))
     else:
         rows, steps = int(max(64, LY * target_s / full_step_s)), 1
     v, dt = oracle_mlups(rows, steps, nthreads)
-    what = "the whole lattice" if rows == LY else f"a {LX}x{rows} band (walls at the band edges) of"
+    what = ("the whole" if rows == LY else f"a {LX}x{rows} band (walls at the band edges) of the")
     return {"value": round(v, 3), "unit": "MLUPS", "cores": nthreads, "kind": "oracle",
-            "sample": f"{steps} steps of {what} the {LX}x{LY} FP64 Rayleigh-Taylor workload, "
+            "sample": f"{steps} steps of {what} {LX}x{LY} FP64 Rayleigh-Taylor workload, "
                       f"{dt:.1f} s of CPU time"}
 
 
