@@ -387,6 +387,7 @@ def main():
             net.close()
         if not args.no_ensemble:
             forms["ensemble"] = measure_ensemble(lb, torch, np, inputs, value / world)
+        forms["table1_1024x8192"] = measure_table1(lb, torch, np, inputs)
 
     line = {"metric": "D2Q37 MLUPS, fused FP64 LB step (propagate+collide+walls)",
             "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
@@ -562,6 +563,55 @@ def measure_learned(lb, torch, np, inputs, st, stream, fp32split_mlups, epochs=2
            "train_s": round(t_train, 1), "pair_generation_s": round(t_data, 1),
            "train_samples_per_s": round(npairs * epochs / t_train, 0)}
     return out, net
+
+
+def measure_table1(lb, torch, np, inputs, reps=20):
+    """The paper's per-kernel metrics (Table 1) on GB300 at its 1024 x 8192 lattice, FP64:
+    separate propagate and collide kernels timed launch by launch (CUDA events), propagate GB/s
+    with 592 B per site, collide MLUPS and GF/s (with the paper's ~6600 flop/site, as Table 1
+    derives it, and with this kernel's 550), and Global MLUPS of the two-kernel step and of the
+    fused step."""
+    Lx, Ly = 1024, 8192
+    sites = Lx * Ly
+    st = inputs.rayleigh_taylor(Lx, Ly, R=RATIO, seed=0)
+    stream = torch.cuda.Stream()
+    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream)
+    for _ in range(3):
+        lat.propagate()
+        lat.collide()
+    lat.sync()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3 * reps)]
+    for k in range(reps):
+        ev[3 * k].record(stream)
+        lat.propagate()
+        ev[3 * k + 1].record(stream)
+        lat.collide()
+        ev[3 * k + 2].record(stream)
+    ev[-1].synchronize()
+    lat.sync()
+    t_prop = sum(ev[3 * k].elapsed_time(ev[3 * k + 1]) for k in range(reps)) / reps
+    t_coll = sum(ev[3 * k + 1].elapsed_time(ev[3 * k + 2]) for k in range(reps)) / reps
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    lat.step(16)
+    e0.record(stream)
+    lat.step(10 * 16)
+    e1.record(stream)
+    e1.synchronize()
+    t_fused = e0.elapsed_time(e1) / 160
+    lat.sync()
+    lat.close()
+    coll_mlups = sites / (t_coll * 1e-3) / 1e6
+    return {"lattice": [Lx, Ly], "T_prop_ms": round(t_prop, 4), "T_coll_ms": round(t_coll, 4),
+            "propagate_GBs": round(FP64_BYTES_PER_SITE * sites / (t_prop * 1e-3) / 1e9, 1),
+            "collide_MLUPS": round(coll_mlups, 1),
+            "collide_GFs_at_6600_flop_per_site": round(coll_mlups * 6600 / 1e3, 1),
+            "collide_GFs_at_550_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
+            "global_MLUPS_two_kernel": round(sites / ((t_prop + t_coll) * 1e-3) / 1e6, 1),
+            "global_MLUPS_fused": round(sites / (t_fused * 1e-3) / 1e6, 1),
+            "paper_KNL_7230_flat": {"T_prop_ms": 12.5, "T_coll_ms": 50.3, "propagate_GBs": 398,
+                                    "collide_GFs": 1100, "collide_MLUPS": 166, "global_MLUPS": 119},
+            "paper_P100": {"T_prop_ms": 12.5, "T_coll_ms": 24.1, "propagate_GBs": 396,
+                           "collide_GFs": 2253, "collide_MLUPS": 340, "global_MLUPS": 232}}
 
 
 def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300):

@@ -110,6 +110,12 @@ lb_status lb_step(lb_ctx* c, int n);
  * halo rows are carried over unchanged. A pure copy: bit-exact. Asynchronous. */
 lb_status lb_propagate(lb_ctx* c);
 
+/* Collide only, in place on the current populations (LB_FP64 contexts): the paper's separate
+ * collide kernel (Sec. 3; timed on its own in Table 1). Moments, shifted equilibrium and BGK as in
+ * lb_step, then the wall halo rows. lb_propagate followed by lb_collide equals one lb_step bit for
+ * bit. Asynchronous; LB_ERR_STATE for FP32 contexts or while the learned collide is set. */
+lb_status lb_collide(lb_ctx* c);
+
 /* Wait for queued work; returns LB_ERR_NONFINITE (once) if any step since the last check saw a
  * non-finite or non-positive density/temperature, else LB_OK. */
 lb_status lb_sync(lb_ctx* c);

@@ -22,6 +22,7 @@ cudaError_t launch_step_fp64(const double* src, double* dst, const StepParams& P
                              cudaStream_t s);
 cudaError_t launch_propagate_fp64(const double* src, double* dst, const StepParams& P,
                                   cudaStream_t s);
+cudaError_t launch_collide_fp64(double* f, const StepParams& P, int* flag, cudaStream_t s);
 cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy,
                              const double* T, double* f, const StepParams& P, cudaStream_t s);
 cudaError_t launch_moments_fp64(const double* f, const StepParams& P, double* rho, double* ux,

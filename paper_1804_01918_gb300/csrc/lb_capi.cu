@@ -413,6 +413,14 @@ lb_status lb_propagate(lb_ctx* c) {
     return LB_OK;
 }
 
+lb_status lb_collide(lb_ctx* c) {
+    if (!c) return LB_ERR_ARG;
+    if (c->p.precision != LB_FP64 || c->learned) return LB_ERR_STATE;
+    cudaError_t e = launch_collide_fp64((double*)c->buf[c->cur], c->sp, c->flag, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "collide kernel launch");
+    return LB_OK;
+}
+
 lb_status lb_sync(lb_ctx* c) {
     if (!c) return LB_ERR_ARG;
     LB_CUDA(cudaStreamSynchronize(c->stream));

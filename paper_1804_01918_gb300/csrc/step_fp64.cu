@@ -236,6 +236,46 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
     }
 }
 
+// Collide only, in place (the paper's separate collide kernel, Sec. 3-5 and Table 1): each thread
+// reads the 37 populations of its own site, relaxes them exactly as the fused step does, writes
+// them back, and on rows 0..2 and Ly-3..Ly-1 writes the wall halo rows. After propagate this gives
+// the same populations, bit for bit, as one fused step.
+__global__ void __launch_bounds__(SITE_BLOCK)
+collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict__ flag) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= Lx * Ly) return;
+    const int y = site / Lx;
+    const int x = site - y * Lx;
+    const long long plane = P.plane;
+    const long long o = (long long)(y + HALO) * Lx + x;
+    double v[NPOP];
+#pragma unroll
+    for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, plane) + o];
+    const SiteMoments m = site_moments(v, P.r, P.r2);
+    if (bad_positive(m.rho) || bad_positive(m.T)) atomicOr(flag, 1);
+    const double uxs = m.ux + P.tgx;
+    const double uys = m.uy + P.tgy;
+    const double th = (m.T + P.dT_force) - 1.0;
+    const double u2 = uxs * uxs + uys * uys;
+    double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], W24[NSHELL], W6[NSHELL];
+    shell_coefficients_scaled(P, th, u2, m.rho * P.omega, WA0, WA2, WB1, W24, W6);
+    __stcs(f + o, fma(P.omc, v[0], WA0[0]));
+    RelaxAll<NPAIR>::run(v, f, o, plane, P.r * uxs, P.r * uys, WA0, WA2, WB1, W24, W6, P.omc);
+    if (!P.y_periodic) {
+        if (y < HALO) {
+            const long long ob = (long long)(HALO - 1 - y) * Lx + x;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) __stcs(f + plane_off(i, plane) + ob, m.rho * P.wall_bot[i]);
+        }
+        if (y >= Ly - HALO) {
+            const long long ot = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
+#pragma unroll
+            for (int i = 0; i < NPOP; ++i) __stcs(f + plane_off(i, plane) + ot, m.rho * P.wall_top[i]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(SITE_BLOCK)
 propagate_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P) {
     const int Lx = P.Lx, Ly = P.Ly;
@@ -349,6 +389,11 @@ inline int site_blocks(const StepParams& P) {
 cudaError_t launch_step_fp64(const double* src, double* dst, const StepParams& P, int* flag,
                              cudaStream_t s) {
     step_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_collide_fp64(double* f, const StepParams& P, int* flag, cudaStream_t s) {
+    collide_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(f, P, flag);
     return cudaGetLastError();
 }
 

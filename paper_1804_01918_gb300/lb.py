@@ -69,6 +69,7 @@ def lib() -> C.CDLL:
         L.lb_init.argtypes = [C.POINTER(lb_params), vp, vp, vp, vp, C.POINTER(vp)]
         L.lb_step.argtypes = [vp, C.c_int]
         L.lb_propagate.argtypes = [vp]
+        L.lb_collide.argtypes = [vp]
         L.lb_sync.argtypes = [vp]
         L.lb_moments.argtypes = [vp, vp, vp, vp, vp]
         L.lb_moments_device.argtypes = [vp, vp, vp, vp, vp]
@@ -251,6 +252,10 @@ class Lattice:
 
     def propagate(self) -> None:
         check(lib().lb_propagate(self._ctx), "lb_propagate")
+
+    def collide(self) -> None:
+        """Collide in place (FP64): lb_propagate + lb_collide = one fused step."""
+        check(lib().lb_collide(self._ctx), "lb_collide")
 
     def sync(self) -> None:
         check(lib().lb_sync(self._ctx), "lb_sync")

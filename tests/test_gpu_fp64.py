@@ -201,3 +201,17 @@ def test_full_size_2304x8192_sampled_sites_match_oracle(L, orc):
         got_o = np.empty(37)
         got_o[perm] = got
         assert rel_err(got_o, want) <= TOL, (x0, y0)
+
+
+@pytest.mark.parametrize("y_periodic", [False, True])
+def test_two_kernel_step_equals_fused_step(L, y_periodic):
+    """The paper's two-kernel structure (propagate, then collide; Sec. 3, Table 1) gives the fused
+    step's populations bit for bit."""
+    st = inputs.rayleigh_taylor(96, 80, R=2.0, seed=5)
+    a = L.Lattice.from_fields(st, tau=0.85, y_periodic=y_periodic)
+    b = L.Lattice.from_fields(st, tau=0.85, y_periodic=y_periodic)
+    for _ in range(7):
+        a.propagate()
+        a.collide()
+    b.step(7)
+    assert np.array_equal(a.get_populations(), b.get_populations())
