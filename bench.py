@@ -142,6 +142,19 @@ class ClockSampler:
                 "power_w_median": statistics.median(power), "reasons": sorted(reasons)}
 
 
+def energy_of(clocks, ms_per_step, sites):
+    """Energy to solution per step from the board power sampled during the timed region (the
+    analog of the paper's RAPL package + DRAM energy per iteration, Sec. 5 and Fig. 5; on GB300 the
+    board power includes the HBM)."""
+    p = clocks.get("power_w_median")
+    if not p:
+        return None
+    j = p * ms_per_step * 1e-3
+    return {"power_w_median": round(p, 1), "joules_per_step": round(j, 4),
+            "nJ_per_site_update": round(j / sites * 1e9, 3),
+            "source": "nvidia-smi power.draw samples every 200 ms during the timed region"}
+
+
 def visible_gpu_index(local_rank):
     cvd = os.environ.get("CUDA_VISIBLE_DEVICES", "")
     ids = [s for s in cvd.split(",") if s.strip() != ""]
@@ -396,6 +409,7 @@ def main():
             "dtype": "f64" if args.precision == "fp64" else "f32",
             "data": "synthetic (seeded Rayleigh-Taylor fields)", "config": workload_config(world),
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps,
+            "energy": energy_of(clocks, ms / args.steps, world * sites),
             "e2e": e2e,
             "paper_context": {"KNL 7230 flat/quad Global MLUPS 1024x8192": 119,
                               "P100 Global MLUPS 1024x8192": 232}}
