@@ -43,8 +43,9 @@ inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 template <bool kSplit>
 __global__ void __launch_bounds__(ENS_BLOCK)
-ensemble_step_kernel(const MemberDesc* __restrict__ members, const int4* __restrict__ items,
-                     int nitems, int tx_log2, int tile_sites, int parity, int* __restrict__ flag) {
+ensemble_step_kernel(const StepParams Pc, const MemberDesc* __restrict__ members,
+                     const int4* __restrict__ items, int nitems, int tx_log2, int tile_sites,
+                     int parity, int* __restrict__ flag) {
     __shared__ __align__(16) StepParams sP;
     __shared__ const float* s_src;
     __shared__ float* s_dst;
@@ -66,7 +67,7 @@ ensemble_step_kernel(const MemberDesc* __restrict__ members, const int4* __restr
             const int y = it.z + (k >> tx_log2);
             if (x < sP.Lx && y < sP.Ly) {
                 if (kSplit)
-                    fp32split_site(s_src, s_dst, sP, x, y, flag);
+                    fp32split_site(s_src, s_dst, Pc, sP, x, y, flag);  // constants from Pc
                 else
                     fp32dev_site(s_src, s_dst, sP, x, y, flag);
             }
@@ -224,12 +225,14 @@ lb_status upload_items(lb_ensemble* e, int tx, int ty) {
 
 cudaError_t launch_ensemble(lb_ensemble* e, int parity) {
     const int txl = log2_exact(e->tile_x);
+    // the lattice constants (r, shell coefficients) are the same for every member: they travel as
+    // a kernel parameter (constant bank); each member's own values are staged in shared memory
     if (e->precision == LB_FP32SPLIT)
         ensemble_step_kernel<true><<<e->grid, ENS_BLOCK, 0, e->stream>>>(
-            e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
+            e->sp[0], e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
     else
         ensemble_step_kernel<false><<<e->grid, ENS_BLOCK, 0, e->stream>>>(
-            e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
+            e->sp[0], e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
     return cudaGetLastError();
 }
 

@@ -74,8 +74,8 @@ __global__ void pairs_kernel(const float* __restrict__ src, const StepParams P, 
     for (int i = 0; i < NPOP; ++i) pre[(size_t)k * NPOP + i] = d[i];
     SplitPre s;
     split_pre(d, P, s, flag);
-    split_collide(d, P, s);
-    split_project(d, P, s);
+    split_collide(d, P, P, s);
+    split_project(d, P, P, s);
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) post[(size_t)k * NPOP + i] = d[i];
 }
@@ -541,7 +541,7 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
         const int mode = tile_mode[t];
         const int x = x0 + (f.tid & 31);
         if (!check && mode) {
-            for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
+            for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
             continue;
         }
         float rmax = 0.0f, fmax = 0.0f;
@@ -566,10 +566,10 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
             float dl[NPOP];
 #pragma unroll
             for (int i = 0; i < NPOP; ++i) dl[i] = d[i] + fmaf(yv[i], sd_t[i], mu_t[i]);
-            split_project(dl, P, s);
+            split_project(dl, P, P, s);
             if (check) {
-                split_collide(d, P, s);  // d becomes the plain collide's candidate
-                split_project(d, P, s);
+                split_collide(d, P, P, s);  // d becomes the plain collide's candidate
+                split_project(d, P, P, s);
 #pragma unroll
                 for (int i = 0; i < NPOP; ++i) {
                     rmax = fmaxf(rmax, fabsf(dl[i] - d[i]));
@@ -602,7 +602,7 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
                 atomicMax(&stats->max_res_bits, __float_as_uint(res));
             }
             if (fall)
-                for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
+                for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
         }
     }
     if (!alive && f.tid == 0) atomicOr(flag, ERR_TIMEOUT);

@@ -326,17 +326,21 @@ __device__ __forceinline__ void split_pre(const float* d, const StepParams& P, S
         atomicOr(flag, !(dmax < RANGE) ? 2 : 1);
 }
 
-// FP32 BGK relaxation of d (in place) toward the shifted Hermite equilibrium of s.
-__device__ __forceinline__ void split_collide(float* d, const StepParams& P, const SplitPre& s) {
-    const float r = P.r_f;
-    const float uxs = s.ux + P.tgx_f, uys = s.uy + P.tgy_f;
-    const float th = (s.T + P.dT_force_f) - 1.0f;
+// FP32 BGK relaxation of d (in place) toward the shifted Hermite equilibrium of s. C supplies the
+// lattice constants (r, shell coefficients: the same for every lattice), M the lattice's own
+// relaxation time and gravity; single lattices pass the same parameters twice.
+__device__ __forceinline__ void split_collide(float* d, const StepParams& C, const StepParams& M,
+                                              const SplitPre& s) {
+    const StepParams& P = C;
+    const float r = C.r_f;
+    const float uxs = s.ux + M.tgx_f, uys = s.uy + M.tgy_f;
+    const float th = (s.T + M.dT_force_f) - 1.0f;
     const float u2 = uxs * uxs + uys * uys;
     const float a00m1 = u2 * fmaf(u2, 0.125f, -0.5f);
     const float a20 = fmaf(u2, -0.25f, 0.5f);
     const float b10 = fmaf(u2, -0.5f, 1.0f);
     const float thu2 = th * u2, th2 = th * th;
-    const float omega = P.omega_f;
+    const float omega = M.omega_f;
     float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], Wd[NSHELL];
 #pragma unroll
     for (int k = 0; k < NSHELL; ++k) {
@@ -347,7 +351,7 @@ __device__ __forceinline__ void split_collide(float* d, const StepParams& P, con
         Wd[k] = omega * P.sh32[k].w;
     }
     const float drho = s.s0;
-    const float omc = P.omc_f;
+    const float omc = M.omc_f;
     d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
     Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, Wd, drho, omc);
 }
@@ -356,12 +360,13 @@ __device__ __forceinline__ void split_collide(float* d, const StepParams& P, con
 // sum d' = sum d, sum d' c = sum d c + rho g / r, sum d' |c|^2 = sum d |c|^2 + rho (2 u.g + g^2) / r^2,
 // with the weighted least-norm correction d_i += w_i (l0 + lx c_x + ly c_y + le |c|^2). The
 // residual is formed from exact hi/mid differences (same quanta before and after).
-__device__ __forceinline__ void split_project(float* d, const StepParams& P, const SplitPre& s) {
+__device__ __forceinline__ void split_project(float* d, const StepParams& C, const StepParams& M,
+                                              const SplitPre& s) {
     using namespace split32;
     Part p1;
     split_sums(d, p1);
-    const float r = P.r_f, r2 = P.r2_f;
-    const float gx = P.gx_f, gy = P.gy_f;
+    const float r = C.r_f, r2 = C.r2_f;
+    const float gx = M.gx_f, gy = M.gy_f;
     const float rinv = 1.0f / r;
     // integer differences are exact; only the residual sums round
     const float R0 = fmaf((float)(s.p.n0 - p1.n0), Q, s.p.r0 - p1.r0);
@@ -411,16 +416,18 @@ __device__ __forceinline__ void split_store(float* __restrict__ dst, const StepP
 // One fused FP32-deviation step of site (x, y) with exact-split FP32 moment accumulation and an
 // FP32 projection residual (no FP64 arithmetic except on the six wall rows). Flag bits: 1 =
 // non-finite or non-positive density/temperature, 2 = a deviation outside the exact-split range.
+// C: lattice constants (r, shell coefficients), M: this lattice's sizes, relaxation, gravity and
+// walls (the same object for a single lattice).
 __device__ __forceinline__ void fp32split_site(const float* __restrict__ src, float* __restrict__ dst,
-                                               const StepParams& P, int x, int y,
+                                               const StepParams& C, const StepParams& M, int x, int y,
                                                int* __restrict__ flag) {
     float d[NPOP];
-    Pull32<NPOP - 1>::run(src, d, x, y, P.Lx, P.Ly, P.y_periodic, P.plane);
+    Pull32<NPOP - 1>::run(src, d, x, y, M.Lx, M.Ly, M.y_periodic, M.plane);
     SplitPre s;
-    split_pre(d, P, s, flag);
-    split_collide(d, P, s);
-    split_project(d, P, s);
-    split_store(dst, P, x, y, d, s.s0);
+    split_pre(d, C, s, flag);
+    split_collide(d, C, M, s);
+    split_project(d, C, M, s);
+    split_store(dst, M, x, y, d, s.s0);
 }
 
 }  // namespace lbg

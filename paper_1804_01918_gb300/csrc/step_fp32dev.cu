@@ -42,7 +42,7 @@ step_fp32split_kernel(const float* __restrict__ src, float* __restrict__ dst, co
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= P.Lx * P.Ly) return;
     const int y = site / P.Lx;
-    fp32split_site(src, dst, P, site - y * P.Lx, y, flag);
+    fp32split_site(src, dst, P, P, site - y * P.Lx, y, flag);
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
