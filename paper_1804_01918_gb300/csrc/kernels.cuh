@@ -35,6 +35,11 @@ cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& 
 // same storage, exact-split FP32 accumulation instead of FP64 (site_fp32dev.cuh)
 cudaError_t launch_step_fp32split(const float* src, float* dst, const StepParams& P, int* flag,
                                   cudaStream_t s);
+// the same step with TMA-staged pulls (step_fp32split_tma.cu); tmap is a CUtensorMap of src
+cudaError_t launch_step_fp32split_tma(const void* tmap, const float* src, float* dst,
+                                      const StepParams& P, int* flag, int grid, cudaStream_t s);
+cudaError_t make_fp32_tensor_map(void* tmap_out, const float* base, const StepParams& P);
+int fp32split_tma_grid();
 cudaError_t launch_propagate_fp32dev(const float* src, float* dst, const StepParams& P,
                                      cudaStream_t s);
 cudaError_t launch_init_fp32dev(const double* rho, const double* ux, const double* uy,

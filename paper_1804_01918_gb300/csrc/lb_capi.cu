@@ -168,6 +168,9 @@ struct lb_ctx {
     bool graph_failed = false;
     long long steps = 0;
     LearnedState* learned = nullptr;  // learned collide, when set
+    alignas(64) unsigned char tmap[2][128];  // TMA descriptors of the two FP32 population copies
+    bool tma_ready = false;                  // tensor maps built (FP32SPLIT, Lx % 4 == 0)
+    bool use_tma = false;                    // step with the TMA-staged kernel
 };
 
 namespace {
@@ -180,6 +183,10 @@ lb_status launch_one_step(lb_ctx* c) {
     else if (c->p.precision == LB_FP64)
         e = launch_step_fp64((const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1], c->sp,
                              c->flag, c->stream);
+    else if (c->p.precision == LB_FP32SPLIT && c->use_tma)
+        e = launch_step_fp32split_tma(c->tmap[c->cur], (const float*)c->buf[c->cur],
+                                      (float*)c->buf[c->cur ^ 1], c->sp, c->flag,
+                                      fp32split_tma_grid(), c->stream);
     else if (c->p.precision == LB_FP32SPLIT)
         e = launch_step_fp32split((const float*)c->buf[c->cur], (float*)c->buf[c->cur ^ 1], c->sp,
                                   c->flag, c->stream);
@@ -347,6 +354,11 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
     }
     c->buf[0] = c->ws + L.off_a;
     c->buf[1] = c->ws + L.off_b;
+    if (p->precision == LB_FP32SPLIT && p->Lx % 4 == 0) {
+        c->tma_ready = make_fp32_tensor_map(c->tmap[0], (const float*)c->buf[0], c->sp) == cudaSuccess &&
+                       make_fp32_tensor_map(c->tmap[1], (const float*)c->buf[1], c->sp) == cudaSuccess;
+        c->use_tma = c->tma_ready;
+    }
     c->stage = (double*)(c->ws + L.off_stage);
     c->flag = (int*)(c->ws + L.off_flag);
 
@@ -410,6 +422,20 @@ lb_status lb_propagate(lb_ctx* c) {
     if (e != cudaSuccess) return cuda_fail(e, "propagate kernel launch");
     c->cur ^= 1;
     c->steps += 1;
+    return LB_OK;
+}
+
+lb_status lb_set_staging(lb_ctx* c, int use_tma) {
+    if (!c) return LB_ERR_ARG;
+    if (use_tma && !c->tma_ready) return LB_ERR_STATE;
+    LB_CUDA(cudaStreamSynchronize(c->stream));
+    for (int k = 0; k < 2; ++k)
+        if (c->graph[k]) {
+            cudaGraphExecDestroy(c->graph[k]);
+            c->graph[k] = nullptr;
+        }
+    c->graph_failed = false;
+    c->use_tma = use_tma != 0;
     return LB_OK;
 }
 

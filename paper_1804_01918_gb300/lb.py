@@ -70,6 +70,7 @@ def lib() -> C.CDLL:
         L.lb_step.argtypes = [vp, C.c_int]
         L.lb_propagate.argtypes = [vp]
         L.lb_collide.argtypes = [vp]
+        L.lb_set_staging.argtypes = [vp, C.c_int]
         L.lb_sync.argtypes = [vp]
         L.lb_moments.argtypes = [vp, vp, vp, vp, vp]
         L.lb_moments_device.argtypes = [vp, vp, vp, vp, vp]
@@ -252,6 +253,10 @@ class Lattice:
 
     def propagate(self) -> None:
         check(lib().lb_propagate(self._ctx), "lb_propagate")
+
+    def set_staging(self, use_tma: bool) -> None:
+        """FP32-split steps: TMA-staged pulls (default where available) or plain loads."""
+        check(lib().lb_set_staging(self._ctx, int(bool(use_tma))), "lb_set_staging")
 
     def collide(self) -> None:
         """Collide in place (FP64): lb_propagate + lb_collide = one fused step."""
