@@ -357,7 +357,7 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
     if (p->precision == LB_FP32SPLIT && p->Lx % 4 == 0) {
         c->tma_ready = make_fp32_tensor_map(c->tmap[0], (const float*)c->buf[0], c->sp) == cudaSuccess &&
                        make_fp32_tensor_map(c->tmap[1], (const float*)c->buf[1], c->sp) == cudaSuccess;
-        c->use_tma = c->tma_ready;
+        c->use_tma = false;  // opt-in: measured slower than plain loads for this issue-bound kernel
     }
     c->stage = (double*)(c->ws + L.off_stage);
     c->flag = (int*)(c->ws + L.off_flag);

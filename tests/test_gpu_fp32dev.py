@@ -148,6 +148,7 @@ def test_tma_staged_step_equals_plain_loads(L, Lx, Ly, yp):
     st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=Lx + Ly)
     a = L.Lattice.from_fields(st, tau=0.8, y_periodic=yp, gy=st.gy * 3, precision="fp32split")
     b = L.Lattice.from_fields(st, tau=0.8, y_periodic=yp, gy=st.gy * 3, precision="fp32split")
+    a.set_staging(True)
     b.set_staging(False)
     a.step(21)
     b.step(21)
