@@ -98,6 +98,10 @@ struct StepParams {
     // FP32 copies of the scalars above and of the shell coefficients
     float r_f, r2_f, omega_f, omc_f, gx_f, gy_f, tgx_f, tgy_f, dT_force_f, pad_f;
     ShellCoef32 sh32[NSHELL];
+    // byte offsets for 4-byte populations: pull_b32[i] = 4 (i plane - c_iy Lx - c_ix) from a site's
+    // own element (valid where the pull does not wrap), plane_b32[i] = 4 i plane
+    long long pull_b32[NPOP];
+    long long plane_b32[NPOP];
 };
 
 }  // namespace lbg

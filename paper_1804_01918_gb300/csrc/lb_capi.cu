@@ -136,6 +136,10 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh32[s].delta = (float)sp.sh[s].delta;
         sp.sh32[s].eps = (float)sp.sh[s].eps;
     }
+    for (int i = 0; i < NPOP; ++i) {
+        sp.plane_b32[i] = 4ll * i * sp.plane;
+        sp.pull_b32[i] = 4ll * ((long long)i * sp.plane - (long long)cy_of(i) * p.Lx - cx_of(i));
+    }
     // rest equilibrium per unit density: w (1 + alpha theta + gamma theta^2) at u = 0
     for (int i = 0; i < NPOP; ++i) {
         const ShellCoef& c = sp.sh[shell_of(i)];

@@ -246,31 +246,37 @@ struct Part {
 };
 
 __device__ __forceinline__ void split_sums(const float* d, Part& p) {
-    int bx[7], by[7];
+    unsigned bx[7], by[7];
     float rx[7], ry[7];
 #pragma unroll
     for (int k = 0; k < 7; ++k) {
-        bx[k] = by[k] = 0;
+        bx[k] = by[k] = 0u;
         rx[k] = ry[k] = 0.0f;
     }
-    const int b3 = __float_as_int(QB);
+    // bins sum the raw bit patterns of t modulo 2^32 (unsigned: well-defined wrap-around); the
+    // bias bits(3.0f) per term cancels in the odd (difference) combinations and is removed once per
+    // even combination (the number of populations per bin is a constant), and every final
+    // combination fits in a signed 32-bit integer, so the modular arithmetic gives it exactly
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) {
         const float t = __fadd_rn(d[i], QB);
         const float r = __fsub_rn(d[i], __fsub_rn(t, QB));
-        const int n = __float_as_int(t) - b3;
+        const unsigned n = __float_as_uint(t);
         const int ix = cx_of(i) + 3, iy = cy_of(i) + 3;
         bx[ix] += n;
         by[iy] += n;
         rx[ix] += r;
         ry[iy] += r;
     }
-    const int px1 = bx[4] + bx[2], px2 = bx[5] + bx[1], px3 = bx[6] + bx[0];
-    const int py1 = by[4] + by[2], py2 = by[5] + by[1], py3 = by[6] + by[0];
-    p.n0 = ((bx[3] + px1) + px2) + px3;
-    p.nx = 3 * (bx[6] - bx[0]) + 2 * (bx[5] - bx[1]) + (bx[4] - bx[2]);
-    p.ny = 3 * (by[6] - by[0]) + 2 * (by[5] - by[1]) + (by[4] - by[2]);
-    p.ne = (9 * px3 + 4 * px2 + px1) + (9 * py3 + 4 * py2 + py1);
+    constexpr unsigned b3 = 0x40400000u;  // bits of 3.0f
+    const unsigned px1 = bx[4] + bx[2], px2 = bx[5] + bx[1], px3 = bx[6] + bx[0];
+    const unsigned py1 = by[4] + by[2], py2 = by[5] + by[1], py3 = by[6] + by[0];
+    // populations per bin: c = 0: 7, |c| = 1: 7 each, 2: 5 each, 3: 3 each (x and y alike)
+    p.n0 = (int)((((bx[3] + px1) + px2) + px3) - (unsigned)NPOP * b3);
+    p.nx = (int)(3u * (bx[6] - bx[0]) + 2u * (bx[5] - bx[1]) + (bx[4] - bx[2]));
+    p.ny = (int)(3u * (by[6] - by[0]) + 2u * (by[5] - by[1]) + (by[4] - by[2]));
+    p.ne = (int)(((9u * px3 + 4u * px2 + px1) + (9u * py3 + 4u * py2 + py1)) -
+                 2u * (9u * 6u + 4u * 10u + 14u) * b3);
     const float qx1 = rx[4] + rx[2], qx2 = rx[5] + rx[1], qx3 = rx[6] + rx[0];
     const float qy1 = ry[4] + ry[2], qy2 = ry[5] + ry[1], qy3 = ry[6] + ry[0];
     p.r0 = ((rx[3] + qx1) + qx2) + qx3;
@@ -377,11 +383,17 @@ __device__ __forceinline__ void split_project(float* d, const StepParams& C, con
     const float lam0 = 2.0f * R0 - 0.5f * r2 * Re;
     const float lame = r2 * (0.25f * r2 * Re - 0.5f * R0);
     const float lamx = r2 * Rx, lamy = r2 * Ry;
+    // correction w_i (even_s +- odd_i): even part per shell, odd part per opposite pair
+    float ev[NSHELL];
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        const float corr = fmaf(lame, (float)shell_c2(shell_of(i)),
-                                fmaf(lamx, (float)cx_of(i), fmaf(lamy, (float)cy_of(i), lam0)));
-        d[i] = fmaf((float)shell_w(shell_of(i)), corr, d[i]);
+    for (int k = 0; k < NSHELL; ++k)
+        ev[k] = (float)shell_w(k) * fmaf(lame, (float)shell_c2(k), lam0);
+    d[0] += ev[0];
+#pragma unroll
+    for (int i = 1; i <= NPAIR; ++i) {
+        const float od = (float)shell_w(shellh(i)) * fmaf(lamx, (float)cxh(i), lamy * (float)cyh(i));
+        d[i] += ev[shellh(i)] + od;
+        d[i + NPAIR] += ev[shellh(i)] - od;
     }
 }
 
@@ -392,8 +404,9 @@ __device__ __forceinline__ void split_store(float* __restrict__ dst, const StepP
     const int Lx = P.Lx, Ly = P.Ly;
     const long long plane = P.plane;
     const long long dsto = (long long)(y + HALO) * Lx + x;
+    char* const base = reinterpret_cast<char*>(dst + dsto);
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) __stcs(dst + (long long)i * plane + dsto, d[i]);
+    for (int i = 0; i < NPOP; ++i) __stcs(reinterpret_cast<float*>(base + P.plane_b32[i]), d[i]);
     if (!P.y_periodic) {
         const double rho_d = 1.0 + (double)s0;
         if (y < HALO) {
@@ -418,11 +431,33 @@ __device__ __forceinline__ void split_store(float* __restrict__ dst, const StepP
 // non-finite or non-positive density/temperature, 2 = a deviation outside the exact-split range.
 // C: lattice constants (r, shell coefficients), M: this lattice's sizes, relaxation, gravity and
 // walls (the same object for a single lattice).
+// Pull with precomputed byte offsets from the site's own element: valid unless the source wraps.
+template <int I>
+struct PullFast32 {
+    __device__ __forceinline__ static void run(const char* base, float* d, const StepParams& M) {
+        PullFast32<I - 1>::run(base, d, M);
+        d[I] = __ldg(reinterpret_cast<const float*>(base + M.pull_b32[I]));
+    }
+};
+template <>
+struct PullFast32<-1> {
+    __device__ __forceinline__ static void run(const char*, float*, const StepParams&) {}
+};
+
+__device__ __forceinline__ void pull32(const float* __restrict__ src, float* d, const StepParams& M, int x,
+                                       int y) {
+    const bool interior = x >= HALO && x < M.Lx - HALO && (!M.y_periodic || (y >= HALO && y < M.Ly - HALO));
+    if (interior)
+        PullFast32<NPOP - 1>::run(reinterpret_cast<const char*>(src + (long long)(y + HALO) * M.Lx + x), d, M);
+    else
+        Pull32<NPOP - 1>::run(src, d, x, y, M.Lx, M.Ly, M.y_periodic, M.plane);
+}
+
 __device__ __forceinline__ void fp32split_site(const float* __restrict__ src, float* __restrict__ dst,
                                                const StepParams& C, const StepParams& M, int x, int y,
                                                int* __restrict__ flag) {
     float d[NPOP];
-    Pull32<NPOP - 1>::run(src, d, x, y, M.Lx, M.Ly, M.y_periodic, M.plane);
+    pull32(src, d, M, x, y);
     SplitPre s;
     split_pre(d, C, s, flag);
     split_collide(d, C, M, s);
