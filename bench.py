@@ -221,7 +221,7 @@ def run_reference(args):
     value = LX * rows * args.steps / dt / 1e6
     sample = (f"each step a {LX}x{rows} band of the {LX}x{LY} FP64 Rayleigh-Taylor workload "
               f"(walls at the band edges)")
-    line = {"impl": "reference", "metric": "D2Q37 MLUPS, fused FP64 LB step (propagate+collide+walls)",
+    line = {"impl": "reference", "metric": metric_name("fp64"),
             "value": round(value, 3), "unit": "MLUPS", "n_gpus": 0, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -234,13 +234,23 @@ def run_reference(args):
     return 0
 
 
-def workload_config(world):
-    return {"workload": f"D2Q37 FP64 Rayleigh-Taylor {LX}x{LY} (18.9M sites, ~11.2 GB "
-                        f"double-buffered), tau {TAU}, T ratio 1:{RATIO}, walls top/bottom, "
-                        f"periodic x, fused propagate+collide+walls",
-            "Lx": LX, "Ly": LY, "tau": TAU, "precision": "fp64",
+PRECISION_LABEL = {"fp64": "FP64", "fp32dev": "FP32-deviation", "fp32split": "FP32 exact-split"}
+
+
+def workload_config(world, precision="fp64"):
+    bpv = 8 if precision == "fp64" else 4
+    half = 37 * LX * (LY + 6) * bpv / 1e9
+    return {"workload": f"D2Q37 {PRECISION_LABEL[precision]} Rayleigh-Taylor {LX}x{LY} (18.9M "
+                        f"sites, ~{2 * half:.1f} GB double-buffered), tau {TAU}, T ratio 1:{RATIO}, "
+                        f"walls top/bottom, periodic x, fused propagate+collide+walls",
+            "Lx": LX, "Ly": LY, "tau": TAU, "precision": precision,
             "replicas": world, "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-            "l2": "inputs larger than L2 (5.6 GB read + 5.6 GB written per step vs 129 MB L2)"}
+            "l2": f"inputs larger than L2 ({half:.1f} GB read + {half:.1f} GB written per step vs "
+                  f"129 MB L2)"}
+
+
+def metric_name(precision="fp64"):
+    return f"D2Q37 MLUPS, fused {PRECISION_LABEL[precision]} LB step (propagate+collide+walls)"
 
 
 # ----------------------------------------------------------------------------------------------
@@ -402,12 +412,13 @@ def main():
             forms["ensemble"] = measure_ensemble(lb, torch, np, inputs, value / world)
         forms["table1_1024x8192"] = measure_table1(lb, torch, np, inputs)
 
-    line = {"metric": "D2Q37 MLUPS, fused FP64 LB step (propagate+collide+walls)",
+    line = {"metric": metric_name(args.precision),
             "value": round(value, 2), "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64" if args.precision == "fp64" else "f32",
-            "data": "synthetic (seeded Rayleigh-Taylor fields)", "config": workload_config(world),
+            "data": "synthetic (seeded Rayleigh-Taylor fields)",
+            "config": workload_config(world, args.precision),
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps,
             "energy": energy_of(clocks, ms / args.steps, world * sites),
             "e2e": e2e,

@@ -23,7 +23,10 @@
  *   - collision: single-relaxation-time BGK with relaxation time tau;
  *   - gravity g: the equilibrium is evaluated at u + tau g and T + tau (1 - tau) |g|^2 / D;
  *   - walls (top/bottom): three halo rows per wall hold the equilibrium at rest, at the wall
- *     temperature and at the density of the mirror interior row;
+ *     temperature and at the density of the mirror interior row; an alternative mirror closure
+ *     (opposite velocity, temperature reflected about the wall value) is also provided;
+ *   - reported fields: moments of the stored populations; optionally the half-step fields that
+ *     average the pre- and post-collision momentum and energy;
  *   - periodic in x (optionally in y, a test mode with no walls);
  *   - one step = write wall halos, propagate (pull), collide.
  *
@@ -219,11 +222,49 @@ void or_walls(int Lx, int Ly, double T_top, double T_bottom, double* f) {
         }
 }
 
+/* Mirror wall step (an alternative wall closure; the paper leaves walls to its references): the
+ * halo row y = -1 - k holds the equilibrium at the density of its mirror row k, the opposite
+ * velocity and the temperature 2 T_bottom - T(x, k); likewise above row Ly - 1 with T_top and
+ * mirror row Ly - 1 - k. The fields of a mirror site are the moments of its current populations.
+ * Linear interpolation between a row and its mirror halo row then gives zero velocity and the
+ * wall temperature exactly on the plane half a site outside the last interior row (y = -1/2 and
+ * y = Ly - 1/2): a no-slip wall at a fixed temperature. */
+void or_walls_mirror(int Lx, int Ly, double T_top, double T_bottom, double* f) {
+    setup();
+    for (int k = 0; k < HALO; ++k)
+        for (int x = 0; x < Lx; ++x) {
+            double rho, ux, uy, T;
+            moments_site(f + ((size_t)(k + HALO) * Lx + x) * NPOP, &rho, &ux, &uy, &T);
+            feq_site(rho, -ux, -uy, 2.0 * T_bottom - T, f + ((size_t)(HALO - 1 - k) * Lx + x) * NPOP);
+            moments_site(f + ((size_t)(Ly - 1 - k + HALO) * Lx + x) * NPOP, &rho, &ux, &uy, &T);
+            feq_site(rho, -ux, -uy, 2.0 * T_top - T, f + ((size_t)(Ly + HALO + k) * Lx + x) * NPOP);
+        }
+}
+
+/* Half-step ("physical") fields of n post-collision sites f[n][37] under gravity g: with the
+ * shifted-equilibrium forcing a collision changes the momentum by rho g and the kinetic energy
+ * sum f xi^2 / 2 by rho (u.g + |g|^2 / 2) while keeping rho and T, so the time averages of the
+ * pre- and post-collision momentum and energy are those of the post-collision state minus half
+ * of these changes: u_h = u_post - g / 2 and, from rho (|u_h|^2 + D T_h) = the averaged
+ * energy, T_h = T_post + |g|^2 / (4 D). rho is unchanged. */
+void or_moments_half_step(size_t n, const double* f, double gx, double gy, double* rho, double* ux,
+                          double* uy, double* T) {
+    setup();
+    for (size_t s = 0; s < n; ++s) {
+        moments_site(f + s * NPOP, rho + s, ux + s, uy + s, T + s);
+        ux[s] -= 0.5 * gx;
+        uy[s] -= 0.5 * gy;
+        T[s] += (gx * gx + gy * gy) / (4.0 * DIM);
+    }
+}
+
 /* Run nsteps time steps from interior populations f0[Ly*Lx][37] and store the interior result
- * in f_out (same layout). One step: wall halos (unless y_periodic), pull propagate, collide.
- * Returns 0, or -1 when memory cannot be allocated. */
-int or_run(int Lx, int Ly, double tau, double gx, double gy, double T_top, double T_bottom,
-           int y_periodic, int nsteps, int nthreads, const double* f0, double* f_out) {
+ * in f_out (same layout). One step: wall halos (unless y_periodic; wall_mode 0 = rest
+ * equilibrium at the wall temperature, 1 = mirror closure), pull propagate, collide. Returns 0,
+ * or -1 when memory cannot be allocated. */
+int or_run_walls(int Lx, int Ly, double tau, double gx, double gy, double T_top, double T_bottom,
+                 int y_periodic, int wall_mode, int nsteps, int nthreads, const double* f0,
+                 double* f_out) {
     setup();
     const size_t rows = (size_t)Ly + 2 * HALO;
     const size_t nfull = rows * (size_t)Lx * NPOP;
@@ -237,7 +278,12 @@ int or_run(int Lx, int Ly, double tau, double gx, double gy, double T_top, doubl
     }
     memcpy(a + (size_t)HALO * Lx * NPOP, f0, nint * sizeof(double));
     for (int t = 0; t < nsteps; ++t) {
-        if (!y_periodic) or_walls(Lx, Ly, T_top, T_bottom, a);
+        if (!y_periodic) {
+            if (wall_mode == 1)
+                or_walls_mirror(Lx, Ly, T_top, T_bottom, a);
+            else
+                or_walls(Lx, Ly, T_top, T_bottom, a);
+        }
         or_propagate(Lx, Ly, y_periodic, a, b, nthreads);
         or_collide((size_t)Ly * Lx, b + (size_t)HALO * Lx * NPOP, tau, gx, gy, nthreads);
         double* t2 = a;
@@ -248,4 +294,10 @@ int or_run(int Lx, int Ly, double tau, double gx, double gy, double T_top, doubl
     free(a);
     free(b);
     return 0;
+}
+
+int or_run(int Lx, int Ly, double tau, double gx, double gy, double T_top, double T_bottom,
+           int y_periodic, int nsteps, int nthreads, const double* f0, double* f_out) {
+    return or_run_walls(Lx, Ly, tau, gx, gy, T_top, T_bottom, y_periodic, 0, nsteps, nthreads, f0,
+                        f_out);
 }

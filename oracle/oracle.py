@@ -40,6 +40,11 @@ def lib():
         L.or_run.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                              C.c_double, C.c_int, C.c_int, C.c_int, dp, dp]
         L.or_run.restype = C.c_int
+        L.or_walls_mirror.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, dp]
+        L.or_moments_half_step.argtypes = [C.c_size_t, dp, C.c_double, C.c_double, dp, dp, dp, dp]
+        L.or_run_walls.argtypes = [C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                   C.c_double, C.c_int, C.c_int, C.c_int, C.c_int, dp, dp]
+        L.or_run_walls.restype = C.c_int
         _lib = L
     return _lib
 
@@ -97,26 +102,41 @@ def propagate(src_full, Lx: int, Ly: int, y_periodic: bool, nthreads: int = 1) -
     return dst[3:Ly + 3]
 
 
-def with_walls(f_int, T_top: float, T_bottom: float) -> np.ndarray:
+WALL_MODES = {"rest": 0, "mirror": 1}
+
+
+def with_walls(f_int, T_top: float, T_bottom: float, wall_mode: str = "rest") -> np.ndarray:
     """Interior populations [Ly, Lx, 37] -> full array [Ly+6, Lx, 37] with wall halo rows."""
     f_int = _c(f_int)
     Ly, Lx, _ = f_int.shape
     full = np.zeros((Ly + 6, Lx, NPOP), np.float64)
     full[3:Ly + 3] = f_int
-    lib().or_walls(Lx, Ly, T_top, T_bottom, full.reshape(-1))
+    walls = lib().or_walls_mirror if WALL_MODES[wall_mode] == 1 else lib().or_walls
+    walls(Lx, Ly, T_top, T_bottom, full.reshape(-1))
     return full
 
 
+def moments_half_step(f, gx: float = 0.0, gy: float = 0.0):
+    """Half-step fields (rho, ux, uy, T) of post-collision populations f[..., 37]."""
+    f = _c(f)
+    shape = f.shape[:-1]
+    n = int(np.prod(shape))
+    out = [np.empty(n) for _ in range(4)]
+    lib().or_moments_half_step(n, f.reshape(-1), gx, gy, *out)
+    return tuple(o.reshape(shape) for o in out)
+
+
 def run(f0, tau: float, nsteps: int, gy: float = 0.0, T_top: float = 1.0, T_bottom: float = 1.0,
-        y_periodic: bool = False, gx: float = 0.0, nthreads: int | None = None) -> np.ndarray:
+        y_periodic: bool = False, gx: float = 0.0, nthreads: int | None = None,
+        wall_mode: str = "rest") -> np.ndarray:
     """nsteps time steps (wall halos, pull, collide) from interior populations f0[Ly, Lx, 37]."""
     f0 = _c(f0)
     Ly, Lx, npop = f0.shape
     assert npop == NPOP
     out = np.empty_like(f0)
     nt = default_threads() if nthreads is None else nthreads
-    rc = lib().or_run(Lx, Ly, tau, gx, gy, T_top, T_bottom, int(bool(y_periodic)), nsteps, nt,
-                      f0.reshape(-1), out.reshape(-1))
+    rc = lib().or_run_walls(Lx, Ly, tau, gx, gy, T_top, T_bottom, int(bool(y_periodic)),
+                            WALL_MODES[wall_mode], nsteps, nt, f0.reshape(-1), out.reshape(-1))
     if rc != 0:
         raise MemoryError("oracle could not allocate its lattice")
     return out
