@@ -36,13 +36,14 @@ if ROOT not in sys.path:
 
 LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
 NPOP = 37
-# FP64 work of the fused step per site in this kernel's formulation: 359 FP64 instructions
-# (191 FMA + 95 add + 73 mul; ncu's opcode counters on step_fp64_kernel, per site), i.e.
-# 550 flops with FMA = 2. The FP64 pipe issues one such instruction per lane-slot whatever its
-# kind, so the ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per SM x f_max
-# (the 1.25 TFLOP/s nominal FP64 rate counts an FMA as 2 flops).
-FP64_INST_PER_SITE = 359
-FP64_FLOP_PER_SITE = 550
+# FP64 work of the fused step per site in this kernel's formulation: 293 FP64-pipe instructions
+# (186 FMA + 75 mul + 23 add + 9 integer-to-FP64 conversions; ncu's opcode counters on
+# step_fp64_kernel, per site), i.e. 470 flops with FMA = 2. The moment sums run as exact 96-bit
+# integer sums on the integer pipe. The FP64 pipe issues one such instruction per lane-slot
+# whatever its kind, so the ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per
+# SM x f_max (the 1.25 TFLOP/s nominal FP64 rate counts an FMA as 2 flops).
+FP64_INST_PER_SITE = 293
+FP64_FLOP_PER_SITE = 470
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 SM_COUNT = 152
@@ -50,11 +51,12 @@ FP64_INST_PER_CLK_SM = 2
 SM_MAX_MHZ = 2070.0
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 698.642 MB + 644.271 MB for 2359296 sites, scaled per site. Valid only for the kernel source
-# it was taken on (sha256 of step_fp64.cu and d2q37_gpu.cuh below); otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (698.642176e6 + 644.271360e6) / 2359296,
-                "sources": {"step_fp64.cu": "76b443659be85d70ad400e4077d0a8a430696d9f2a20dd27b3bb805cbb96a075",
-                            "d2q37_gpu.cuh": "4fc41d583a7b75f6a860893613dc2e3f2a7fb7e26d650bc5c1467a5cf947583f"}}
+# 698.451 MB + 645.175 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# it was taken on (sha256 of the files below); otherwise reported as null.
+TRAFFIC_FP64 = {"bytes_per_site": (698.451200e6 + 645.175040e6) / 2359296,
+                "sources": {"step_fp64.cu": "0abbdc17f0c49c061493148a094d8aee8ea20ef9035373627fa5b96fb794b621",
+                            "d2q37_gpu.cuh": "e799c3d0676dd4783c435ef37669924b7c1fe610b5ed2ce10eee8a6d1b32e702",
+                            "fixed96.cuh": "230ce312473f859cc6d2a14a546ddbc82d3e920b1271978c9772d38d0f9c9945"}}
 
 
 def sources_match(table):
@@ -594,7 +596,7 @@ def measure_table1(lb, torch, np, inputs, reps=20):
     """The paper's per-kernel metrics (Table 1) on GB300 at its 1024 x 8192 lattice, FP64:
     separate propagate and collide kernels timed launch by launch (CUDA events), propagate GB/s
     with 592 B per site, collide MLUPS and GF/s (with the paper's ~6600 flop/site, as Table 1
-    derives it, and with this kernel's 550), and Global MLUPS of the two-kernel step and of the
+    derives it, and with this kernel's 470), and Global MLUPS of the two-kernel step and of the
     fused step."""
     Lx, Ly = 1024, 8192
     sites = Lx * Ly
@@ -630,7 +632,7 @@ def measure_table1(lb, torch, np, inputs, reps=20):
             "propagate_GBs": round(FP64_BYTES_PER_SITE * sites / (t_prop * 1e-3) / 1e9, 1),
             "collide_MLUPS": round(coll_mlups, 1),
             "collide_GFs_at_6600_flop_per_site": round(coll_mlups * 6600 / 1e3, 1),
-            "collide_GFs_at_550_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
+            "collide_GFs_at_470_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
             "global_MLUPS_two_kernel": round(sites / ((t_prop + t_coll) * 1e-3) / 1e6, 1),
             "global_MLUPS_fused": round(sites / (t_fused * 1e-3) / 1e6, 1),
             "paper_KNL_7230_flat": {"T_prop_ms": 12.5, "T_coll_ms": 50.3, "propagate_GBs": 398,

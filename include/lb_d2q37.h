@@ -15,8 +15,11 @@
  *   - collide: BGK with relaxation time tau; gravity g by evaluating the equilibrium at
  *     u + tau g and T + tau (1 - tau) |g|^2 / 2;
  *   - x is periodic; below row 0 and above row Ly-1 sit walls: three halo rows per wall hold the
- *     rest equilibrium at the wall temperature with the density of the mirror interior row;
- *   - macroscopic output: rho = sum f, rho u = sum f xi, rho (u^2 + 2 T) = sum f xi^2.
+ *     rest equilibrium at the wall temperature with the density of the mirror interior row
+ *     (LB_WALL_REST), or, as an alternative closure, the equilibrium at the mirror row's
+ *     density, opposite velocity and temperature reflected about the wall value (LB_WALL_MIRROR);
+ *   - macroscopic output: rho = sum f, rho u = sum f xi, rho (u^2 + 2 T) = sum f xi^2; optionally
+ *     the half-step fields that average the pre- and post-collision momentum and energy.
  *
  * Conventions:
  *   - Host fields are row-major [Ly][Lx] float64 (x fastest). Populations exchanged with the
@@ -50,12 +53,15 @@ typedef enum {
     LB_ERR_CUDA = 3,      /* a CUDA call failed; see lb_last_error() */
     LB_ERR_NONFINITE = 4, /* a site produced a non-finite or non-positive density or temperature */
     LB_ERR_STATE = 5,     /* call not valid in the context's current state */
-    LB_ERR_RANGE = 6      /* LB_FP32SPLIT: a deviation |f - w| reached 1, outside the exact-split
-                             accumulation range */
+    LB_ERR_RANGE = 6      /* a population outside the exact-accumulation range: LB_FP32SPLIT, a
+                             deviation |f - w| reached 1; LB_FP64, a finite |f| reached 16 (the
+                             moment sums are exact 96-bit fixed-point sums with quantum 2^-80) */
 } lb_status;
 
 typedef enum {
-    LB_FP64 = 0,   /* populations stored and collided in FP64 */
+    LB_FP64 = 0,   /* populations stored and collided in FP64; the moment sums are accumulated
+                      exactly in 96-bit fixed point on the integer pipe and rounded to FP64 once
+                      (at least as accurate as FP64 summation; GB300's FP64 pipe binds the step) */
     LB_FP32DEV = 1,  /* populations stored as FP32 deviations f - w; FP32 collide, FP64 moment
                         accumulation and FP64 conservation projection */
     LB_FP32SPLIT = 2 /* same storage and FP32 collide; the moment sums and the projection residual
@@ -65,6 +71,19 @@ typedef enum {
                         GB300 is 1/64 of FP32 */
 } lb_precision;
 
+/* Wall closure (the paper defers boundary conditions to its references; Table 1 counts them in
+ * the "Global" time). Halo row y = -1 - k mirrors interior row k and y = Ly + k mirrors row
+ * Ly - 1 - k (k = 0, 1, 2); the fields of a mirror site are the moments of its current populations
+ * (after a step: the post-collision ones, rho, u + g, T). */
+typedef enum {
+    LB_WALL_REST = 0,  /* f_eq(rho_mirror, 0, T_wall): a rest gas at the wall temperature */
+    LB_WALL_MIRROR = 1 /* f_eq(rho_mirror, -u_mirror, 2 T_wall - T_mirror): linear interpolation
+                          between a row and its halo row gives u = 0 and T = T_wall half a site
+                          outside the last interior row (no-slip isothermal wall). A non-positive
+                          reflected temperature sets the LB_ERR_NONFINITE flag and that halo site
+                          gets the LB_WALL_REST value instead */
+} lb_wall_mode;
+
 typedef struct {
     int Lx, Ly;           /* lattice size; 4 <= Lx, 4 <= Ly, Lx * Ly < 2^31 */
     double tau;           /* BGK relaxation time, > 0.5 */
@@ -73,6 +92,7 @@ typedef struct {
     double T_bottom;      /* wall temperature below row 0 */
     int y_periodic;       /* 0: walls at top/bottom; 1: periodic in y (no walls) */
     int precision;        /* lb_precision */
+    int wall_mode;        /* lb_wall_mode (ignored when y_periodic) */
     void* stream;         /* cudaStream_t or NULL */
     void* workspace;      /* caller-owned device memory or NULL */
     size_t workspace_bytes;
@@ -134,6 +154,15 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T);
 
 /* Same into caller-owned device arrays of Lx*Ly float64 (any may be NULL). Asynchronous. */
 lb_status lb_moments_device(lb_ctx* c, double* rho, double* ux, double* uy, double* T);
+
+/* Half-step ("physical") fields of the current populations, taken as the post-collision state a
+ * step leaves: with the shifted-equilibrium forcing a collision adds rho g to the momentum and
+ * rho (u.g + |g|^2 / 2) to the kinetic energy sum f xi^2 / 2 and keeps rho and T, so averaging
+ * the pre- and post-collision momentum and energy gives u_h = u - g / 2 and
+ * T_h = T + |g|^2 / (4 D) (D = 2) from the stored moments (rho, u, T); rho is unchanged. The
+ * paper reports no fields (the cited D2Q37 works use these); with g = 0 they equal lb_moments.
+ * Caller-owned host arrays [Ly][Lx] float64 (any may be NULL). Synchronous. */
+lb_status lb_moments_half_step(lb_ctx* c, double* rho, double* ux, double* uy, double* T);
 
 /* Copy the current interior populations to host f[37][Ly][Lx] float64 (FP32DEV contexts return
  * w + deviation). Synchronous. */

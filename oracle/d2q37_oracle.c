@@ -228,16 +228,25 @@ void or_walls(int Lx, int Ly, double T_top, double T_bottom, double* f) {
  * mirror row Ly - 1 - k. The fields of a mirror site are the moments of its current populations.
  * Linear interpolation between a row and its mirror halo row then gives zero velocity and the
  * wall temperature exactly on the plane half a site outside the last interior row (y = -1/2 and
- * y = Ly - 1/2): a no-slip wall at a fixed temperature. */
+ * y = Ly - 1/2): a no-slip wall at a fixed temperature. A mirror site hotter than twice the wall
+ * temperature has no positive reflection; its halo site gets the rest closure instead. */
+static void mirror_site(double rho, double ux, double uy, double T, double T_wall, double* out) {
+    const double Th = 2.0 * T_wall - T;
+    if (Th > 0.0)
+        feq_site(rho, -ux, -uy, Th, out);
+    else
+        feq_site(rho, 0.0, 0.0, T_wall, out); /* not reflectable: the rest closure */
+}
+
 void or_walls_mirror(int Lx, int Ly, double T_top, double T_bottom, double* f) {
     setup();
     for (int k = 0; k < HALO; ++k)
         for (int x = 0; x < Lx; ++x) {
             double rho, ux, uy, T;
             moments_site(f + ((size_t)(k + HALO) * Lx + x) * NPOP, &rho, &ux, &uy, &T);
-            feq_site(rho, -ux, -uy, 2.0 * T_bottom - T, f + ((size_t)(HALO - 1 - k) * Lx + x) * NPOP);
+            mirror_site(rho, ux, uy, T, T_bottom, f + ((size_t)(HALO - 1 - k) * Lx + x) * NPOP);
             moments_site(f + ((size_t)(Ly - 1 - k + HALO) * Lx + x) * NPOP, &rho, &ux, &uy, &T);
-            feq_site(rho, -ux, -uy, 2.0 * T_top - T, f + ((size_t)(Ly + HALO + k) * Lx + x) * NPOP);
+            mirror_site(rho, ux, uy, T, T_top, f + ((size_t)(Ly + HALO + k) * Lx + x) * NPOP);
         }
 }
 

@@ -83,7 +83,7 @@ struct ShellCoef32 {
 struct StepParams {
     int Lx, Ly;
     int y_periodic;
-    int pad0;
+    int wall_mode;         // lb_wall_mode: 0 rest-equilibrium halo rows, 1 mirror closure
     long long plane;       // elements per population plane, (Ly + 2*HALO) * Lx
     double r;              // thermal scale, xi = r c
     double r2;             // r^2
@@ -92,6 +92,7 @@ struct StepParams {
     double gx, gy;         // gravity
     double tgx, tgy;       // tau * g
     double dT_force;       // tau (1 - tau) |g|^2 / D
+    double T_bot, T_top;   // wall temperatures below row 0 and above row Ly - 1
     ShellCoef sh[NSHELL];
     double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population
     double wall_top[NPOP]; // same at T_top
@@ -103,5 +104,86 @@ struct StepParams {
     long long pull_b32[NPOP];
     long long plane_b32[NPOP];
 };
+
+// The equilibrium of one site (Sec. 3 model: 4th-order Hermite expansion, D = 2) in FP64, handed
+// population by population to sink(i, f_eq_i) in the library's order. With theta = T - 1,
+// u2 = |u|^2 and a = xi.u, per shell f_eq(+-c) = w rho (E +- O), E = A0 + a^2 (A2 + a^2 / 24),
+// O = a (B1 + a^2 / 6). Used on the wall rows only.
+template <class Sink>
+__device__ __forceinline__ void for_each_equilibrium(const StepParams& P, double rho, double ux,
+                                                     double uy, double T, Sink&& sink) {
+    const double th = T - 1.0;
+    const double u2 = ux * ux + uy * uy;
+    const double a00 = fma(u2, fma(u2, 0.125, -0.5), 1.0);
+    const double a20 = fma(u2, -0.25, 0.5);
+    const double b10 = fma(u2, -0.5, 1.0);
+    const double thu2 = th * u2, th2 = th * th;
+    const double urx = P.r * ux, ury = P.r * uy;
+    sink(0, rho * P.sh[0].w * fma(P.sh[0].gamma, th2, fma(P.sh[0].beta, thu2, fma(P.sh[0].alpha, th, a00))));
+#pragma unroll
+    for (int i = 1; i <= NPAIR; ++i) {
+        const ShellCoef& c = P.sh[shellh(i)];
+        const double A0 = fma(c.gamma, th2, fma(c.beta, thu2, fma(c.alpha, th, a00)));
+        const double A2 = fma(c.delta, th, a20);
+        const double B1 = fma(c.eps, th, b10);
+        const double a = fma((double)cxh(i), urx, (double)cyh(i) * ury);
+        const double a2 = a * a;
+        const double e = fma(a2, fma(a2, 1.0 / 24.0, A2), A0);
+        const double o = a * fma(a2, 1.0 / 6.0, B1);
+        const double W = rho * c.w;
+        sink(i, W * (e + o));
+        sink(i + NPAIR, W * (e - o));
+    }
+}
+
+// Halo row y_h (0..2 below the lattice, Ly+3..Ly+5 above, in padded row numbers) of the mirror
+// closure: the equilibrium at the mirror site's density, the opposite of its velocity and the
+// temperature 2 T_wall - T. Returns false (and writes nothing) when that temperature is not
+// positive. The caller stores sink(i, f_eq_i).
+template <class Sink>
+__device__ __forceinline__ bool mirror_halo(const StepParams& P, bool bottom, double rho, double ux,
+                                            double uy, double T, Sink&& sink) {
+    const double Th = 2.0 * (bottom ? P.T_bot : P.T_top) - T;
+    if (!(Th > 0.0)) return false;
+    for_each_equilibrium(P, rho, -ux, -uy, Th, sink);
+    return true;
+}
+
+// Half-step fields from the moments (u, T) of a post-collision state: the shifted-equilibrium
+// collision adds g to u and keeps T, and the mean of the pre- and post-collision momentum and
+// energy gives u - g / 2 and T + |g|^2 / (4 D).
+__device__ __forceinline__ void half_step_shift(const StepParams& P, double& ux, double& uy, double& T) {
+    ux -= 0.5 * P.gx;
+    uy -= 0.5 * P.gy;
+    T += (P.gx * P.gx + P.gy * P.gy) / (4.0 * DIM);
+}
+
+// The wall halo rows that interior site (x, y) feeds, written after its collide: halo row -1-y if
+// y < 3, halo row Ly + (Ly-1-y) if y >= Ly - 3. (rho, ux, uy, T) are the site's post-collision
+// fields. store(i, o, v) writes FP64 value v of population i at element offset o of a plane.
+// Rest closure: rho times the rest equilibrium per unit density at the wall temperature; mirror
+// closure: mirror_halo (a non-positive reflected temperature sets flag bit 1 and that halo site
+// gets the rest closure instead).
+template <class Store>
+__device__ __forceinline__ void write_wall_rows(const StepParams& P, int x, int y, double rho, double ux,
+                                                double uy, double T, int* __restrict__ flag,
+                                                Store&& store) {
+    if (P.y_periodic) return;
+    const int Lx = P.Lx, Ly = P.Ly;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const bool bottom = side == 0;
+        if (bottom ? (y >= HALO) : (y < Ly - HALO)) continue;
+        const long long o = bottom ? (long long)(HALO - 1 - y) * Lx + x
+                                   : (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
+        if (P.wall_mode == 1) {
+            if (mirror_halo(P, bottom, rho, ux, uy, T, [&](int i, double v) { store(i, o, v); })) continue;
+            atomicOr(flag, 1);  // not reflectable: flag it and fall back to the rest closure
+        }
+        const double* wr = bottom ? P.wall_bot : P.wall_top;
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i) store(i, o, rho * wr[i]);
+    }
+}
 
 }  // namespace lbg

@@ -67,9 +67,9 @@ ensemble_step_kernel(const StepParams Pc, const MemberDesc* __restrict__ members
             const int y = it.z + (k >> tx_log2);
             if (x < sP.Lx && y < sP.Ly) {
                 if (kSplit)
-                    fp32split_site(s_src, s_dst, Pc, sP, x, y, flag);  // constants from Pc
+                    fp32split_site<false>(s_src, s_dst, Pc, sP, x, y, flag);  // constants from Pc
                 else
-                    fp32dev_site(s_src, s_dst, sP, x, y, flag);
+                    fp32dev_site<false>(s_src, s_dst, sP, x, y, flag);
             }
         }
     }
@@ -190,6 +190,7 @@ lb_status check_members(int n, const lb_params* m) {
         if (p.Lx < 4 || p.Ly < 4 || (long long)p.Lx * ((long long)p.Ly + 2 * HALO) >= (1ll << 31) - 1)
             return LB_ERR_ARG;
         if (!(p.tau > 0.5) || !(p.T_top > 0.0) || !(p.T_bottom > 0.0)) return LB_ERR_ARG;
+        if (p.wall_mode != LB_WALL_REST) return LB_ERR_ARG;  // members use the rest closure
     }
     return LB_OK;
 }
@@ -373,7 +374,7 @@ lb_status lb_ensemble_init(int n, const lb_params* members, const double* const*
                                      cudaMemcpyHostToDevice, e->stream);
             if (ce == cudaSuccess)
                 ce = launch_init_fp32dev(e->stage, e->stage + ns, e->stage + 2 * ns, e->stage + 3 * ns,
-                                         e->buf0[k], e->sp[k], e->stream);
+                                         e->buf0[k], e->sp[k], e->flag, e->stream);
             if (ce == cudaSuccess) ce = cudaStreamSynchronize(e->stream);  // staging is reused
         }
         if (ce != cudaSuccess) {
@@ -491,7 +492,7 @@ lb_status lb_ensemble_moments(lb_ensemble* e, int k, double* rho, double* ux, do
     const size_t n = e->sites[k];
     const float* cur = e->cur ? e->buf1[k] : e->buf0[k];
     ENS_CUDA(launch_moments_fp32dev(cur, e->sp[k], e->stage, e->stage + n, e->stage + 2 * n,
-                                    e->stage + 3 * n, e->stream));
+                                    e->stage + 3 * n, 0, e->stream));
     double* dst[4] = {rho, ux, uy, T};
     for (int f = 0; f < 4; ++f)
         if (dst[f])

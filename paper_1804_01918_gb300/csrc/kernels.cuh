@@ -24,10 +24,11 @@ cudaError_t launch_propagate_fp64(const double* src, double* dst, const StepPara
                                   cudaStream_t s);
 cudaError_t launch_collide_fp64(double* f, const StepParams& P, int* flag, cudaStream_t s);
 cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy,
-                             const double* T, double* f, const StepParams& P, cudaStream_t s);
+                             const double* T, double* f, const StepParams& P, int* flag, cudaStream_t s);
+// half_step != 0: the half-step fields (u - g/2, T + |g|^2 / (4 D)) instead of the plain moments
 cudaError_t launch_moments_fp64(const double* f, const StepParams& P, double* rho, double* ux,
-                                double* uy, double* T, cudaStream_t s);
-cudaError_t launch_halo_fp64(double* f, const StepParams& P, cudaStream_t s);
+                                double* uy, double* T, int half_step, cudaStream_t s);
+cudaError_t launch_halo_fp64(double* f, const StepParams& P, int* flag, cudaStream_t s);
 
 // ---- FP32 deviation populations (step_fp32dev.cu) ----
 cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& P, int* flag,
@@ -43,10 +44,10 @@ int fp32split_tma_grid();
 cudaError_t launch_propagate_fp32dev(const float* src, float* dst, const StepParams& P,
                                      cudaStream_t s);
 cudaError_t launch_init_fp32dev(const double* rho, const double* ux, const double* uy,
-                                const double* T, float* f, const StepParams& P, cudaStream_t s);
+                                const double* T, float* f, const StepParams& P, int* flag, cudaStream_t s);
 cudaError_t launch_moments_fp32dev(const float* f, const StepParams& P, double* rho, double* ux,
-                                   double* uy, double* T, cudaStream_t s);
-cudaError_t launch_halo_fp32dev(float* f, const StepParams& P, cudaStream_t s);
+                                   double* uy, double* T, int half_step, cudaStream_t s);
+cudaError_t launch_halo_fp32dev(float* f, const StepParams& P, int* flag, cudaStream_t s);
 // plane i interior: FP64 absolute populations <-> FP32 deviations
 cudaError_t launch_plane_to_dev32(const double* src, float* dst_plane_interior, double w,
                                   long long n, cudaStream_t s);

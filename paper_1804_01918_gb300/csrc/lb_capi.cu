@@ -74,6 +74,7 @@ lb_status check_params(const lb_params* p) {
         return LB_ERR_ARG;
     if (p->precision != LB_FP64 && p->precision != LB_FP32DEV && p->precision != LB_FP32SPLIT)
         return LB_ERR_ARG;
+    if (p->wall_mode != LB_WALL_REST && p->wall_mode != LB_WALL_MIRROR) return LB_ERR_ARG;
     return LB_OK;
 }
 
@@ -92,6 +93,9 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
     sp.Lx = p.Lx;
     sp.Ly = p.Ly;
     sp.y_periodic = p.y_periodic ? 1 : 0;
+    sp.wall_mode = p.wall_mode == LB_WALL_MIRROR ? 1 : 0;
+    sp.T_bot = p.T_bottom;
+    sp.T_top = p.T_top;
     sp.plane = (long long)p.Lx * ((long long)p.Ly + 2 * HALO);
     const double r = thermal_scale();
     sp.r = r;
@@ -249,12 +253,13 @@ lb_status read_flag(lb_ctx* c) {
     return LB_OK;
 }
 
-lb_status launch_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+lb_status launch_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T, int half_step = 0) {
     cudaError_t e;
     if (c->p.precision == LB_FP64)
-        e = launch_moments_fp64((const double*)c->buf[c->cur], c->sp, rho, ux, uy, T, c->stream);
+        e = launch_moments_fp64((const double*)c->buf[c->cur], c->sp, rho, ux, uy, T, half_step, c->stream);
     else
-        e = launch_moments_fp32dev((const float*)c->buf[c->cur], c->sp, rho, ux, uy, T, c->stream);
+        e = launch_moments_fp32dev((const float*)c->buf[c->cur], c->sp, rho, ux, uy, T, half_step,
+                                   c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "moments kernel launch");
     return LB_OK;
 }
@@ -262,8 +267,8 @@ lb_status launch_moments(lb_ctx* c, double* rho, double* ux, double* uy, double*
 lb_status rewrite_halos(lb_ctx* c) {
     if (c->p.y_periodic) return LB_OK;
     cudaError_t e = c->p.precision == LB_FP64
-                        ? launch_halo_fp64((double*)c->buf[c->cur], c->sp, c->stream)
-                        : launch_halo_fp32dev((float*)c->buf[c->cur], c->sp, c->stream);
+                        ? launch_halo_fp64((double*)c->buf[c->cur], c->sp, c->flag, c->stream)
+                        : launch_halo_fp32dev((float*)c->buf[c->cur], c->sp, c->flag, c->stream);
     if (e != cudaSuccess) return cuda_fail(e, "halo kernel launch");
     return LB_OK;
 }
@@ -380,10 +385,10 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
         if (e != cudaSuccess) { rs = cuda_fail(e, "cudaMemsetAsync(flag)"); break; }
         if (p->precision == LB_FP64)
             e = launch_init_fp64(c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n,
-                                 (double*)c->buf[0], c->sp, c->stream);
+                                 (double*)c->buf[0], c->sp, c->flag, c->stream);
         else
             e = launch_init_fp32dev(c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n,
-                                    (float*)c->buf[0], c->sp, c->stream);
+                                    (float*)c->buf[0], c->sp, c->flag, c->stream);
         if (e != cudaSuccess) { rs = cuda_fail(e, "init kernel launch"); break; }
         e = cudaStreamSynchronize(c->stream);
         if (e != cudaSuccess) { rs = cuda_fail(e, "cudaStreamSynchronize(init)"); break; }
@@ -464,10 +469,11 @@ lb_status lb_moments_device(lb_ctx* c, double* rho, double* ux, double* uy, doub
                           uy ? uy : c->stage + 2 * n, T ? T : c->stage + 3 * n);
 }
 
-lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+namespace {
+lb_status moments_to_host(lb_ctx* c, double* rho, double* ux, double* uy, double* T, int half_step) {
     if (!c) return LB_ERR_ARG;
     const size_t n = (size_t)c->p.Lx * c->p.Ly;
-    lb_status st = launch_moments(c, c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n);
+    lb_status st = launch_moments(c, c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n, half_step);
     if (st != LB_OK) return st;
     double* dst[4] = {rho, ux, uy, T};
     for (int k = 0; k < 4; ++k)
@@ -476,6 +482,15 @@ lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) 
                                     cudaMemcpyDeviceToHost, c->stream));
     LB_CUDA(cudaStreamSynchronize(c->stream));
     return read_flag(c);
+}
+}  // namespace
+
+lb_status lb_moments(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    return moments_to_host(c, rho, ux, uy, T, 0);
+}
+
+lb_status lb_moments_half_step(lb_ctx* c, double* rho, double* ux, double* uy, double* T) {
+    return moments_to_host(c, rho, ux, uy, T, 1);
 }
 
 lb_status lb_get_populations(lb_ctx* c, double* f) {

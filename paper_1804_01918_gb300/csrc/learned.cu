@@ -576,7 +576,7 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
                     fmax = fmaxf(fmax, fabsf((float)shell_w(shell_of(i)) + d[i]));
                 }
             }
-            split_store(dst, P, x, y, dl, s.s0);
+            split_store(dst, P, x, y, dl, s, flag);
         }
         if (!alive) break;
         if (check) {

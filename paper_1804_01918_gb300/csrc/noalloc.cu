@@ -92,10 +92,10 @@ extern "C" lb_status lb_moments_noalloc(const lb_params* p, const void* f, doubl
     cudaStream_t s = (cudaStream_t)p->stream;
     if (p->precision == LB_FP64)
         e = launch_moments_fp64((const double*)f, sp, scratch, scratch + n, scratch + 2 * n,
-                                scratch + 3 * n, s);
+                                scratch + 3 * n, 0, s);
     else
         e = launch_moments_fp32dev((const float*)f, sp, scratch, scratch + n, scratch + 2 * n,
-                                   scratch + 3 * n, s);
+                                   scratch + 3 * n, 0, s);
     double* dst[4] = {rho, ux, uy, T};
     for (int k = 0; k < 4 && e == cudaSuccess; ++k)
         if (dst[k])

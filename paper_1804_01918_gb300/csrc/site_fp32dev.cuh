@@ -139,8 +139,55 @@ struct Collide32<0> {
 
 }  // namespace
 
+// Wall halo rows of an FP32-deviation lattice fed by site (x, y), from its post-collision fields.
+// Not inlined: the six wall rows' FP64 code then costs the per-site path no registers.
+static __device__ __noinline__ void split_wall_rows(float* __restrict__ dst, const StepParams& P, int x, int y,
+                                             double rho, double ux, double uy, double T,
+                                             int* __restrict__ flag) {
+    const long long plane = P.plane;
+    write_wall_rows(P, x, y, rho, ux, uy, T, flag, [&](int i, long long o, double v) {
+        __stcs(dst + (long long)i * plane + o, (float)(v - shell_w(shell_of(i))));
+    });
+}
+
+// Rest-closure wall halo rows fed by site (x, y): rho times the rest equilibrium per unit density
+// at the wall temperature, stored as FP32 deviations.
+__device__ __forceinline__ void rest_wall_rows32(float* __restrict__ dst, const StepParams& P, int x, int y,
+                                                 double rho) {
+    const int Lx = P.Lx, Ly = P.Ly;
+    const long long plane = P.plane;
+    if (y < HALO) {
+        const long long o = (long long)(HALO - 1 - y) * Lx + x;
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i)
+            __stcs(dst + (long long)i * plane + o, (float)fma(rho, P.wall_bot[i], -shell_w(shell_of(i))));
+    }
+    if (y >= Ly - HALO) {
+        const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
+#pragma unroll
+        for (int i = 0; i < NPOP; ++i)
+            __stcs(dst + (long long)i * plane + o, (float)fma(rho, P.wall_top[i], -shell_w(shell_of(i))));
+    }
+}
+
+// Wall halo rows of an FP32-deviation lattice fed by site (x, y) on rows 0..2 / Ly-3..Ly-1, from
+// its post-collision fields. kMirror = false compiles the rest closure only (kernels whose
+// lattices all use it); otherwise the mirror closure runs out of line, so its FP64 code costs the
+// per-site path no registers.
+template <bool kMirror>
+__device__ __forceinline__ void wall_rows32(float* __restrict__ dst, const StepParams& P, int x, int y,
+                                            double rho, double ux, double uy, double T,
+                                            int* __restrict__ flag) {
+    if (P.y_periodic || (y >= HALO && y < P.Ly - HALO)) return;
+    if (kMirror && P.wall_mode == 1)
+        split_wall_rows(dst, P, x, y, rho, ux, uy, T, flag);
+    else
+        rest_wall_rows32(dst, P, x, y, rho);
+}
+
 // One fused FP32-deviation step of site (x, y): src/dst are the member's two population copies,
 // P its parameters (kernel parameter space or shared memory). Shared with the ensemble kernel.
+template <bool kMirror = true>
 __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, float* __restrict__ dst,
                                              const StepParams& P, int x, int y,
                                              int* __restrict__ flag) {
@@ -206,20 +253,8 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
         __stcs(dst + poff(i, plane) + dsto, fmaf((float)shell_w(shell_of(i)), corr, d[i]));
     }
 
-    if (!P.y_periodic) {
-        if (y < HALO) {
-            const long long o = (long long)(HALO - 1 - y) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i)
-                __stcs(dst + poff(i, plane) + o, (float)fma(m.rho, P.wall_bot[i], -shell_w(shell_of(i))));
-        }
-        if (y >= Ly - HALO) {
-            const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i)
-                __stcs(dst + poff(i, plane) + o, (float)fma(m.rho, P.wall_top[i], -shell_w(shell_of(i))));
-        }
-    }
+    // wall halo rows from the post-collision fields (rho, u + g, T), stored as FP32 deviations
+    wall_rows32<kMirror>(dst, P, x, y, m.rho, m.ux + gx, m.uy + gy, m.T, flag);
 }
 
 }  // namespace lbg
@@ -397,33 +432,18 @@ __device__ __forceinline__ void split_project(float* d, const StepParams& C, con
     }
 }
 
-// Store a site's deviations and, on wall rows, the wall halo rows (rest equilibrium at the wall
-// temperature with the summed density; FP64 on the six wall rows only).
+// Store a site's deviations and, on wall rows, the wall halo rows from the site's post-collision
+// fields (rho, u + g, T; FP64 arithmetic on the six wall rows only).
+template <bool kMirror = true>
 __device__ __forceinline__ void split_store(float* __restrict__ dst, const StepParams& P, int x,
-                                            int y, const float* d, float s0) {
-    const int Lx = P.Lx, Ly = P.Ly;
-    const long long plane = P.plane;
-    const long long dsto = (long long)(y + HALO) * Lx + x;
+                                            int y, const float* d, const SplitPre& s,
+                                            int* __restrict__ flag) {
+    const long long dsto = (long long)(y + HALO) * P.Lx + x;
     char* const base = reinterpret_cast<char*>(dst + dsto);
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) __stcs(reinterpret_cast<float*>(base + P.plane_b32[i]), d[i]);
-    if (!P.y_periodic) {
-        const double rho_d = 1.0 + (double)s0;
-        if (y < HALO) {
-            const long long o = (long long)(HALO - 1 - y) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i)
-                __stcs(dst + (long long)i * plane + o,
-                       (float)fma(rho_d, P.wall_bot[i], -shell_w(shell_of(i))));
-        }
-        if (y >= Ly - HALO) {
-            const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i)
-                __stcs(dst + (long long)i * plane + o,
-                       (float)fma(rho_d, P.wall_top[i], -shell_w(shell_of(i))));
-        }
-    }
+    wall_rows32<kMirror>(dst, P, x, y, 1.0 + (double)s.s0, (double)s.ux + P.gx, (double)s.uy + P.gy,
+                         (double)s.T, flag);
 }
 
 // One fused FP32-deviation step of site (x, y) with exact-split FP32 moment accumulation and an
@@ -453,6 +473,7 @@ __device__ __forceinline__ void pull32(const float* __restrict__ src, float* d, 
         Pull32<NPOP - 1>::run(src, d, x, y, M.Lx, M.Ly, M.y_periodic, M.plane);
 }
 
+template <bool kMirror = true>
 __device__ __forceinline__ void fp32split_site(const float* __restrict__ src, float* __restrict__ dst,
                                                const StepParams& C, const StepParams& M, int x, int y,
                                                int* __restrict__ flag) {
@@ -462,7 +483,7 @@ __device__ __forceinline__ void fp32split_site(const float* __restrict__ src, fl
     split_pre(d, C, s, flag);
     split_collide(d, C, M, s);
     split_project(d, C, M, s);
-    split_store(dst, M, x, y, d, s.s0);
+    split_store<kMirror>(dst, M, x, y, d, s, flag);
 }
 
 }  // namespace lbg

@@ -99,33 +99,33 @@ init_fp32dev_kernel(const double* __restrict__ rho, const double* __restrict__ u
     }
 }
 
-__global__ void halo_fp32dev_kernel(float* __restrict__ f, const StepParams P) {
+// Wall halos of f from the current interior rows 0..2 and Ly-3..Ly-1 (their FP64 moments), as
+// the step writes them: thread t handles interior row k = t / Lx of each wall.
+__global__ void halo_fp32dev_kernel(float* __restrict__ f, const StepParams P, int* __restrict__ flag) {
     const int Lx = P.Lx, Ly = P.Ly;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= HALO * Lx) return;
     const int k = t / Lx;
     const int x = t - k * Lx;
-    const long long ib = (long long)(HALO + k) * Lx + x;
-    const long long it = (long long)(HALO + Ly - 1 - k) * Lx + x;
-    double rb = 1.0, rt = 1.0;
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        rb += (double)f[poff(i, P.plane) + ib];
-        rt += (double)f[poff(i, P.plane) + it];
-    }
-    const long long ob = (long long)(HALO - 1 - k) * Lx + x;
-    const long long ot = (long long)(Ly + HALO + k) * Lx + x;
+    for (int side = 0; side < 2; ++side) {
+        const int y = side == 0 ? k : Ly - 1 - k;
+        if (side == 1 && y < HALO) continue;  // lattices with Ly < 6: that row was handled already
+        const long long o = (long long)(HALO + y) * Lx + x;
+        float d[NPOP];
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        const double w = shell_w(shell_of(i));
-        f[poff(i, P.plane) + ob] = (float)fma(rb, P.wall_bot[i], -w);
-        f[poff(i, P.plane) + ot] = (float)fma(rt, P.wall_top[i], -w);
+        for (int i = 0; i < NPOP; ++i) d[i] = f[poff(i, P.plane) + o];
+        const Macro m = macro_of(dev_sums(d), P.r, P.r2);
+        write_wall_rows(P, x, y, m.rho, m.ux, m.uy, m.T, flag, [&](int i, long long oh, double v) {
+            f[poff(i, P.plane) + oh] = (float)(v - shell_w(shell_of(i)));
+        });
     }
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
 moments_fp32dev_kernel(const float* __restrict__ f, const StepParams P, double* __restrict__ rho,
-                       double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ T) {
+                       double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ T,
+                       int half_step) {
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
@@ -135,7 +135,8 @@ moments_fp32dev_kernel(const float* __restrict__ f, const StepParams P, double* 
     float d[NPOP];
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) d[i] = f[poff(i, P.plane) + o];
-    const Macro m = macro_of(dev_sums(d), P.r, P.r2);
+    Macro m = macro_of(dev_sums(d), P.r, P.r2);
+    if (half_step) half_step_shift(P, m.ux, m.uy, m.T);
     rho[site] = m.rho;
     ux[site] = m.ux;
     uy[site] = m.uy;
@@ -180,22 +181,22 @@ cudaError_t launch_propagate_fp32dev(const float* src, float* dst, const StepPar
 }
 
 cudaError_t launch_init_fp32dev(const double* rho, const double* ux, const double* uy,
-                                const double* T, float* f, const StepParams& P, cudaStream_t s) {
+                                const double* T, float* f, const StepParams& P, int* flag, cudaStream_t s) {
     init_fp32dev_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(rho, ux, uy, T, f, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || P.y_periodic) return e;
-    return launch_halo_fp32dev(f, P, s);
+    return launch_halo_fp32dev(f, P, flag, s);
 }
 
 cudaError_t launch_moments_fp32dev(const float* f, const StepParams& P, double* rho, double* ux,
-                                   double* uy, double* T, cudaStream_t s) {
-    moments_fp32dev_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(f, P, rho, ux, uy, T);
+                                   double* uy, double* T, int half_step, cudaStream_t s) {
+    moments_fp32dev_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(f, P, rho, ux, uy, T, half_step);
     return cudaGetLastError();
 }
 
-cudaError_t launch_halo_fp32dev(float* f, const StepParams& P, cudaStream_t s) {
+cudaError_t launch_halo_fp32dev(float* f, const StepParams& P, int* flag, cudaStream_t s) {
     const int n = HALO * P.Lx;
-    halo_fp32dev_kernel<<<(n + 127) / 128, 128, 0, s>>>(f, P);
+    halo_fp32dev_kernel<<<(n + 127) / 128, 128, 0, s>>>(f, P, flag);
     return cudaGetLastError();
 }
 

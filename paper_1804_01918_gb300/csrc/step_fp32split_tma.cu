@@ -135,7 +135,7 @@ step_fp32split_tma_kernel(const __grid_constant__ CUtensorMap tsrc, const float*
             split_pre(d, P, sp, flag);
             split_collide(d, P, P, sp);
             split_project(d, P, P, sp);
-            split_store(dst, P, x, y, d, sp.s0);
+            split_store(dst, P, x, y, d, sp, flag);
         }
     }
     // drain: wait (bounded) for copies still in flight before the block's shared memory goes away

@@ -20,6 +20,7 @@
 #include <cstdint>
 
 #include "d2q37_gpu.cuh"
+#include "fixed96.cuh"
 #include "kernels.cuh"
 
 namespace lbg {
@@ -76,36 +77,52 @@ struct SiteMoments {
 
 // rho, u, T of one site from bins of equal c_x and equal c_y:
 //   rho = sum f, rho u = r sum f c, rho (u^2 + D T) = r^2 sum f |c|^2.
-__device__ __forceinline__ SiteMoments site_moments(const double* f, double r, double r2) {
-    double sx[7], sy[7];
+// The bins and their combinations are exact 96-bit fixed-point sums on the integer pipe
+// (fixed96.cuh); each of the four sums is rounded to FP64 once. *bad gets the status-word bit of a
+// population outside the exact range: 1 for an infinity or NaN, 2 for a finite |f| >= 16, else 0.
+__device__ __forceinline__ SiteMoments site_moments(const double* f, double r, double r2, int* bad) {
+    using namespace fx;
+    I96 bx[7], by[7];
 #pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        sx[k] = 0.0;
-        sy[k] = 0.0;
-    }
+    for (int k = 0; k < 7; ++k) bx[k] = by[k] = zero96();
+    unsigned emax = 0u;
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) {
-        sx[cx_of(i) + 3] += f[i];
-        sy[cy_of(i) + 3] += f[i];
+        const I96 n = to96(f[i], emax);
+        add96(bx[cx_of(i) + 3], n);
+        add96(by[cy_of(i) + 3], n);
     }
-    const double px1 = sx[4] + sx[2], px2 = sx[5] + sx[1], px3 = sx[6] + sx[0];
-    const double mx1 = sx[4] - sx[2], mx2 = sx[5] - sx[1], mx3 = sx[6] - sx[0];
-    const double py1 = sy[4] + sy[2], py2 = sy[5] + sy[1], py3 = sy[6] + sy[0];
-    const double my1 = sy[4] - sy[2], my2 = sy[5] - sy[1], my3 = sy[6] - sy[0];
-    const double rho = sx[3] + px1 + px2 + px3;
-    const double jx = fma(3.0, mx3, fma(2.0, mx2, mx1));
-    const double jy = fma(3.0, my3, fma(2.0, my2, my1));
-    const double ex = fma(9.0, px3, fma(4.0, px2, px1));
-    const double ey = fma(9.0, py3, fma(4.0, py2, py1));
-    const double inv = 1.0 / rho;
+    *bad = emax == 0x7FFu ? 1 : (emax > EXP_LIMIT ? 2 : 0);
+    const I96 px1 = plus96(bx[4], bx[2]), px2 = plus96(bx[5], bx[1]), px3 = plus96(bx[6], bx[0]);
+    const I96 py1 = plus96(by[4], by[2]), py2 = plus96(by[5], by[1]), py3 = plus96(by[6], by[0]);
+    const I96 n0 = plus96(plus96(bx[3], px1), plus96(px2, px3));
+    const I96 nx = plus96(plus96(times3(minus96(bx[6], bx[0])), times2(minus96(bx[5], bx[1]))),
+                          minus96(bx[4], bx[2]));
+    const I96 ny = plus96(plus96(times3(minus96(by[6], by[0])), times2(minus96(by[5], by[1]))),
+                          minus96(by[4], by[2]));
+    const I96 ne = plus96(plus96(plus96(times9(px3), times4(px2)), px1),
+                          plus96(plus96(times9(py3), times4(py2)), py1));
+    // the four sums in units of 2^-48: the scale cancels in u and T
+    const double n0d = to_double48(n0);
+    const double inv = 1.0 / n0d;
     const double rinv = r * inv;
     SiteMoments m;
-    m.rho = rho;
-    m.ux = jx * rinv;
-    m.uy = jy * rinv;
+    m.rho = n0d * 0x1p-48;
+    m.ux = to_double48(nx) * rinv;
+    m.uy = to_double48(ny) * rinv;
     const double u2 = m.ux * m.ux + m.uy * m.uy;
-    m.T = 0.5 * fma(r2 * inv, ex + ey, -u2);
+    m.T = 0.5 * fma(r2 * inv, to_double48(ne), -u2);
     return m;
+}
+
+// xi.u of pair I from the multiples U[k] = k r u_x, V[k] = k r u_y (k = 1, 2, 3): a copy for the
+// axis pairs, one add or subtract for the others.
+template <int I>
+__device__ __forceinline__ double pair_a(const double* U, const double* V) {
+    constexpr int cx = cxh(I), cy = cyh(I);
+    if (cy == 0) return U[cx];
+    if (cx == 0) return cy > 0 ? V[cy] : -V[-cy];
+    return cy > 0 ? U[cx] + V[cy] : U[cx] - V[-cy];
 }
 
 // Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S. With the prefactor
@@ -114,19 +131,11 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
 // W f_eq(+-c) = W E +- W O, and f' = (1 - 1/tau) f + W f_eq -- one multiply (a^2) and 7 FMAs.
 template <int I>
 __device__ __forceinline__ void relax_pair(const double* f, double* __restrict__ dst, long long dsto,
-                                           long long plane, double urx, double ury,
+                                           long long plane, const double* U, const double* V,
                                            const double* WA0, const double* WA2, const double* WB1,
                                            const double* W24, const double* W6, double omc) {
     constexpr int S = shellh(I);
-    constexpr double cx = (double)cxh(I);
-    constexpr double cy = (double)cyh(I);
-    double a;
-    if (cyh(I) == 0)
-        a = cx * urx;
-    else if (cxh(I) == 0)
-        a = cy * ury;
-    else
-        a = fma(cx, urx, cy * ury);
+    const double a = pair_a<I>(U, V);
     const double a2 = a * a;
     const double we = fma(a2, fma(a2, W24[S], WA2[S]), WA0[S]);
     const double q = fma(a2, W6[S], WB1[S]);
@@ -139,20 +148,31 @@ __device__ __forceinline__ void relax_pair(const double* f, double* __restrict__
 template <int I>
 struct RelaxAll {
     __device__ __forceinline__ static void run(const double* f, double* __restrict__ dst,
-                                               long long dsto, long long plane, double urx,
-                                               double ury, const double* WA0, const double* WA2,
+                                               long long dsto, long long plane, const double* U,
+                                               const double* V, const double* WA0, const double* WA2,
                                                const double* WB1, const double* W24, const double* W6,
                                                double omc) {
-        RelaxAll<I - 1>::run(f, dst, dsto, plane, urx, ury, WA0, WA2, WB1, W24, W6, omc);
-        relax_pair<I>(f, dst, dsto, plane, urx, ury, WA0, WA2, WB1, W24, W6, omc);
+        RelaxAll<I - 1>::run(f, dst, dsto, plane, U, V, WA0, WA2, WB1, W24, W6, omc);
+        relax_pair<I>(f, dst, dsto, plane, U, V, WA0, WA2, WB1, W24, W6, omc);
     }
 };
 template <>
 struct RelaxAll<0> {
-    __device__ __forceinline__ static void run(const double*, double*, long long, long long, double,
-                                               double, const double*, const double*, const double*,
+    __device__ __forceinline__ static void run(const double*, double*, long long, long long, const double*,
+                                               const double*, const double*, const double*, const double*,
                                                const double*, const double*, double) {}
 };
+
+// The multiples k r u (k = 1, 2, 3) of the shifted velocity, for pair_a.
+__device__ __forceinline__ void velocity_multiples(double urx, double ury, double* U, double* V) {
+    U[0] = V[0] = 0.0;
+    U[1] = urx;
+    V[1] = ury;
+    U[2] = urx + urx;
+    V[2] = ury + ury;
+    U[3] = U[2] + urx;
+    V[3] = V[2] + ury;
+}
 
 // Per-shell coefficients of the equilibrium at (theta, u2) scaled by prefactor W_s = wscale w_s.
 __device__ __forceinline__ void shell_coefficients(const StepParams& P, double th, double u2,
@@ -206,8 +226,9 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
     double f[NPOP];
     PullAll<NPOP - 1>::run(src, f, x, y, Lx, Ly, P.y_periodic, plane);
 
-    const SiteMoments m = site_moments(f, P.r, P.r2);
-    if (bad_positive(m.rho) || bad_positive(m.T)) atomicOr(flag, 1);
+    int bad;
+    const SiteMoments m = site_moments(f, P.r, P.r2, &bad);
+    if (bad_positive(m.rho) || bad_positive(m.T) || bad) atomicOr(flag, bad ? bad : 1);
 
     // forcing: equilibrium at u + tau g, T + tau (1 - tau) |g|^2 / D
     const double uxs = m.ux + P.tgx;
@@ -219,21 +240,13 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
 
     const long long dsto = (long long)(y + HALO) * Lx + x;
     __stcs(dst + dsto, fma(P.omc, f[0], WA0[0]));
-    RelaxAll<NPAIR>::run(f, dst, dsto, plane, P.r * uxs, P.r * uys, WA0, WA2, WB1, W24, W6, P.omc);
+    double U[4], V[4];
+    velocity_multiples(P.r * uxs, P.r * uys, U, V);
+    RelaxAll<NPAIR>::run(f, dst, dsto, plane, U, V, WA0, WA2, WB1, W24, W6, P.omc);
 
-    if (!P.y_periodic) {
-        // wall halo rows of dst from this row's density (collide conserves it)
-        if (y < HALO) {
-            const long long o = (long long)(HALO - 1 - y) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i) __stcs(dst + plane_off(i, plane) + o, m.rho * P.wall_bot[i]);
-        }
-        if (y >= Ly - HALO) {
-            const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i) __stcs(dst + plane_off(i, plane) + o, m.rho * P.wall_top[i]);
-        }
-    }
+    // wall halo rows of dst from this site's post-collision fields (rho, u + g, T)
+    write_wall_rows(P, x, y, m.rho, m.ux + P.gx, m.uy + P.gy, m.T, flag,
+                    [&](int i, long long o, double v) { __stcs(dst + plane_off(i, plane) + o, v); });
 }
 
 // Collide only, in place (the paper's separate collide kernel, Sec. 3-5 and Table 1): each thread
@@ -252,8 +265,9 @@ collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict_
     double v[NPOP];
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, plane) + o];
-    const SiteMoments m = site_moments(v, P.r, P.r2);
-    if (bad_positive(m.rho) || bad_positive(m.T)) atomicOr(flag, 1);
+    int bad;
+    const SiteMoments m = site_moments(v, P.r, P.r2, &bad);
+    if (bad_positive(m.rho) || bad_positive(m.T) || bad) atomicOr(flag, bad ? bad : 1);
     const double uxs = m.ux + P.tgx;
     const double uys = m.uy + P.tgy;
     const double th = (m.T + P.dT_force) - 1.0;
@@ -261,19 +275,11 @@ collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict_
     double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], W24[NSHELL], W6[NSHELL];
     shell_coefficients_scaled(P, th, u2, m.rho * P.omega, WA0, WA2, WB1, W24, W6);
     __stcs(f + o, fma(P.omc, v[0], WA0[0]));
-    RelaxAll<NPAIR>::run(v, f, o, plane, P.r * uxs, P.r * uys, WA0, WA2, WB1, W24, W6, P.omc);
-    if (!P.y_periodic) {
-        if (y < HALO) {
-            const long long ob = (long long)(HALO - 1 - y) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i) __stcs(f + plane_off(i, plane) + ob, m.rho * P.wall_bot[i]);
-        }
-        if (y >= Ly - HALO) {
-            const long long ot = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i) __stcs(f + plane_off(i, plane) + ot, m.rho * P.wall_top[i]);
-        }
-    }
+    double U[4], V[4];
+    velocity_multiples(P.r * uxs, P.r * uys, U, V);
+    RelaxAll<NPAIR>::run(v, f, o, plane, U, V, WA0, WA2, WB1, W24, W6, P.omc);
+    write_wall_rows(P, x, y, m.rho, m.ux + P.gx, m.uy + P.gy, m.T, flag,
+                    [&](int i, long long oh, double val) { __stcs(f + plane_off(i, plane) + oh, val); });
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
@@ -335,34 +341,34 @@ init_fp64_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
     for (int i = 0; i < NPOP; ++i) f[plane_off(i, P.plane) + o] = fe[i];
 }
 
-// Wall halos of f from the current interior rows: halo row -1-k <- rho(x, k) * wall_bot,
-// halo row Ly+k <- rho(x, Ly-1-k) * wall_top, k = 0, 1, 2.
-__global__ void halo_fp64_kernel(double* __restrict__ f, const StepParams P) {
+// Wall halos of f from the current interior rows 0..2 and Ly-3..Ly-1 (their moments), as the
+// step writes them: thread t handles interior row k = t / Lx of each wall.
+__global__ void halo_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict__ flag) {
     const int Lx = P.Lx, Ly = P.Ly;
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= HALO * Lx) return;
     const int k = t / Lx;
     const int x = t - k * Lx;
-    const long long ib = (long long)(HALO + k) * Lx + x;
-    const long long it = (long long)(HALO + Ly - 1 - k) * Lx + x;
-    double rb = 0.0, rt = 0.0;
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        rb += f[plane_off(i, P.plane) + ib];
-        rt += f[plane_off(i, P.plane) + it];
-    }
-    const long long ob = (long long)(HALO - 1 - k) * Lx + x;
-    const long long ot = (long long)(Ly + HALO + k) * Lx + x;
+    for (int side = 0; side < 2; ++side) {
+        const int y = side == 0 ? k : Ly - 1 - k;
+        if (side == 1 && y < HALO) continue;  // lattices with Ly < 6: that row was handled already
+        const long long o = (long long)(HALO + y) * Lx + x;
+        double v[NPOP];
 #pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        f[plane_off(i, P.plane) + ob] = rb * P.wall_bot[i];
-        f[plane_off(i, P.plane) + ot] = rt * P.wall_top[i];
+        for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, P.plane) + o];
+        int bad;
+        const SiteMoments m = site_moments(v, P.r, P.r2, &bad);
+        if (bad) atomicOr(flag, bad);
+        write_wall_rows(P, x, y, m.rho, m.ux, m.uy, m.T, flag,
+                        [&](int i, long long oh, double val) { f[plane_off(i, P.plane) + oh] = val; });
     }
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
 moments_fp64_kernel(const double* __restrict__ f, const StepParams P, double* __restrict__ rho,
-                    double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ T) {
+                    double* __restrict__ ux, double* __restrict__ uy, double* __restrict__ T,
+                    int half_step) {
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
@@ -372,7 +378,9 @@ moments_fp64_kernel(const double* __restrict__ f, const StepParams P, double* __
     double v[NPOP];
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, P.plane) + o];
-    const SiteMoments m = site_moments(v, P.r, P.r2);
+    int bad;
+    SiteMoments m = site_moments(v, P.r, P.r2, &bad);
+    if (half_step) half_step_shift(P, m.ux, m.uy, m.T);
     rho[site] = m.rho;
     ux[site] = m.ux;
     uy[site] = m.uy;
@@ -404,22 +412,22 @@ cudaError_t launch_propagate_fp64(const double* src, double* dst, const StepPara
 }
 
 cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy,
-                             const double* T, double* f, const StepParams& P, cudaStream_t s) {
+                             const double* T, double* f, const StepParams& P, int* flag, cudaStream_t s) {
     init_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(rho, ux, uy, T, f, P);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess || P.y_periodic) return e;
-    return launch_halo_fp64(f, P, s);
+    return launch_halo_fp64(f, P, flag, s);
 }
 
 cudaError_t launch_moments_fp64(const double* f, const StepParams& P, double* rho, double* ux,
-                                double* uy, double* T, cudaStream_t s) {
-    moments_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(f, P, rho, ux, uy, T);
+                                double* uy, double* T, int half_step, cudaStream_t s) {
+    moments_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(f, P, rho, ux, uy, T, half_step);
     return cudaGetLastError();
 }
 
-cudaError_t launch_halo_fp64(double* f, const StepParams& P, cudaStream_t s) {
+cudaError_t launch_halo_fp64(double* f, const StepParams& P, int* flag, cudaStream_t s) {
     const int n = HALO * P.Lx;
-    halo_fp64_kernel<<<(n + 127) / 128, 128, 0, s>>>(f, P);
+    halo_fp64_kernel<<<(n + 127) / 128, 128, 0, s>>>(f, P, flag);
     return cudaGetLastError();
 }
 

@@ -39,7 +39,8 @@ class NonFiniteError(LBError):
 class lb_params(C.Structure):
     _fields_ = [("Lx", C.c_int), ("Ly", C.c_int), ("tau", C.c_double), ("gx", C.c_double),
                 ("gy", C.c_double), ("T_top", C.c_double), ("T_bottom", C.c_double),
-                ("y_periodic", C.c_int), ("precision", C.c_int), ("stream", C.c_void_p),
+                ("y_periodic", C.c_int), ("precision", C.c_int), ("wall_mode", C.c_int),
+                ("stream", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t)]
 
 
@@ -73,6 +74,7 @@ def lib() -> C.CDLL:
         L.lb_set_staging.argtypes = [vp, C.c_int]
         L.lb_sync.argtypes = [vp]
         L.lb_moments.argtypes = [vp, vp, vp, vp, vp]
+        L.lb_moments_half_step.argtypes = [vp, vp, vp, vp, vp]
         L.lb_moments_device.argtypes = [vp, vp, vp, vp, vp]
         L.lb_get_populations.argtypes = [vp, vp]
         L.lb_set_populations.argtypes = [vp, vp]
@@ -155,11 +157,23 @@ def _precision_code(p) -> int:
     raise ValueError(f"unknown precision {p!r}")
 
 
+WALL_MODES = {"rest": 0, "mirror": 1}
+
+
+def _wall_code(m) -> int:
+    if isinstance(m, int):
+        return m  # validated by the library
+    if m in WALL_MODES:
+        return WALL_MODES[m]
+    raise ValueError(f"unknown wall mode {m!r}")
+
+
 def make_params(Lx, Ly, tau, gx=0.0, gy=0.0, T_top=1.0, T_bottom=1.0, y_periodic=False,
-                precision=LB_FP64, stream=None, workspace=0, workspace_bytes=0) -> lb_params:
+                precision=LB_FP64, stream=None, workspace=0, workspace_bytes=0,
+                wall_mode="rest") -> lb_params:
     return lb_params(int(Lx), int(Ly), float(tau), float(gx), float(gy), float(T_top),
                      float(T_bottom), int(bool(y_periodic)), _precision_code(precision),
-                     stream, workspace, workspace_bytes)
+                     _wall_code(wall_mode), stream, workspace, workspace_bytes)
 
 
 def workspace_bytes(Lx, Ly, precision=LB_FP64) -> int:
@@ -211,6 +225,7 @@ class Lattice:
     precision: object = LB_FP64
     stream: object = None
     own_memory: bool = False
+    wall_mode: object = "rest"
 
     def __post_init__(self):
         import torch
@@ -230,7 +245,7 @@ class Lattice:
             ws_ptr = self._ws.data_ptr()
         self._params = make_params(self.Lx, self.Ly, self.tau, self.gx, self.gy, self.T_top,
                                    self.T_bottom, self.y_periodic, prec, sh, ws_ptr,
-                                   nbytes if ws_ptr else 0)
+                                   nbytes if ws_ptr else 0, wall_mode=self.wall_mode)
         check(lib().lb_init(C.byref(self._params), *[_ptr(f) for f in fields], C.byref(self._ctx)),
               "lb_init")
         self.rho = self.ux = self.uy = self.T = None  # the context holds its own copy
@@ -271,6 +286,15 @@ class Lattice:
             out = tuple(np.empty((self.Ly, self.Lx), np.float64) for _ in range(4))
         check(lib().lb_moments(self._ctx, *[_ptr(o) if o is not None else None for o in out]),
               "lb_moments")
+        return out
+
+    def moments_half_step(self, out=None):
+        """Half-step fields (rho, u - g/2, T + |g|^2/8) of the current post-collision state as host
+        float64 arrays [Ly][Lx] (lb_moments_half_step)."""
+        if out is None:
+            out = tuple(np.empty((self.Ly, self.Lx), np.float64) for _ in range(4))
+        check(lib().lb_moments_half_step(self._ctx, *[_ptr(o) if o is not None else None for o in out]),
+              "lb_moments_half_step")
         return out
 
     def moments_device(self, out):
@@ -423,7 +447,8 @@ class Ensemble:
         for k, m in enumerate(members):
             params[k] = make_params(m["Lx"], m["Ly"], m["tau"], m.get("gx", 0.0), m.get("gy", 0.0),
                                     m.get("T_top", 1.0), m.get("T_bottom", 1.0),
-                                    m.get("y_periodic", False), precision)
+                                    m.get("y_periodic", False), precision,
+                                    wall_mode=m.get("wall_mode", "rest"))
             for j, key in enumerate(("rho", "ux", "uy", "T")):
                 a = _host_f64(m[key], (int(m["Ly"]), int(m["Lx"])))
                 keep.append(a)

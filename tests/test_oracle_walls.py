@@ -120,3 +120,20 @@ def test_conduction_between_mirror_walls(orc):
             assert abs(yb + 0.5) < tol and abs(yt - (Ly - 0.5)) < tol
         else:
             assert yb < -0.75 and yt > Ly - 0.25
+
+
+def test_mirror_halo_falls_back_to_rest_where_not_reflectable(orc):
+    """Where the mirror row is hotter than twice the wall temperature the reflected temperature
+    would not be positive; that halo site holds the rest closure's value instead."""
+    Lx, Ly, Tt, Tb = 4, 8, 0.3, 1.0
+    one, z = np.ones((Ly, Lx)), np.zeros((Ly, Lx))
+    T = one.copy()
+    T[-1, 1] = 0.5  # reflectable at the top: 2 * 0.3 - 0.5 > 0
+    f = orc.equilibrium(one, z, z, T)
+    mirror = orc.with_walls(f, Tt, Tb, wall_mode="mirror")
+    rest = orc.with_walls(f, Tt, Tb, wall_mode="rest")
+    top = Ly + 3  # halo row above row Ly - 1
+    cols = [0, 2, 3]
+    assert np.array_equal(mirror[top][cols], rest[top][cols])
+    _, _, _, Th = orc.moments(mirror[top])
+    assert Th[1] == pytest.approx(2 * Tt - 0.5, rel=1e-14)
