@@ -42,7 +42,7 @@ struct MemberDesc {
 inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 
 template <bool kSplit>
-__global__ void __launch_bounds__(ENS_BLOCK)
+__global__ void __launch_bounds__(ENS_BLOCK, kSplit ? 5 : 1)  // split: 20 warps per SM, <= 102 registers
 ensemble_step_kernel(const StepParams Pc, const MemberDesc* __restrict__ members,
                      const int4* __restrict__ items, int nitems, int tx_log2, int tile_sites,
                      int parity, int* __restrict__ flag) {

@@ -99,8 +99,8 @@ __device__ __forceinline__ Macro macro_of(const DevSums& s, double r, double r2)
 // FP32 collide of pair I: deviations of the post-collision populations I and I + NPAIR.
 template <int I>
 __device__ __forceinline__ void collide_pair32(float* d, float urx, float ury, const float* A0m1,
-                                               const float* A2, const float* B1, const float* Wd,
-                                               float drho, float omc) {
+                                               const float* A2, const float* B1, const float* K,
+                                               const float* D, float omc) {
     constexpr int S = shellh(I);
     constexpr float cx = (float)cxh(I);
     constexpr float cy = (float)cyh(I);
@@ -115,26 +115,24 @@ __device__ __forceinline__ void collide_pair32(float* d, float urx, float ury, c
     const float em1 = fmaf(a2, fmaf(a2, 1.0f / 24.0f, A2[S]), A0m1[S]);
     const float o = a * fmaf(a2, 1.0f / 6.0f, B1[S]);
     const float pp = em1 + o, pm = em1 - o;
-    // w (rho P - 1) = w (drho (1 + p) + p)
-    const float qp = fmaf(drho, pp, drho + pp);
-    const float qm = fmaf(drho, pm, drho + pm);
-    d[I] = fmaf(omc, d[I], Wd[S] * qp);
-    d[I + NPAIR] = fmaf(omc, d[I + NPAIR], Wd[S] * qm);
+    // (w / tau) (rho P - 1) = (w rho / tau) p + (w / tau) drho = K p + D, P = 1 + p
+    d[I] = fmaf(omc, d[I], fmaf(K[S], pp, D[S]));
+    d[I + NPAIR] = fmaf(omc, d[I + NPAIR], fmaf(K[S], pm, D[S]));
 }
 
 template <int I>
 struct Collide32 {
     __device__ __forceinline__ static void run(float* d, float urx, float ury, const float* A0m1,
-                                               const float* A2, const float* B1, const float* Wd,
-                                               float drho, float omc) {
-        Collide32<I - 1>::run(d, urx, ury, A0m1, A2, B1, Wd, drho, omc);
-        collide_pair32<I>(d, urx, ury, A0m1, A2, B1, Wd, drho, omc);
+                                               const float* A2, const float* B1, const float* K,
+                                               const float* D, float omc) {
+        Collide32<I - 1>::run(d, urx, ury, A0m1, A2, B1, K, D, omc);
+        collide_pair32<I>(d, urx, ury, A0m1, A2, B1, K, D, omc);
     }
 };
 template <>
 struct Collide32<0> {
     __device__ __forceinline__ static void run(float*, float, float, const float*, const float*,
-                                               const float*, const float*, float, float) {}
+                                               const float*, const float*, const float*, float) {}
 };
 
 }  // namespace
@@ -211,20 +209,20 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
     const float a20 = fmaf(u2f, -0.25f, 0.5f);
     const float b10 = fmaf(u2f, -0.5f, 1.0f);
     const float thu2 = thf * u2f, th2 = thf * thf;
-    const float omega = P.omega_f;
-    float A0m1[NSHELL], A2[NSHELL], B1[NSHELL], Wd[NSHELL];
+    const float orho = P.omega_f * (float)m.rho, odrho = P.omega_f * (float)pre.s0;
+    float A0m1[NSHELL], A2[NSHELL], B1[NSHELL], K[NSHELL], D[NSHELL];
 #pragma unroll
     for (int s = 0; s < NSHELL; ++s) {
         A0m1[s] = fmaf(P.sh32[s].gamma, th2,
                        fmaf(P.sh32[s].beta, thu2, fmaf(P.sh32[s].alpha, thf, a00m1)));
         A2[s] = fmaf(P.sh32[s].delta, thf, a20);
         B1[s] = fmaf(P.sh32[s].eps, thf, b10);
-        Wd[s] = omega * P.sh32[s].w;
+        K[s] = orho * P.sh32[s].w;
+        D[s] = odrho * P.sh32[s].w;
     }
-    const float drho = (float)pre.s0;
     const float omc = P.omc_f;
-    d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
-    Collide32<NPAIR>::run(d, (float)(P.r * uxs), (float)(P.r * uys), A0m1, A2, B1, Wd, drho, omc);
+    d[0] = fmaf(omc, d[0], fmaf(K[0], A0m1[0], D[0]));
+    Collide32<NPAIR>::run(d, (float)(P.r * uxs), (float)(P.r * uys), A0m1, A2, B1, K, D, omc);
 
     // FP64 projection onto the exact post-collision moments (c units):
     //   sum d' = rho - 1,  sum d' c = sum d c + rho g / r,
@@ -254,7 +252,8 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
     }
 
     // wall halo rows from the post-collision fields (rho, u + g, T), stored as FP32 deviations
-    wall_rows32<kMirror>(dst, P, x, y, m.rho, m.ux + gx, m.uy + gy, m.T, flag);
+    if (!P.y_periodic && (y < HALO || y >= Ly - HALO))
+        wall_rows32<kMirror>(dst, P, x, y, m.rho, m.ux + gx, m.uy + gy, m.T, flag);
 }
 
 }  // namespace lbg
@@ -381,20 +380,22 @@ __device__ __forceinline__ void split_collide(float* d, const StepParams& C, con
     const float a20 = fmaf(u2, -0.25f, 0.5f);
     const float b10 = fmaf(u2, -0.5f, 1.0f);
     const float thu2 = th * u2, th2 = th * th;
-    const float omega = M.omega_f;
-    float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], Wd[NSHELL];
+    // K_k = (w_k / tau) rho and D_k = (w_k / tau) (rho - 1): the relaxed equilibrium deviation of
+    // population i in shell k is K_k p_i + D_k with f_eq = w rho (1 + p)
+    const float orho = M.omega_f * s.rho, odrho = M.omega_f * s.s0;
+    float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], K[NSHELL], D[NSHELL];
 #pragma unroll
     for (int k = 0; k < NSHELL; ++k) {
         A0m1[k] = fmaf(P.sh32[k].gamma, th2,
                        fmaf(P.sh32[k].beta, thu2, fmaf(P.sh32[k].alpha, th, a00m1)));
         A2[k] = fmaf(P.sh32[k].delta, th, a20);
         B1c[k] = fmaf(P.sh32[k].eps, th, b10);
-        Wd[k] = omega * P.sh32[k].w;
+        K[k] = orho * P.sh32[k].w;
+        D[k] = odrho * P.sh32[k].w;
     }
-    const float drho = s.s0;
     const float omc = M.omc_f;
-    d[0] = fmaf(omc, d[0], Wd[0] * fmaf(drho, A0m1[0], drho + A0m1[0]));
-    Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, Wd, drho, omc);
+    d[0] = fmaf(omc, d[0], fmaf(K[0], A0m1[0], D[0]));
+    Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, K, D, omc);
 }
 
 // Project candidate post-collision deviations d (in place) onto the exact post-collision moments:
@@ -442,8 +443,9 @@ __device__ __forceinline__ void split_store(float* __restrict__ dst, const StepP
     char* const base = reinterpret_cast<char*>(dst + dsto);
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) __stcs(reinterpret_cast<float*>(base + P.plane_b32[i]), d[i]);
-    wall_rows32<kMirror>(dst, P, x, y, 1.0 + (double)s.s0, (double)s.ux + P.gx, (double)s.uy + P.gy,
-                         (double)s.T, flag);
+    if (!P.y_periodic && (y < HALO || y >= P.Ly - HALO))  // FP64 work on the six wall rows only
+        wall_rows32<kMirror>(dst, P, x, y, 1.0 + (double)s.s0, (double)s.ux + P.gx, (double)s.uy + P.gy,
+                             (double)s.T, flag);
 }
 
 // One fused FP32-deviation step of site (x, y) with exact-split FP32 moment accumulation and an
