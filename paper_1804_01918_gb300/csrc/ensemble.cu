@@ -50,17 +50,21 @@ ensemble_step_kernel(const StepParams Pc, const MemberDesc* __restrict__ members
     __shared__ const float* s_src;
     __shared__ float* s_dst;
     constexpr int NWORDS = (int)(sizeof(StepParams) / sizeof(unsigned long long));
+    int staged = -1;  // member whose parameters sit in sP (block-uniform)
     for (int t = blockIdx.x; t < nitems; t += gridDim.x) {
         const int4 it = items[t];
-        __syncthreads();  // the previous item is finished with sP
-        const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&members[it.x].P);
-        unsigned long long* s = reinterpret_cast<unsigned long long*>(&sP);
-        for (int k = threadIdx.x; k < NWORDS; k += ENS_BLOCK) s[k] = g[k];
-        if (threadIdx.x == 0) {
-            s_src = members[it.x].buf[parity];
-            s_dst = members[it.x].buf[parity ^ 1];
+        if (it.x != staged) {  // items run member by member: most items reuse the staged member
+            __syncthreads();   // the previous item is finished with sP
+            const unsigned long long* g = reinterpret_cast<const unsigned long long*>(&members[it.x].P);
+            unsigned long long* s = reinterpret_cast<unsigned long long*>(&sP);
+            for (int k = threadIdx.x; k < NWORDS; k += ENS_BLOCK) s[k] = g[k];
+            if (threadIdx.x == 0) {
+                s_src = members[it.x].buf[parity];
+                s_dst = members[it.x].buf[parity ^ 1];
+            }
+            __syncthreads();
+            staged = it.x;
         }
-        __syncthreads();
         const int xmask = (1 << tx_log2) - 1;
         for (int k = threadIdx.x; k < tile_sites; k += ENS_BLOCK) {
             const int x = it.y + (k & xmask);
