@@ -49,6 +49,14 @@ lb_status lb_mlp_eval(lb_mlp* net, const float* x, float* y, int n, void* stream
 lb_status lb_mlp_loss_grad(lb_mlp* net, const float* x, const float* t, int n, double* loss,
                            float* grad, void* stream);
 
+/* FP32 debug mode of lb_mlp_loss_grad: the same loss and gradient computed in plain FP32 on the
+ * CUDA cores (no BF16 rounding; GELU from the CUDA math library's erff), gradients summed over the
+ * samples in FP64. For checking against an FP64 reference (agreement ~1e-6 relative); slow, and
+ * allocates temporary device memory. Any n > 0. Synchronous. The paper has no counterpart (its
+ * method has no learned part). */
+lb_status lb_mlp_loss_grad_fp32(lb_mlp* net, const float* x, const float* t, int n, double* loss,
+                                float* grad, void* stream);
+
 /* Train on n (pre, post) pairs: sets the normalisation from the data, then `epochs` passes of
  * shuffled mini-batches (batch a multiple of 128) with Adam (beta 0.9 / 0.999, eps 1e-8, rate lr).
  * epoch_loss (host, may be NULL) receives each epoch's mean loss. Synchronous. */

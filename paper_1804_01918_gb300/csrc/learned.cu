@@ -609,6 +609,73 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
     fwd_teardown(f);
 }
 
+// ---- FP32 debug mode of the loss and gradient ------------------------------------------------
+// The same network, loss and gradient as the tensor-core training kernel, in plain FP32 on the CUDA
+// cores without BF16 rounding: GELU from the library erff/expf, one block of HID threads per sample
+// (thread j owns hidden unit j; output unit j < NOUT), activations in shared memory, gradients
+// accumulated over the samples in FP64 (atomics) so that only the per-sample FP32 arithmetic
+// rounds. Slow by design: a tight check of the host logic (packing, normalisation, loss scaling)
+// and of the backward formulas against an FP64 reference.
+__device__ __forceinline__ float gelu_ref(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad_ref(float z) {
+    return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+}
+
+__global__ void __launch_bounds__(HID)
+mlp_loss_grad_fp32_kernel(const float* __restrict__ p, const float* __restrict__ x, const float* __restrict__ t,
+                          int n, double* __restrict__ g, double* __restrict__ loss) {
+    __shared__ float xs[NIN], h1[HID], h2[HID], dy[NOUT], dz2[HID];
+    const float* W1 = p + OFF_W1;
+    const float* b1 = p + OFF_B1;
+    const float* W2 = p + OFF_W2;
+    const float* b2 = p + OFF_B2;
+    const float* W3 = p + OFF_W3;
+    const float* b3 = p + OFF_B3;
+    const int j = threadIdx.x;
+    const double scale = 2.0 / ((double)n * NOUT);
+    for (int smp = blockIdx.x; smp < n; smp += gridDim.x) {
+        if (j < NIN) xs[j] = x[(size_t)smp * NIN + j];
+        __syncthreads();
+        float z1 = b1[j];
+        for (int k = 0; k < NIN; ++k) z1 = fmaf(W1[j * NIN + k], xs[k], z1);
+        h1[j] = gelu_ref(z1);
+        __syncthreads();
+        float z2 = b2[j];
+        for (int k = 0; k < HID; ++k) z2 = fmaf(W2[j * HID + k], h1[k], z2);
+        h2[j] = gelu_ref(z2);
+        __syncthreads();
+        if (j < NOUT) {
+            float y = b3[j];
+            for (int k = 0; k < HID; ++k) y = fmaf(W3[j * HID + k], h2[k], y);
+            const float e = y - t[(size_t)smp * NOUT + j];
+            atomicAdd(loss, (double)e * (double)e);
+            dy[j] = (float)(scale * e);
+        }
+        __syncthreads();
+        // output layer: dW3[i][k] = dy_i h2_k (thread j owns column k = j), db3
+        for (int i = 0; i < NOUT; ++i) atomicAdd(&g[OFF_W3 + i * HID + j], (double)dy[i] * h2[j]);
+        if (j < NOUT) atomicAdd(&g[OFF_B3 + j], (double)dy[j]);
+        float dh2 = 0.0f;
+        for (int i = 0; i < NOUT; ++i) dh2 = fmaf(W3[i * HID + j], dy[i], dh2);
+        const float d2 = dh2 * gelu_grad_ref(z2);
+        dz2[j] = d2;
+        __syncthreads();
+        for (int i = 0; i < HID; ++i) atomicAdd(&g[OFF_W2 + i * HID + j], (double)dz2[i] * h1[j]);
+        atomicAdd(&g[OFF_B2 + j], (double)d2);
+        float dh1 = 0.0f;
+        for (int i = 0; i < HID; ++i) dh1 = fmaf(W2[i * HID + j], dz2[i], dh1);
+        const float d1 = dh1 * gelu_grad_ref(z1);
+        for (int k = 0; k < NIN; ++k) atomicAdd(&g[OFF_W1 + j * NIN + k], (double)d1 * xs[k]);
+        atomicAdd(&g[OFF_B1 + j], (double)d1);
+        __syncthreads();  // xs, h1, h2, dy, dz2 are reused by the next sample
+    }
+}
+
+__global__ void doubles_to_floats(const double* __restrict__ a, float* __restrict__ b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
 }  // namespace learn
 }  // namespace lbg
 
@@ -895,6 +962,35 @@ lb_status lb_mlp_loss_grad(lb_mlp* net, const float* x, const float* t, int n, d
     L_CUDA(cudaMemcpy(&l, sc.loss, sizeof(double), cudaMemcpyDeviceToHost));
     if (loss) *loss = l / ((double)n * NOUT);
     if (grad) L_CUDA(cudaMemcpy(grad, sc.grad, NPARAM * sizeof(float), cudaMemcpyDeviceToHost));
+    return LB_OK;
+}
+
+lb_status lb_mlp_loss_grad_fp32(lb_mlp* net, const float* x, const float* t, int n, double* loss, float* grad,
+                                void* stream) {
+    if (!net || !x || !t || n <= 0) return LB_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    double* acc = nullptr;  // NPARAM gradient sums + 1 loss sum (FP64)
+    L_CUDA(cudaMalloc((void**)&acc, (NPARAM + 1) * sizeof(double)));
+    float* gf = nullptr;
+    cudaError_t e = cudaMalloc((void**)&gf, NPARAM * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemsetAsync(acc, 0, (NPARAM + 1) * sizeof(double), s);
+    if (e == cudaSuccess) {
+        mlp_loss_grad_fp32_kernel<<<std::min(n, 8 * sm_count()), HID, 0, s>>>(net->params, x, t, n, acc,
+                                                                              acc + NPARAM);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        doubles_to_floats<<<(NPARAM + 255) / 256, 256, 0, s>>>(acc, gf, NPARAM);
+        e = cudaGetLastError();
+    }
+    double l = 0.0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&l, acc + NPARAM, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && grad) e = cudaMemcpyAsync(grad, gf, NPARAM * sizeof(float), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(gf);
+    cudaFree(acc);
+    if (e != cudaSuccess) return fail_l(e, "lb_mlp_loss_grad_fp32");
+    if (loss) *loss = l / ((double)n * NOUT);
     return LB_OK;
 }
 

@@ -106,6 +106,7 @@ def lib() -> C.CDLL:
         L.lb_mlp_set_params.argtypes = [vp, vp, vp]
         L.lb_mlp_eval.argtypes = [vp, vp, vp, C.c_int, vp]
         L.lb_mlp_loss_grad.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_double), vp, vp]
+        L.lb_mlp_loss_grad_fp32.argtypes = [vp, vp, vp, C.c_int, C.POINTER(C.c_double), vp, vp]
         L.lb_mlp_train.argtypes = [vp, vp, vp, C.c_longlong, C.c_int, C.c_int, C.c_float, C.c_uint64,
                                    vp, vp]
         L.lb_collect_pairs.argtypes = [vp, vp, C.c_int, vp, vp]
@@ -389,6 +390,15 @@ class MLP:
         g = np.empty(MLP_NPARAM, np.float32)
         check(lib().lb_mlp_loss_grad(self._ptr, x.data_ptr(), t.data_ptr(), int(x.shape[0]), C.byref(loss),
                                      g.ctypes.data, sh), "lb_mlp_loss_grad")
+        return loss.value, g
+
+    def loss_grad_fp32(self, x, t, stream=None):
+        """The same in the library's FP32 debug mode (CUDA cores, no BF16 rounding)."""
+        sh = None if stream is None else stream.cuda_stream
+        loss = C.c_double()
+        g = np.empty(MLP_NPARAM, np.float32)
+        check(lib().lb_mlp_loss_grad_fp32(self._ptr, x.data_ptr(), t.data_ptr(), int(x.shape[0]),
+                                          C.byref(loss), g.ctypes.data, sh), "lb_mlp_loss_grad_fp32")
         return loss.value, g
 
     def train(self, pre, post, epochs: int = 20, batch: int = 4096, lr: float = 1e-3, seed: int = 0,

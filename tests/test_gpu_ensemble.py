@@ -106,3 +106,28 @@ def test_ensemble_moments_and_seed_drawn_members(L, orc):
         assert np.linalg.norm(rho - orho) / np.linalg.norm(orho) < 40 * 37 * 2.0**-24 * 0.35
         assert np.linalg.norm(T - oT) / np.linalg.norm(oT) < 40 * 37 * 2.0**-24 * 0.35
     ens.close()
+
+
+def test_bench_ensemble_64_members_equal_single_lattice_runs(L):
+    """The bench's ensemble (64 seed-drawn members, 96 M sites, FP32 split, autotuned tile,
+    100-step graphs) in its launch configuration: sampled members -- the smallest, the largest
+    and two others -- equal, bit for bit, the same lattices advanced alone."""
+    descs = inputs.ensemble_members(64, seed=0)
+    specs = []
+    for d in descs:
+        st = inputs.rayleigh_taylor(d["Lx"], d["Ly"], R=d["R"], seed=d["seed"])
+        specs.append({"Lx": d["Lx"], "Ly": d["Ly"], "tau": d["tau"], "gy": st.gy,
+                      "T_top": st.T_top, "T_bottom": st.T_bottom, "rho": st.rho, "ux": st.ux,
+                      "uy": st.uy, "T": st.T})
+    sizes = [d["Lx"] * d["Ly"] for d in descs]
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 42})
+    ens = L.Ensemble(specs, precision="fp32split", graph_steps=100)
+    ens.autotune(steps=3)
+    ens.step(103)                     # one 100-step graph replay + 3 single launches
+    ens.sync()
+    assert ens.info()["sites"] == sum(sizes)
+    got = {k: ens.get_populations(k) for k in pick}
+    ens.close()
+    want = single_runs(L, [specs[k] for k in pick], 103, "fp32split")
+    for k, w in zip(pick, want):
+        assert np.array_equal(got[k], w), k

@@ -163,3 +163,46 @@ def test_tma_staging_unavailable_for_unaligned_rows(L):
     with pytest.raises(L.LBError):
         lat.set_staging(True)      # Lx = 30: rows are not 16-byte multiples
     lat.set_staging(False)
+
+
+def _window_oracle(orc, st, x0, y0, n, half, tau):
+    """FP64 oracle populations at (x0, y0) after n steps on a window around it (wrong values enter
+    a window's cut edges at <= 3 sites per step, so the centre of a half-width >= 3 (n + 1) window
+    is exact). Windows wrap in x and stop at real walls."""
+    Ly, Lx = st.rho.shape
+    xs = np.arange(x0 - half, x0 + half + 1) % Lx
+    ylo, yhi = max(0, y0 - half), min(Ly, y0 + half + 1)
+    sub = [a[ylo:yhi][:, xs] for a in (st.rho, st.ux, st.uy, st.T)]
+    out = orc.run(orc.equilibrium(*sub), tau=tau, nsteps=n, gy=st.gy, T_top=st.T_top,
+                  T_bottom=st.T_bottom, nthreads=1)
+    return out[y0 - ylo, half]
+
+
+def test_fp32split_full_size_2304x8192_sampled_sites_match_oracle(L, orc):
+    """The FP32 split form at the bench size (2304 x 8192) in its launch configuration; sampled
+    sites, including the x wrap and both walls, against the FP64 oracle on windows around them.
+    Bound: n steps x 37 populations x 2^-24 x 0.35 relative to each population's weight."""
+    Lx, Ly, n, tau = 2304, 8192, 4, 0.9
+    st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=tau, precision="fp32split")
+    lat.step(n)
+    lat.sync()
+    f = lat.get_populations()
+    lat.close()
+    cx, cy, w, _ = L.velocity_set()
+    perm = orc.order_map(cx, cy)
+    wo = np.empty(37)
+    wo[perm] = w
+    half = 3 * (n + 1)
+    rng = np.random.default_rng(1)
+    samples = [(0, 0), (Lx - 1, Ly - 1), (2, 1), (Lx - 3, Ly - 2), (1151, 4095), (7, Ly // 2)]
+    samples += [(int(rng.integers(Lx)), int(rng.integers(Ly))) for _ in range(10)]
+    bound = n * 37 * 2.0**-24 * 0.35
+    worst = 0.0
+    for (x0, y0) in samples:
+        want = _window_oracle(orc, st, x0, y0, n, half, tau)
+        got = np.empty(37)
+        got[perm] = f[:, y0, x0]
+        worst = max(worst, float(np.max(np.abs(got - want) / wo)))
+    print(f"fp32split 2304x8192 sampled sites, {n} steps: max |f - f_oracle| / w = {worst:.2e}")
+    assert worst < bound

@@ -66,6 +66,31 @@ def test_gradients_match_oracle(L):
     net.close()
 
 
+@pytest.mark.parametrize("n", [256, 77])
+def test_fp32_debug_gradients_match_fp64_oracle(L, n):
+    """The FP32 debug mode (no BF16 rounding) against the FP64 oracle MLP without rounding: loss
+    and every parameter block within 1e-6 relative -- a tight check of packing, loss scaling and
+    the backward formulas that the BF16 tensor-core path can only be held to 1e-2."""
+    rng = np.random.default_rng(7)
+    p = omlp.init_params(9, scale=2.0).astype(np.float32)
+    net = L.MLP(seed=0)
+    net.set_params(p)
+    x = rng.standard_normal((n, 37)).astype(np.float32)
+    t = (0.5 * rng.standard_normal((n, 37))).astype(np.float32)
+    loss, g = net.loss_grad_fp32(dev(x), dev(t))
+    lref, gref = omlp.loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), bf16=False)
+    assert loss == pytest.approx(lref, rel=1e-6)
+    for name, a, b in BLOCKS:
+        rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
+        assert rel < 1e-6, (name, rel)
+    # and the tensor-core path agrees with the debug mode to its own (BF16) tolerance
+    if n % 128 == 0:
+        loss_tc, g_tc = net.loss_grad(dev(x), dev(t))
+        for name, a, b in BLOCKS:
+            assert np.linalg.norm(g_tc[a:b] - g[a:b]) / np.linalg.norm(g[a:b]) < 2e-2, name
+    net.close()
+
+
 def collect_pairs(L, Lx=64, Ly=256, steps=24, every=3, seed=0, tau=0.9, R=2.0):
     """Pairs (pre, post) of all sites of a Rayleigh-Taylor lattice every `every` steps."""
     import torch
