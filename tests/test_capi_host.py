@@ -74,5 +74,11 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
     assert lib.lb_init(C.byref(p), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
                        C.byref(ctx)) == 1
     assert lib.lb_step(None, 1) == 1
+    for field, value in (("wall_mode", 5), ("gx", float("nan")), ("T_top", 0.0), ("T_bottom", -1.0),
+                         ("tau", float("inf"))):
+        p = L.make_params(64, 64, 0.9)
+        setattr(p, field, value)
+        assert lib.lb_init(C.byref(p), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
+                           C.byref(ctx)) == 1, field
     lib.lb_free(None)
     assert lib.lb_status_str(4) == b"non-finite or non-positive density/temperature"

@@ -215,3 +215,27 @@ def test_two_kernel_step_equals_fused_step(L, y_periodic):
         a.collide()
     b.step(7)
     assert np.array_equal(a.get_populations(), b.get_populations())
+
+
+@pytest.mark.parametrize("case", range(10))
+def test_randomized_configurations_match_oracle(L, orc, case):
+    """Seeded random configurations -- size (ragged, down to the 4 x 4 minimum), relaxation time,
+    gravity on both axes, wall temperatures, wall closure, periodic or walled y -- each run 30 FP64
+    steps from a random state and compared with the oracle at the 1e-12 bar."""
+    rng = np.random.default_rng(1000 + case)
+    Lx, Ly = (4, 4) if case == 0 else (int(rng.integers(4, 72)), int(rng.integers(4, 64)))
+    tau = float(rng.uniform(0.65, 1.4))
+    gx, gy = (float(v) for v in rng.uniform(-1.5e-3, 1.5e-3, 2))
+    T_top, T_bottom = (float(v) for v in rng.uniform(0.85, 1.15, 2))
+    y_periodic = bool(rng.integers(2))
+    wall = "mirror" if rng.integers(2) else "rest"
+    st = inputs.random_state(Lx, Ly, seed=case, du=0.02, dT=0.1, drho=0.1)
+    lat = L.Lattice(Lx, Ly, tau, st.rho, st.ux, st.uy, st.T, gx=gx, gy=gy, T_top=T_top,
+                    T_bottom=T_bottom, y_periodic=y_periodic, wall_mode=wall)
+    lat.step(30)
+    lat.sync()
+    got = gpu_to_oracle(L, orc, lat.get_populations())
+    lat.close()
+    want = orc.run(orc.init_fields(st), tau=tau, nsteps=30, gx=gx, gy=gy, T_top=T_top,
+                   T_bottom=T_bottom, y_periodic=y_periodic, wall_mode=wall)
+    assert rel_err(got, want) <= TOL, (Lx, Ly, tau, gx, gy, y_periodic, wall)
