@@ -257,15 +257,16 @@ def metric_name(precision="fp64"):
 
 # ----------------------------------------------------------------------------------------------
 
-def fp64_probe(lb, torch, stream):
-    """Achieved FP64 FMA rate of the library's probe (TFLOP/s) and the time it took."""
+def fp64_probe(lb, torch, stream, kind="fp64"):
+    """Achieved FP64 FMA rate of the library's probe (TFLOP/s, FMA = 2 flops). kind "fp64": chains
+    that settle on a fixed point; "fp64_varying": operands that keep changing."""
     blocks, threads, iters = SM_COUNT * 8, 256, 2048
     out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
-        lb.probe_fma("fp64", blocks, threads, iters, out, stream)   # warm-up
+        lb.probe_fma(kind, blocks, threads, iters, out, stream)   # warm-up
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        lb.probe_fma("fp64", blocks, threads, iters, out, stream)
+        lb.probe_fma(kind, blocks, threads, iters, out, stream)
         e1.record(stream)
     e1.synchronize()
     ms = e0.elapsed_time(e1)
@@ -325,6 +326,7 @@ def main():
     lat.step(args.warmup)
     lat.sync()
     probe_tf = fp64_probe(lb, torch, stream)
+    probe_var_tf = fp64_probe(lb, torch, stream, "fp64_varying")
 
     sampler = ClockSampler(visible_gpu_index(local))
     if dist:
@@ -389,6 +391,11 @@ def main():
                     "achieved_tflops": round(FP64_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
                     "peak_tflops": round(2 * peak, 4),
                     "probe_fp64_tflops": round(probe_tf, 4),
+                    "probe_fp64_varying_tflops": round(probe_var_tf, 4),
+                    "frac_of_varying_probe": round(inst_rate / (probe_var_tf / 2), 4),
+                    "probe_note": "FMA chains that settle on a fixed point reach nearly the nominal "
+                                  "rate; with operands that keep changing GB300's FP64 pipe sustains "
+                                  "less (varying probe), the rate real data sees",
                     "traffic_note": "ncu dram bytes of a 1152x2048 launch scaled to 2304x8192 by sites",
                     "hbm_achieved_gbs": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9, 1),
                     "hbm_frac": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9 / hbm, 4)}

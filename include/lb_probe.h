@@ -18,7 +18,10 @@ extern "C" {
 
 /* Launch blocks x threads threads; each runs 8 independent FMA chains of `iters` steps in FP64
  * (kind 0) or FP32 (kind 1), i.e. 16 * iters flops per thread, and writes one value per thread
- * to out (device memory of blocks*threads elements of that type, caller-owned). Asynchronous on
+ * to out (device memory of blocks*threads elements of that type, caller-owned). The chains of
+ * kinds 0 and 1 converge to a fixed point, after which their operands stop changing; kind 2 is
+ * FP64 with an addend that alternates every step, so the operands keep changing as in a real
+ * kernel (GB300's FP64 pipe sustains a lower rate on such data). Asynchronous on
  * `stream` (cudaStream_t, NULL = legacy default stream). LB_ERR_ARG for non-positive sizes,
  * threads > 1024 or an unknown kind. */
 lb_status lb_probe_fma(int kind, void* stream, int blocks, int threads, int iters, void* out);

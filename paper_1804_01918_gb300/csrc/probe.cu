@@ -19,6 +19,22 @@ __global__ void fma_chains_kernel(T* __restrict__ out, int iters, T m, T a) {
     out[t] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
 }
 
+// The same chains with operands that keep changing: each chain alternates its addend between two
+// values, so no chain settles on a fixed point (the FP64 pipe of GB300 runs measurably faster on
+// operands that stop changing, so this is the rate a real kernel's varying data sees).
+template <typename T>
+__global__ void fma_chains_varying_kernel(T* __restrict__ out, int iters, T m, T a, T b) {
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    T x0 = (T)(t & 7), x1 = x0 + (T)1, x2 = x0 + (T)2, x3 = x0 + (T)3;
+    T x4 = x0 + (T)4, x5 = x0 + (T)5, x6 = x0 + (T)6, x7 = x0 + (T)7;
+    for (int k = 0; k < iters; ++k) {
+        const T c = (k & 1) ? a : b;
+        x0 = x0 * m + c; x1 = x1 * m + c; x2 = x2 * m + c; x3 = x3 * m + c;
+        x4 = x4 * m + c; x5 = x5 * m + c; x6 = x6 * m + c; x7 = x7 * m + c;
+    }
+    out[t] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
+}
+
 }  // namespace
 
 extern "C" lb_status lb_probe_fma(int kind, void* stream, int blocks, int threads, int iters,
@@ -29,6 +45,8 @@ extern "C" lb_status lb_probe_fma(int kind, void* stream, int blocks, int thread
         fma_chains_kernel<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.9999999, 1e-7);
     else if (kind == 1)
         fma_chains_kernel<float><<<blocks, threads, 0, s>>>((float*)out, iters, 0.9999f, 1e-4f);
+    else if (kind == 2)
+        fma_chains_varying_kernel<double><<<blocks, threads, 0, s>>>((double*)out, iters, 0.9999999, 1e-7, 3e-7);
     else
         return LB_ERR_ARG;
     return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;

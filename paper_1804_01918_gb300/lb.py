@@ -424,8 +424,9 @@ class MLP:
 
 
 def probe_fma(kind: str, blocks: int, threads: int, iters: int, out, stream=None) -> None:
-    """Launch the FMA-throughput probe (kind 'fp64' or 'fp32') into the torch tensor `out`."""
-    k = {"fp64": 0, "fp32": 1}[kind]
+    """Launch the FMA-throughput probe (kind 'fp64', 'fp32', or 'fp64_varying': FP64 chains whose
+    operands keep changing) into the torch tensor `out`."""
+    k = {"fp64": 0, "fp32": 1, "fp64_varying": 2}[kind]
     sh = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
     check(lib().lb_probe_fma(k, sh, blocks, threads, iters, out.data_ptr()), "lb_probe_fma")
 
