@@ -292,6 +292,8 @@ def main():
     ap.add_argument("--lattice", default=None,
                     help="LXxLY of a smaller case for profiling (default: the 2304x8192 workload)")
     ap.add_argument("--precision", choices=["fp64", "fp32dev", "fp32split"], default="fp64")
+    ap.add_argument("--staging", choices=["plain", "tma"], default="plain",
+                    help="fp32split: read the pulled rows with plain loads or TMA-staged tiles")
     args = ap.parse_args()
     if args.lattice:
         global LX, LY
@@ -323,6 +325,8 @@ def main():
     st = inputs.rayleigh_taylor(LX, LY, R=RATIO, seed=replicas.replica_seed(rank))
     stream = torch.cuda.Stream()
     lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision=args.precision)
+    if args.precision == "fp32split" and args.staging == "tma":
+        lat.set_staging(True)
     lat.step(args.warmup)
     lat.sync()
     probe_tf = fp64_probe(lb, torch, stream)
@@ -401,7 +405,8 @@ def main():
                     "hbm_frac": round(FP64_BYTES_PER_SITE * sites / kernel_s / 1e9 / hbm, 4)}
     else:
         gbs = FP32DEV_BYTES_PER_SITE * sites / kernel_s / 1e9
-        roofline = {"bound": "hbm", "kernel": f"step_{args.precision}_kernel", "achieved": round(gbs, 1),
+        kname = "step_fp32split_tma_kernel" if args.staging == "tma" else f"step_{args.precision}_kernel"
+        roofline = {"bound": "hbm", "kernel": kname, "achieved": round(gbs, 1),
                     "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": None,
                     "peak_note": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 

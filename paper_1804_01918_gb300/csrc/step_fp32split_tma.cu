@@ -5,10 +5,12 @@
 // sites. For each tile one thread issues, per population i, a TMA copy (cp.async.bulk.tensor) of
 // the box of 40 columns x 4 rows that contains the tile shifted by -c_i: columns x0 - 4 .. x0 + 35
 // (x0 a multiple of 32, so the box start is 16-byte aligned for every shift |c_x| <= 3) and rows
-// y0 - c_iy .. y0 - c_iy + 3 of the halo-padded plane. Tiles are prefetched STAGES deep into a
-// shared-memory ring, so the next tiles' loads are in flight while the current tile computes.
-// Source columns that wrap around x (and, in the y-periodic test mode, rows that wrap around y)
-// are read directly from global memory instead: the TMA box holds fill values there.
+// y0 - c_iy .. y0 - c_iy + 3 of the halo-padded plane. Tiles are prefetched STAGES = 2 deep into
+// a shared-memory ring (47 KB per CTA, so four CTAs -- 16 warps -- share an SM), so the next
+// tile's loads are in flight while the current tile computes. Interior tiles read every
+// population from the staged box at a compile-time offset; tiles whose sources wrap around x (the
+// first and last tile columns; in the y-periodic test mode also the first and last tile rows)
+// read the wrapping populations directly from global memory: the TMA box holds fill values there.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -26,7 +28,7 @@ constexpr int TX = 32, TY = 4;
 constexpr int BOXW = TX + 8;                 // 40 columns, 160 bytes (a multiple of 16)
 constexpr int BOX_FLOATS = BOXW * TY;        // 160 floats = 640 bytes per population
 constexpr int STAGE_BYTES = NPOP * BOX_FLOATS * 4;
-constexpr int STAGES = 3;
+constexpr int STAGES = 2;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 64;
 constexpr uint32_t WAIT_LIMIT = 1u << 22;
 constexpr int ERR_TIMEOUT = 8;
@@ -85,6 +87,19 @@ struct GatherAll<-1> {
                                                const StepParams&) {}
 };
 
+// Population I of thread (tx, ty) of an interior tile: always inside the staged box.
+template <int I>
+struct GatherFast {
+    __device__ __forceinline__ static void run(const float* stage, float* d, int tx, int ty) {
+        GatherFast<I - 1>::run(stage, d, tx, ty);
+        d[I] = stage[I * BOX_FLOATS + ty * BOXW + tx + (4 - cx_of(I))];
+    }
+};
+template <>
+struct GatherFast<-1> {
+    __device__ __forceinline__ static void run(const float*, float*, int, int) {}
+};
+
 __global__ void __launch_bounds__(128)
 step_fp32split_tma_kernel(const __grid_constant__ CUtensorMap tsrc, const float* __restrict__ src,
                           float* __restrict__ dst, const StepParams P, int* __restrict__ flag) {
@@ -119,9 +134,17 @@ step_fp32split_tma_kernel(const __grid_constant__ CUtensorMap tsrc, const float*
         const int ty = tid >> 5;
         const int x = x0 + (tid & 31), y = y0 + ty;
         const bool active = x < P.Lx && y < P.Ly;
+        // tile-uniform: does any source of this tile wrap around x (or, y-periodic, around y)?
+        const bool edge = x0 < HALO || x0 + TX + HALO > P.Lx ||
+                          (P.y_periodic && (y0 < HALO || y0 + TY + HALO > P.Ly));
         float d[NPOP];
-        if (active) GatherAll<NPOP - 1>::run(reinterpret_cast<const float*>(sm + s * STAGE_BYTES), src, d, x, y,
-                                             x0, ty, P);
+        const float* stage = reinterpret_cast<const float*>(sm + s * STAGE_BYTES);
+        if (active) {
+            if (edge)
+                GatherAll<NPOP - 1>::run(stage, src, d, x, y, x0, ty, P);
+            else
+                GatherFast<NPOP - 1>::run(stage, d, tid & 31, ty);
+        }
         __syncthreads();  // every thread has read stage s: refill it with a later tile
         if (tid == 0) {
             const int tn = t + STAGES * gridDim.x;
