@@ -16,6 +16,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -778,13 +779,17 @@ int sm_count() {
     return std::max(1, n);
 }
 
+// The kernels' dynamic shared-memory limits, raised once per device (the attribute is per device).
 lb_status set_smem_limits() {
-    static bool done = false;
-    if (done) return LB_OK;
+    constexpr int MAXDEV = 64;
+    static std::atomic<bool> done[MAXDEV];
+    int dev = 0;
+    L_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < MAXDEV && done[dev].load()) return LB_OK;
     L_CUDA(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES));
     L_CUDA(cudaFuncSetAttribute(mlp_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
     L_CUDA(cudaFuncSetAttribute(step_learned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
-    done = true;
+    if (dev >= 0 && dev < MAXDEV) done[dev].store(true);
     return LB_OK;
 }
 

@@ -14,6 +14,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 
 #include "d2q37_gpu.cuh"
@@ -209,15 +210,19 @@ cudaError_t make_fp32_tensor_map(void* tmap_out, const float* base, const StepPa
 }
 
 int fp32split_tma_grid() {
-    static int grid = 0;
-    if (grid) return grid;
+    // co-resident CTAs of the current device (cached per device; the shared-memory attribute is
+    // per device too)
+    constexpr int MAXDEV = 64;
+    static std::atomic<int> cached[MAXDEV];
     int dev = 0, sms = 1, per = 1;
     cudaGetDevice(&dev);
+    if (dev >= 0 && dev < MAXDEV && cached[dev].load() > 0) return cached[dev].load();
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaFuncSetAttribute(tma32::step_fp32split_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          tma32::SMEM_BYTES);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, tma32::step_fp32split_tma_kernel, 128, tma32::SMEM_BYTES);
-    grid = (per > 0 ? per : 1) * sms;
+    const int grid = (per > 0 ? per : 1) * sms;
+    if (dev >= 0 && dev < MAXDEV) cached[dev].store(grid);
     return grid;
 }
 
