@@ -41,7 +41,9 @@ lb_status lb_ensemble_workspace_bytes(int n, const lb_params* members, const lb_
                                       size_t* bytes);
 
 /* Create an ensemble of n >= 1 members. members[k]: Lx, Ly, tau, gx, gy, T_top, T_bottom,
- * y_periodic of member k (its precision, stream and workspace fields are ignored). rho[k], ux[k],
+ * y_periodic of member k (its precision, stream and workspace fields are ignored; wall_mode must
+ * be LB_WALL_REST -- the ensemble kernel is built with the rest closure only -- else LB_ERR_ARG).
+ * rho[k], ux[k],
  * uy[k], T[k]: host fields [Ly][Lx] float64 of member k. Populations start at equilibrium with
  * wall halos written. Synchronous. */
 lb_status lb_ensemble_init(int n, const lb_params* members, const double* const* rho,
