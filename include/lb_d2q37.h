@@ -120,6 +120,23 @@ lb_status lb_workspace_bytes(const lb_params* p, size_t* bytes);
 lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const double* uy,
                   const double* T, lb_ctx** out);
 
+/* Seeded Rayleigh-Taylor initial fields (the paper's application, Sec. 3; the recipe is a reading,
+ * the paper prints none): walls top and bottom, periodic x; T_top = 2 / (1 + R),
+ * T_bottom = 2 R / (1 + R) with R = T_bottom / T_top > 0 the temperature ratio (for an Atwood
+ * number A use R = (1 + A) / (1 - A)); interface y_i(x) = Ly/2 + Ly sum_{k=1..8} a_k
+ * cos(2 pi k x / Lx + phi_k) with a_1..a_8 uniform draws scaled to sum 1e-3 and phi_1..phi_8
+ * uniform in [0, 2 pi), drawn in that order from SplitMix64 seeded with `seed` (u = (next >> 11)
+ * 2^-53); T = 1 + (T_bottom - T_top)/2 tanh((y_i - y)/2); u = 0; rho = exp(-g (y - y_i)/T)/T;
+ * gravity g = 0.1 T_top / Ly downward. Writes host arrays rho, ux, uy, T ([Ly][Lx] float64,
+ * caller-owned) and, if not NULL, *T_top, *T_bottom and *gy (= -g). Pure host call (no GPU);
+ * LB_ERR_ARG for non-positive sizes or R. */
+lb_status lb_rt_fields(int Lx, int Ly, double R, uint64_t seed, double* rho, double* ux, double* uy,
+                       double* T, double* T_top, double* T_bottom, double* gy);
+
+/* lb_init with the fields of lb_rt_fields(p->Lx, p->Ly, R, seed): p's T_top, T_bottom and gy are
+ * replaced by the recipe's; every other field of p is used as given. Synchronous. */
+lb_status lb_init_rt(const lb_params* p, double R, uint64_t seed, lb_ctx** out);
+
 /* Advance n >= 0 fused time steps: pull propagate (Fig. 3 listing) + collide (Sec. 3) + wall halo
  * write, one kernel per step, CUDA-graph launched. Asynchronous on the context's stream; a
  * non-finite state is reported by the next lb_sync / lb_moments / lb_get_populations. */

@@ -51,6 +51,11 @@ lb_status lb_ensemble_init(int n, const lb_params* members, const double* const*
                            const double* const* T, const lb_ensemble_opts* opts,
                            lb_ensemble** out);
 
+/* lb_ensemble_init with member k's fields from lb_rt_fields(members[k].Lx, members[k].Ly, R[k],
+ * seeds[k]) (its T_top, T_bottom and gy replaced by the recipe's). Synchronous. */
+lb_status lb_ensemble_init_rt(int n, const lb_params* members, const double* R, const uint64_t* seeds,
+                              const lb_ensemble_opts* opts, lb_ensemble** out);
+
 /* Advance every member by n steps: one persistent launch per step (graph-replayed). Async. */
 lb_status lb_ensemble_step(lb_ensemble* e, int n);
 

@@ -67,6 +67,24 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
  * (y * Lx + x, device array) pre = the pulled deviations, post = their plain collide. Async. */
 lb_status lb_collect_pairs(lb_ctx* c, const int* sites, int n, float* pre, float* post);
 
+/* Context-owned learned collide. lb_collide_train: the context creates (once) its own network
+ * (seeded with `seed`), trains it on npairs device pairs pre/post [npairs][37] float32 (as
+ * lb_mlp_train: `epochs` passes, batch min(4096, npairs rounded down to a multiple of 128), rate
+ * 1e-3, Adam) and switches the context to the learned collide with bound 1e-4 checked every
+ * step. Needs an LB_FP32SPLIT context with Lx, Ly multiples of 32 (else LB_ERR_STATE) and
+ * npairs >= 128. Synchronous.
+ * lb_collide_save: write the context's current learned collide (network parameters,
+ * normalisation, bound, check interval) to a file: 8-byte magic "LBMLP37", uint32 version 1,
+ * uint32 LB_MLP_NPARAM, uint32 148, int32 check_every, float64 bound, then the float32 parameters
+ * and normalisation, all little-endian. LB_ERR_STATE without a learned collide, LB_ERR_ARG if the
+ * file cannot be written.
+ * lb_collide_load: read such a file into the context's own network and switch the context to it
+ * with the stored bound and interval. LB_ERR_ARG for a missing, short or foreign file. */
+lb_status lb_collide_train(lb_ctx* c, const float* pre, const float* post, size_t npairs, int epochs,
+                           uint64_t seed);
+lb_status lb_collide_save(lb_ctx* c, const char* path);
+lb_status lb_collide_load(lb_ctx* c, const char* path);
+
 /* Switch the context's collide to the learned one (net must outlive the setting), or back. */
 lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int check_every);
 lb_status lb_set_collide_plain(lb_ctx* c);

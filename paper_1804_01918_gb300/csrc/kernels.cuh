@@ -59,6 +59,8 @@ struct LearnedState;
 lb_status learned_create(const struct lb_mlp* net, int Lx, int Ly, double bound, int check_every,
                          LearnedState** out);
 void learned_destroy(LearnedState* ls);
+// the network, bound and check interval a learned state was created with
+lb_status learned_info(const LearnedState* ls, const struct lb_mlp** net, double* bound, int* check_every);
 cudaError_t launch_step_learned(const float* src, float* dst, const StepParams& P, LearnedState* ls,
                                 int* flag, cudaStream_t s);
 cudaError_t launch_pairs(const float* src, const StepParams& P, const int* sites, int n, float* pre,

@@ -9,7 +9,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <new>
+#include <vector>
 
 #include "../../include/lb_d2q37.h"
 #include "../../include/lb_learned.h"
@@ -176,6 +178,7 @@ struct lb_ctx {
     bool graph_failed = false;
     long long steps = 0;
     LearnedState* learned = nullptr;  // learned collide, when set
+    lb_mlp* own_net = nullptr;        // network owned by the context (lb_collide_train/load)
     alignas(64) unsigned char tmap[2][128];  // TMA descriptors of the two FP32 population copies
     bool tma_ready = false;                  // tensor maps built (FP32SPLIT, Lx % 4 == 0)
     bool use_tma = false;                    // step with the TMA-staged kernel
@@ -316,6 +319,7 @@ void lb_free(lb_ctx* c) {
     for (int k = 0; k < 2; ++k)
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     learned_destroy(c->learned);
+    lb_mlp_free(c->own_net);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -560,6 +564,76 @@ lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int
     learned_destroy(c->learned);
     c->learned = ls;
     return LB_OK;
+}
+
+lb_status lb_collide_train(lb_ctx* c, const float* pre, const float* post, size_t npairs, int epochs,
+                           uint64_t seed) {
+    if (!c || !pre || !post || npairs < (size_t)LB_MLP_TILE || epochs < 1) return LB_ERR_ARG;
+    if (c->p.precision != LB_FP32SPLIT || c->p.Lx % 32 || c->p.Ly % 32) return LB_ERR_STATE;
+    if (npairs > (size_t)((1ll << 31) - 1)) return LB_ERR_ARG;
+    if (!c->own_net) {
+        lb_status st = lb_mlp_create(seed, &c->own_net);
+        if (st != LB_OK) return st;
+    }
+    const long long n = (long long)npairs;
+    const int batch = (int)std::min<long long>(4096, n / LB_MLP_TILE * LB_MLP_TILE);
+    lb_status st = lb_mlp_train(c->own_net, pre, post, n, epochs, batch, 1e-3f, seed, nullptr, c->stream);
+    if (st != LB_OK) return st;
+    return lb_set_collide_learned(c, c->own_net, 1e-4, 1);
+}
+
+namespace {
+constexpr char MLP_MAGIC[8] = {'L', 'B', 'M', 'L', 'P', '3', '7', '\0'};
+constexpr uint32_t MLP_FILE_VERSION = 1;
+constexpr uint32_t MLP_NNORM = 4 * 37;
+}  // namespace
+
+lb_status lb_collide_save(lb_ctx* c, const char* path) {
+    if (!c || !path) return LB_ERR_ARG;
+    const lb_mlp* net = nullptr;
+    double bound = 0.0;
+    int check_every = 1;
+    lb_status st = learned_info(c->learned, &net, &bound, &check_every);
+    if (st != LB_OK) return st;
+    std::vector<float> params(LB_MLP_NPARAM), norm(MLP_NNORM);
+    st = lb_mlp_get_params(net, params.data(), norm.data());
+    if (st != LB_OK) return st;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return LB_ERR_ARG;
+    const uint32_t head[3] = {MLP_FILE_VERSION, (uint32_t)LB_MLP_NPARAM, MLP_NNORM};
+    const int32_t ce = check_every;
+    bool ok = std::fwrite(MLP_MAGIC, 1, 8, fp) == 8 && std::fwrite(head, 4, 3, fp) == 3 &&
+              std::fwrite(&ce, 4, 1, fp) == 1 && std::fwrite(&bound, 8, 1, fp) == 1 &&
+              std::fwrite(params.data(), 4, params.size(), fp) == params.size() &&
+              std::fwrite(norm.data(), 4, norm.size(), fp) == norm.size();
+    ok = (std::fclose(fp) == 0) && ok;
+    return ok ? LB_OK : LB_ERR_ARG;
+}
+
+lb_status lb_collide_load(lb_ctx* c, const char* path) {
+    if (!c || !path) return LB_ERR_ARG;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return LB_ERR_ARG;
+    char magic[8];
+    uint32_t head[3];
+    int32_t ce = 0;
+    double bound = 0.0;
+    std::vector<float> params(LB_MLP_NPARAM), norm(MLP_NNORM);
+    bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, MLP_MAGIC, 8) == 0 &&
+              std::fread(head, 4, 3, fp) == 3 && head[0] == MLP_FILE_VERSION &&
+              head[1] == (uint32_t)LB_MLP_NPARAM && head[2] == MLP_NNORM && std::fread(&ce, 4, 1, fp) == 1 &&
+              std::fread(&bound, 8, 1, fp) == 1 &&
+              std::fread(params.data(), 4, params.size(), fp) == params.size() &&
+              std::fread(norm.data(), 4, norm.size(), fp) == norm.size();
+    std::fclose(fp);
+    if (!ok || ce < 1 || !(bound >= 0.0)) return LB_ERR_ARG;
+    if (!c->own_net) {
+        lb_status st = lb_mlp_create(0, &c->own_net);
+        if (st != LB_OK) return st;
+    }
+    lb_status st = lb_mlp_set_params(c->own_net, params.data(), norm.data());
+    if (st != LB_OK) return st;
+    return lb_set_collide_learned(c, c->own_net, bound, ce);
 }
 
 lb_status lb_set_collide_plain(lb_ctx* c) {

@@ -1116,6 +1116,14 @@ lb_status learned_create(const lb_mlp* net, int Lx, int Ly, double bound, int ch
     return LB_OK;
 }
 
+lb_status learned_info(const LearnedState* ls, const lb_mlp** net, double* bound, int* check_every) {
+    if (!ls) return LB_ERR_STATE;
+    if (net) *net = ls->net;
+    if (bound) *bound = ls->bound;
+    if (check_every) *check_every = ls->check_every;
+    return LB_OK;
+}
+
 void learned_destroy(LearnedState* ls) {
     if (!ls) return;
     cudaDeviceSynchronize();

@@ -130,3 +130,49 @@ def ensemble_members(n: int, seed: int = 0, lx_min: int = 128, lx_max: int = 102
         out.append({"Lx": Lx, "Ly": 4 * Lx, "atwood": A, "R": atwood_to_ratio(A), "tau": tau,
                     "seed": int(rng.integers(0, 2**31 - 1))})
     return out
+
+
+def _splitmix64(state: int) -> tuple[int, int]:
+    """One step of SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): (new state, output)."""
+    mask = (1 << 64) - 1
+    state = (state + 0x9E3779B97F4A7C15) & mask
+    z = state
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & mask
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & mask
+    return state, z ^ (z >> 31)
+
+
+def rayleigh_taylor_splitmix(Lx: int, Ly: int, R: float = 2.0, seed: int = 0) -> RTFields:
+    """The Rayleigh-Taylor recipe above with its eight amplitudes and eight phases drawn, in that
+    order, from SplitMix64 seeded with ``seed`` (u = (next >> 11) 2^-53) instead of PCG64: the
+    generator the C library's lb_rt_fields / lb_init_rt implement from the same published
+    definition. Arithmetic in the same order as there, so the two agree up to the last-place
+    rounding of cos, tanh and exp."""
+    if Lx < 1 or Ly < 1:
+        raise ValueError("lattice sizes must be positive")
+    T_top, T_bottom = wall_temperatures(R)
+    g = 0.1 * T_top / Ly
+    s = seed & ((1 << 64) - 1)
+    a, phi = [], []
+    total = 0.0
+    for _ in range(N_MODES):
+        s, z = _splitmix64(s)
+        a.append((z >> 11) * 2.0**-53)
+        total = total + a[-1]
+    scale = 1e-3 / total
+    a = [v * scale for v in a]
+    two_pi = 6.283185307179586476925286766559
+    for _ in range(N_MODES):
+        s, z = _splitmix64(s)
+        phi.append((z >> 11) * 2.0**-53 * two_pi)
+    x = np.arange(Lx, dtype=np.float64)
+    acc = np.zeros(Lx)
+    for k in range(N_MODES):
+        acc = acc + a[k] * np.cos(((two_pi * (k + 1)) * x) / Lx + phi[k])
+    yi = Ly / 2.0 + Ly * acc
+    y = np.arange(Ly, dtype=np.float64)[:, None]
+    T = 1.0 + (0.5 * (T_bottom - T_top)) * np.tanh((yi[None, :] - y) / 2.0)
+    rho = np.exp((-g * (y - yi[None, :])) / T) / T
+    zero = np.zeros((Ly, Lx), dtype=np.float64)
+    return RTFields(rho=np.ascontiguousarray(rho), ux=zero.copy(), uy=zero.copy(),
+                    T=np.ascontiguousarray(T), T_top=T_top, T_bottom=T_bottom, gy=-g)

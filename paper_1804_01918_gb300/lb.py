@@ -75,6 +75,13 @@ def lib() -> C.CDLL:
         L.lb_sync.argtypes = [vp]
         L.lb_moments.argtypes = [vp, vp, vp, vp, vp]
         L.lb_moments_half_step.argtypes = [vp, vp, vp, vp, vp]
+        L.lb_rt_fields.argtypes = [C.c_int, C.c_int, C.c_double, C.c_uint64, vp, vp, vp, vp, vp, vp, vp]
+        L.lb_init_rt.argtypes = [C.POINTER(lb_params), C.c_double, C.c_uint64, C.POINTER(vp)]
+        L.lb_ensemble_init_rt.argtypes = [C.c_int, C.POINTER(lb_params), vp, vp, C.POINTER(lb_ensemble_opts),
+                                          C.POINTER(vp)]
+        L.lb_collide_train.argtypes = [vp, vp, vp, C.c_size_t, C.c_int, C.c_uint64]
+        L.lb_collide_save.argtypes = [vp, C.c_char_p]
+        L.lb_collide_load.argtypes = [vp, C.c_char_p]
         L.lb_moments_device.argtypes = [vp, vp, vp, vp, vp]
         L.lb_get_populations.argtypes = [vp, vp]
         L.lb_set_populations.argtypes = [vp, vp]
@@ -201,6 +208,19 @@ def _host_f64(a, shape):
     return arr
 
 
+def rt_fields(Lx: int, Ly: int, R: float = 2.0, seed: int = 0):
+    """The library's seeded Rayleigh-Taylor fields (lb_rt_fields, host only) as an
+    inputs.RTFields."""
+    from .inputs import RTFields
+    out = [np.empty((Ly, Lx), np.float64) for _ in range(4)]
+    tt, tb, gy = C.c_double(), C.c_double(), C.c_double()
+    check(lib().lb_rt_fields(int(Lx), int(Ly), float(R), int(seed) & ((1 << 64) - 1),
+                             *[o.ctypes.data for o in out], C.byref(tt), C.byref(tb), C.byref(gy)),
+          "lb_rt_fields")
+    return RTFields(rho=out[0], ux=out[1], uy=out[2], T=out[3], T_top=tt.value, T_bottom=tb.value,
+                    gy=gy.value)
+
+
 @dataclass
 class Lattice:
     """One D2Q37 lattice on the GPU (wraps an lb_ctx).
@@ -227,12 +247,15 @@ class Lattice:
     stream: object = None
     own_memory: bool = False
     wall_mode: object = "rest"
+    rt_ratio: object = None  # set (with rt_seed) to initialise through lb_init_rt instead of fields
+    rt_seed: int = 0
 
     def __post_init__(self):
         import torch
         self._ctx = C.c_void_p()
         shape = (self.Ly, self.Lx)
-        fields = [_host_f64(v, shape) for v in (self.rho, self.ux, self.uy, self.T)]
+        fields = (None if self.rt_ratio is not None else
+                  [_host_f64(v, shape) for v in (self.rho, self.ux, self.uy, self.T)])
         prec = _precision_code(self.precision)
         if self.stream is None:
             # a stream of its own: the legacy default stream cannot be captured into a CUDA graph
@@ -247,8 +270,15 @@ class Lattice:
         self._params = make_params(self.Lx, self.Ly, self.tau, self.gx, self.gy, self.T_top,
                                    self.T_bottom, self.y_periodic, prec, sh, ws_ptr,
                                    nbytes if ws_ptr else 0, wall_mode=self.wall_mode)
-        check(lib().lb_init(C.byref(self._params), *[_ptr(f) for f in fields], C.byref(self._ctx)),
-              "lb_init")
+        if fields is None:
+            check(lib().lb_init_rt(C.byref(self._params), float(self.rt_ratio),
+                                   int(self.rt_seed) & ((1 << 64) - 1), C.byref(self._ctx)), "lb_init_rt")
+            R = float(self.rt_ratio)
+            self.T_top, self.T_bottom = 2.0 / (1.0 + R), 2.0 * R / (1.0 + R)
+            self.gy = -0.1 * self.T_top / self.Ly
+        else:
+            check(lib().lb_init(C.byref(self._params), *[_ptr(f) for f in fields], C.byref(self._ctx)),
+                  "lb_init")
         self.rho = self.ux = self.uy = self.T = None  # the context holds its own copy
 
     @classmethod
@@ -259,6 +289,22 @@ class Lattice:
         kw.setdefault("T_bottom", fields.T_bottom)
         Ly, Lx = fields.rho.shape
         return cls(Lx, Ly, tau, fields.rho, fields.ux, fields.uy, fields.T, **kw)
+
+    @classmethod
+    def rayleigh_taylor(cls, Lx, Ly, tau, R=2.0, seed=0, **kw):
+        """A lattice initialised by lb_init_rt (the library's seeded Rayleigh-Taylor fields)."""
+        return cls(Lx, Ly, tau, None, None, None, None, rt_ratio=R, rt_seed=seed, **kw)
+
+    def collide_train(self, pre, post, epochs: int = 20, seed: int = 0) -> None:
+        """lb_collide_train on device pairs pre/post (torch float32 [n, 37])."""
+        check(lib().lb_collide_train(self._ctx, pre.data_ptr(), post.data_ptr(), int(pre.shape[0]),
+                                     int(epochs), int(seed) & ((1 << 64) - 1)), "lb_collide_train")
+
+    def collide_save(self, path: str) -> None:
+        check(lib().lb_collide_save(self._ctx, os.fsencode(path)), "lb_collide_save")
+
+    def collide_load(self, path: str) -> None:
+        check(lib().lb_collide_load(self._ctx, os.fsencode(path)), "lb_collide_load")
 
     @property
     def sites(self) -> int:
@@ -445,7 +491,8 @@ def moments_noalloc(Lx: int, Ly: int, f_device_ptr: int, precision=LB_FP64, stre
 class Ensemble:
     """Independent D2Q37 lattices advanced together by one persistent launch per step
     (include/lb_ensemble.h). members: list of dicts with Lx, Ly, tau and optional gx, gy, T_top,
-    T_bottom, y_periodic, plus host fields rho, ux, uy, T ([Ly][Lx] float64)."""
+    T_bottom, y_periodic, plus host fields rho, ux, uy, T ([Ly][Lx] float64) -- or, for every
+    member, a temperature ratio R and a seed instead of fields (lb_ensemble_init_rt)."""
 
     def __init__(self, members, precision="fp32split", tile=(0, 0), graph_steps=0, stream=None):
         import torch
@@ -455,11 +502,14 @@ class Ensemble:
         params = (lb_params * n)()
         keep = []
         ptrs = [(C.c_void_p * n)() for _ in range(4)]
+        rt = all("rho" not in m and "R" in m for m in members)  # lb_ensemble_init_rt members
         for k, m in enumerate(members):
             params[k] = make_params(m["Lx"], m["Ly"], m["tau"], m.get("gx", 0.0), m.get("gy", 0.0),
                                     m.get("T_top", 1.0), m.get("T_bottom", 1.0),
                                     m.get("y_periodic", False), precision,
                                     wall_mode=m.get("wall_mode", "rest"))
+            if rt:
+                continue
             for j, key in enumerate(("rho", "ux", "uy", "T")):
                 a = _host_f64(m[key], (int(m["Ly"]), int(m["Lx"])))
                 keep.append(a)
@@ -474,8 +524,14 @@ class Ensemble:
         self._ws = torch.empty(nbytes.value, dtype=torch.uint8, device="cuda")
         opts.workspace = self._ws.data_ptr()
         opts.workspace_bytes = nbytes.value
-        check(lib().lb_ensemble_init(n, params, *ptrs, C.byref(opts), C.byref(self._ctx)),
-              "lb_ensemble_init")
+        if rt:
+            ratios = np.array([float(m["R"]) for m in members], np.float64)
+            seeds = np.array([int(m.get("seed", 0)) & ((1 << 64) - 1) for m in members], np.uint64)
+            check(lib().lb_ensemble_init_rt(n, params, ratios.ctypes.data, seeds.ctypes.data, C.byref(opts),
+                                            C.byref(self._ctx)), "lb_ensemble_init_rt")
+        else:
+            check(lib().lb_ensemble_init(n, params, *ptrs, C.byref(opts), C.byref(self._ctx)),
+                  "lb_ensemble_init")
 
     def step(self, n: int = 1) -> None:
         check(lib().lb_ensemble_step(self._ctx, int(n)), "lb_ensemble_step")
