@@ -295,6 +295,7 @@ lb_status lb_ensemble_init(int n, const lb_params* members, const double* const*
                            const double* const* ux, const double* const* uy,
                            const double* const* T, const lb_ensemble_opts* opts,
                            lb_ensemble** out) {
+    lbg::NvtxRange nvtx_("lb_ensemble_init");
     if (!out) return LB_ERR_ARG;
     *out = nullptr;
     if (check_members(n, members) != LB_OK || !rho || !ux || !uy || !T) return LB_ERR_ARG;
@@ -410,6 +411,7 @@ lb_status lb_ensemble_init(int n, const lb_params* members, const double* const*
 }
 
 lb_status lb_ensemble_step(lb_ensemble* e, int n) {
+    lbg::NvtxRange nvtx_("lb_ensemble_step");
     if (!e || n < 0) return LB_ERR_ARG;
     while (n >= e->graph_steps && !e->graph_failed) {
         if (!e->graph[e->cur] && !capture(e, e->cur)) {
@@ -441,6 +443,7 @@ lb_status lb_ensemble_sync(lb_ensemble* e) {
 }
 
 lb_status lb_ensemble_autotune(lb_ensemble* e, int steps, int* tile_x, int* tile_y, double* mlups) {
+    lbg::NvtxRange nvtx_("lb_ensemble_autotune");
     if (!e || steps < 1) return LB_ERR_ARG;
     cudaEvent_t a, b;
     ENS_CUDA(cudaEventCreate(&a));

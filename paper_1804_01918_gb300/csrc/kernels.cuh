@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "d2q37_gpu.cuh"
 
@@ -13,6 +14,16 @@ namespace lbg {
 double thermal_scale();                                   // r = 1 / sqrt(sum w c_x^2)
 void fill_step_params(const lb_params& p, StepParams& sp);  // per-lattice kernel parameters
 void set_last_error(const char* msg);                     // message returned by lb_last_error()
+
+// A named NVTX range for the lifetime of a scope: the C ABI marks each entry point, so profilers
+// (ncu --nvtx, nsys) can attribute the kernels they capture to the call that queued them. Costs
+// nothing measurable when no tool is attached.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Threads per block of the site-parallel kernels.
 constexpr int SITE_BLOCK = 128;

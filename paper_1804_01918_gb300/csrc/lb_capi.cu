@@ -327,6 +327,7 @@ void lb_free(lb_ctx* c) {
 
 lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const double* uy,
                   const double* T, lb_ctx** out) {
+    lbg::NvtxRange nvtx_("lb_init");
     if (!out) return LB_ERR_ARG;
     *out = nullptr;
     lb_status st = check_params(p);
@@ -406,6 +407,7 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
 }
 
 lb_status lb_step(lb_ctx* c, int n) {
+    lbg::NvtxRange nvtx_("lb_step");
     if (!c || n < 0) return LB_ERR_ARG;
     // the learned step's check schedule varies from step to step: launch it directly
     while (n >= GRAPH_STEPS && !c->graph_failed && !c->learned) {
@@ -426,6 +428,7 @@ lb_status lb_step(lb_ctx* c, int n) {
 }
 
 lb_status lb_propagate(lb_ctx* c) {
+    lbg::NvtxRange nvtx_("lb_propagate");
     if (!c) return LB_ERR_ARG;
     cudaError_t e = c->p.precision == LB_FP64
                         ? launch_propagate_fp64((const double*)c->buf[c->cur],
@@ -453,6 +456,7 @@ lb_status lb_set_staging(lb_ctx* c, int use_tma) {
 }
 
 lb_status lb_collide(lb_ctx* c) {
+    lbg::NvtxRange nvtx_("lb_collide");
     if (!c) return LB_ERR_ARG;
     if (c->p.precision != LB_FP64 || c->learned) return LB_ERR_STATE;
     cudaError_t e = launch_collide_fp64((double*)c->buf[c->cur], c->sp, c->flag, c->stream);
@@ -475,6 +479,7 @@ lb_status lb_moments_device(lb_ctx* c, double* rho, double* ux, double* uy, doub
 
 namespace {
 lb_status moments_to_host(lb_ctx* c, double* rho, double* ux, double* uy, double* T, int half_step) {
+    lbg::NvtxRange nvtx_("lb_moments");
     if (!c) return LB_ERR_ARG;
     const size_t n = (size_t)c->p.Lx * c->p.Ly;
     lb_status st = launch_moments(c, c->stage, c->stage + n, c->stage + 2 * n, c->stage + 3 * n, half_step);
@@ -498,6 +503,7 @@ lb_status lb_moments_half_step(lb_ctx* c, double* rho, double* ux, double* uy, d
 }
 
 lb_status lb_get_populations(lb_ctx* c, double* f) {
+    lbg::NvtxRange nvtx_("lb_get_populations");
     if (!c || !f) return LB_ERR_ARG;
     const size_t n = (size_t)c->p.Lx * c->p.Ly;
     const size_t skip = (size_t)HALO * c->p.Lx;
@@ -521,6 +527,7 @@ lb_status lb_get_populations(lb_ctx* c, double* f) {
 }
 
 lb_status lb_set_populations(lb_ctx* c, const double* f) {
+    lbg::NvtxRange nvtx_("lb_set_populations");
     if (!c || !f) return LB_ERR_ARG;
     const size_t n = (size_t)c->p.Lx * c->p.Ly;
     const size_t skip = (size_t)HALO * c->p.Lx;
@@ -568,6 +575,7 @@ lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int
 
 lb_status lb_collide_train(lb_ctx* c, const float* pre, const float* post, size_t npairs, int epochs,
                            uint64_t seed) {
+    lbg::NvtxRange nvtx_("lb_collide_train");
     if (!c || !pre || !post || npairs < (size_t)LB_MLP_TILE || epochs < 1) return LB_ERR_ARG;
     if (c->p.precision != LB_FP32SPLIT || c->p.Lx % 32 || c->p.Ly % 32) return LB_ERR_STATE;
     if (npairs > (size_t)((1ll << 31) - 1)) return LB_ERR_ARG;

@@ -1001,6 +1001,7 @@ lb_status lb_mlp_loss_grad_fp32(lb_mlp* net, const float* x, const float* t, int
 
 lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long long n, int epochs, int batch,
                        float lr, uint64_t seed, float* epoch_loss, void* stream) {
+    lbg::NvtxRange nvtx_("lb_mlp_train");
     if (!net || !pre || !post || n < batch || epochs < 1 || batch < TILE || batch % TILE || !(lr > 0.0f))
         return LB_ERR_ARG;
     if (n > (1ll << 31) - 1) return LB_ERR_ARG;

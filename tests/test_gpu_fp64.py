@@ -255,3 +255,38 @@ def test_fused_step_matches_oracle_over_1000_steps(L, orc, wall_mode):
     want = orc.run(orc.init_fields(st), tau=0.9, nsteps=1000, gy=st.gy, T_top=st.T_top,
                    T_bottom=st.T_bottom, wall_mode=wall_mode)
     assert rel_err(got, want) <= TOL
+
+
+def test_device_allocation_failure_is_reported(L):
+    """A lattice whose populations cannot fit in device memory (2e9 sites, ~1.2 TB): lb_init fails
+    with LB_ERR_ALLOC before it reads any host field, names the failed allocation, and the device
+    stays usable."""
+    import ctypes as C
+    lib = L.lib()
+    ctx = C.c_void_p()
+    p = L.make_params(40000, 50000, 0.9)
+    z = np.zeros(4)
+    assert lib.lb_init(C.byref(p), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
+                       C.byref(ctx)) == 2
+    assert not ctx.value
+    assert "cudaMalloc" in L.last_error()
+    st = inputs.rayleigh_taylor(32, 32, R=2.0, seed=0)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    lat.step(3)
+    lat.sync()
+    lat.close()
+
+
+def test_nan_in_the_initial_fields_is_reported(L):
+    """A NaN planted in the host density field: the first step flags it and lb_sync reports
+    LB_ERR_NONFINITE once."""
+    st = inputs.rayleigh_taylor(32, 32, R=2.0, seed=0)
+    rho = st.rho.copy()
+    rho[17, 9] = np.nan
+    lat = L.Lattice(32, 32, 0.9, rho, st.ux, st.uy, st.T, gy=st.gy, T_top=st.T_top,
+                    T_bottom=st.T_bottom)
+    lat.step(1)
+    with pytest.raises(L.NonFiniteError):
+        lat.sync()
+    lat.sync()
+    lat.close()
