@@ -59,6 +59,14 @@ TRAFFIC_FP64 = {"bytes_per_site": (698.451200e6 + 645.175040e6) / 2359296,
                             "fixed96.cuh": "230ce312473f859cc6d2a14a546ddbc82d3e920b1271978c9772d38d0f9c9945"}}
 
 
+# The same for step_fp32split_kernel: ncu DRAM bytes of one launch on the 1152x2048 capture
+# (profiles/step_fp32split_1152x2048_full.md), 349.268 MB + 302.076 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.267968e6 + 302.075648e6) / 2359296,
+                     "sources": {"step_fp32dev.cu": "f7bea2d3cbbe2d04fe483e7128f764fa264de6526fc29eb26adead235e1bd8fd",
+                                 "site_fp32dev.cuh": "f4542e2a08c5072a0ae055c99012edf604399ac0cb580e2041a22c3c7185ac0b",
+                                 "d2q37_gpu.cuh": "e799c3d0676dd4783c435ef37669924b7c1fe610b5ed2ce10eee8a6d1b32e702"}}
+
+
 def sources_match(table):
     import hashlib
     csrc = os.path.join(ROOT, "paper_1804_01918_gb300", "csrc")
@@ -409,8 +417,11 @@ def main():
     else:
         gbs = FP32DEV_BYTES_PER_SITE * sites / kernel_s / 1e9
         kname = "step_fp32split_tma_kernel" if args.staging == "tma" else f"step_{args.precision}_kernel"
+        traffic32 = (round(TRAFFIC_FP32SPLIT["bytes_per_site"] * sites)
+                     if args.precision == "fp32split" and args.staging == "plain"
+                     and sources_match(TRAFFIC_FP32SPLIT) and (LX, LY) == (2304, 8192) else None)
         roofline = {"bound": "hbm", "kernel": kname, "achieved": round(gbs, 1),
-                    "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": None,
+                    "peak": hbm, "unit": "GB/s", "frac": round(gbs / hbm, 4), "traffic": traffic32,
                     "peak_note": "MEASURED_PEAKS.json hbm_gbs (of measured)"}
 
     # ---- FP32-deviation form: MLUPS and L2 error against the FP64 path ----
