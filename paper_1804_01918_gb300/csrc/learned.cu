@@ -412,10 +412,16 @@ constexpr int FW_W2 = FW_W1 + BYTES_W1;
 constexpr int FW_W3 = FW_W2 + BYTES_W2;
 constexpr int FW_RED = FW_W3 + BYTES_W3;   // block reductions (2 x 4 floats)
 constexpr int FW_MISC = FW_RED + 64;
-constexpr int FW_BYTES = FW_MISC + 64;
+// per-CTA copies of the biases and of the normalisation (input standard deviations as reciprocals)
+constexpr int FC_B1 = 0, FC_B2 = FC_B1 + HID, FC_B3 = FC_B2 + HID, FC_MUX = FC_B3 + NOUTP,
+              FC_ISDX = FC_MUX + NOUTP, FC_MUT = FC_ISDX + NOUTP, FC_SDT = FC_MUT + NOUTP,
+              FC_FLOATS = FC_SDT + NOUTP;
+constexpr int FW_CONST = FW_MISC + 64;
+constexpr int FW_BYTES = FW_CONST + FC_FLOATS * 4;
 
 struct FwdCtx {
     char* sm;
+    const float* cst;  // FC_* constants in shared memory
     uint64_t* bar;
     uint32_t tm;
     uint32_t ph;
@@ -425,9 +431,9 @@ struct FwdCtx {
 // Network output (normalised, 37 values) of the inputs this thread stored as row tid of the X
 // image (all threads call it together). Returns false if a tensor-core wait gave up.
 __device__ __forceinline__ bool mlp_forward_tile(FwdCtx& f, const NetDev& net, float* y) {
-    const float* b1 = net.params + OFF_B1;
-    const float* b2 = net.params + OFF_B2;
-    const float* b3 = net.params + OFF_B3;
+    const float* b1 = f.cst + FC_B1;
+    const float* b2 = f.cst + FC_B2;
+    const float* b3 = f.cst + FC_B3;
     float v[32];
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -480,6 +486,19 @@ __device__ __forceinline__ void fwd_setup(FwdCtx& f, const NetDev& net, char* sm
     copy_to_smem(sm + FW_W1, net.w1img, BYTES_W1);
     copy_to_smem(sm + FW_W2, net.w2img, BYTES_W2);
     copy_to_smem(sm + FW_W3, net.w3img, BYTES_W3);
+    float* cst = reinterpret_cast<float*>(sm + FW_CONST);
+    for (int k = f.tid; k < HID; k += blockDim.x) {
+        cst[FC_B1 + k] = net.params[OFF_B1 + k];
+        cst[FC_B2 + k] = net.params[OFF_B2 + k];
+    }
+    for (int k = f.tid; k < NOUT; k += blockDim.x) {
+        cst[FC_B3 + k] = net.params[OFF_B3 + k];
+        cst[FC_MUX + k] = net.norm[k];
+        cst[FC_ISDX + k] = 1.0f / net.norm[NIN + k];
+        cst[FC_MUT + k] = net.norm[2 * NIN + k];
+        cst[FC_SDT + k] = net.norm[3 * NIN + k];
+    }
+    f.cst = cst;
     if (f.tid == 0) tc::mbar_init(f.bar, 1);
     if (f.warp == 0) tc::tmem_alloc(tslot, 256);
     tc::fence_before_sync();
@@ -532,10 +551,10 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
     fwd_setup(f, net, sm);
     float* red = reinterpret_cast<float*>(sm + FW_RED);
     const int ntx = P.Lx / 32, ntiles = ntx * (P.Ly / 32);
-    const float* mu_x = net.norm;
-    const float* sd_x = net.norm + NIN;
-    const float* mu_t = net.norm + 2 * NIN;
-    const float* sd_t = net.norm + 3 * NIN;
+    const float* mu_x = f.cst + FC_MUX;
+    const float* isd_x = f.cst + FC_ISDX;
+    const float* mu_t = f.cst + FC_MUT;
+    const float* sd_t = f.cst + FC_SDT;
     bool alive = true;
     for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
         const int x0 = (t % ntx) * 32, y0 = (t / ntx) * 32;
@@ -554,7 +573,7 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
             split_pre(d, P, s, flag);
             float xn[KIN];
 #pragma unroll
-            for (int i = 0; i < NIN; ++i) xn[i] = (d[i] - mu_x[i]) / sd_x[i];
+            for (int i = 0; i < NIN; ++i) xn[i] = (d[i] - mu_x[i]) * isd_x[i];
 #pragma unroll
             for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
 #pragma unroll
