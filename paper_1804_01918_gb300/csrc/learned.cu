@@ -81,12 +81,15 @@ __global__ void pairs_kernel(const float* __restrict__ src, const StepParams P, 
     for (int i = 0; i < NPOP; ++i) post[(size_t)k * NPOP + i] = d[i];
 }
 
-// Per-population sums (FP64) of pre and of post - pre for the normalisation statistics.
-__global__ void stats_kernel(const float* __restrict__ pre, const float* __restrict__ post, long long n,
-                             double* __restrict__ acc /* [4][37]: sum x, sum x^2, sum t, sum t^2 */) {
-    __shared__ double s[4 * NIN];
-    for (int k = threadIdx.x; k < 4 * NIN; k += blockDim.x) s[k] = 0.0;
-    __syncthreads();
+// Per-population sums (FP64) of pre and of post - pre for the normalisation statistics, as
+// per-block partials part[block][4][37] (sum x, sum x^2, sum t, sum t^2) that the host adds in
+// block order. Each block reduces its threads' sums with a fixed tree, so the result does not
+// depend on scheduling.
+constexpr int STATS_THREADS = 256;
+__global__ void __launch_bounds__(STATS_THREADS)
+stats_kernel(const float* __restrict__ pre, const float* __restrict__ post, long long n,
+             double* __restrict__ part) {
+    __shared__ double red[STATS_THREADS];
     double lx[NIN], lx2[NIN], lt[NIN], lt2[NIN];
     for (int i = 0; i < NIN; ++i) lx[i] = lx2[i] = lt[i] = lt2[i] = 0.0;
     for (long long r = (long long)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (long long)gridDim.x * blockDim.x)
@@ -97,14 +100,17 @@ __global__ void stats_kernel(const float* __restrict__ pre, const float* __restr
             lt[i] += t;
             lt2[i] += t * t;
         }
-    for (int i = 0; i < NIN; ++i) {
-        atomicAdd(&s[i], lx[i]);
-        atomicAdd(&s[NIN + i], lx2[i]);
-        atomicAdd(&s[2 * NIN + i], lt[i]);
-        atomicAdd(&s[3 * NIN + i], lt2[i]);
+    for (int k = 0; k < 4 * NIN; ++k) {
+        const int i = k % NIN, q = k / NIN;
+        red[threadIdx.x] = q == 0 ? lx[i] : q == 1 ? lx2[i] : q == 2 ? lt[i] : lt2[i];
+        __syncthreads();
+        for (int w = STATS_THREADS / 2; w > 0; w >>= 1) {
+            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) part[(size_t)blockIdx.x * 4 * NIN + k] = red[0];
+        __syncthreads();
     }
-    __syncthreads();
-    for (int k = threadIdx.x; k < 4 * NIN; k += blockDim.x) atomicAdd(&acc[k], s[k]);
 }
 
 // Column sums over a warp: on return lane L holds the sum over the warp's 32 lanes of their v[L]
@@ -137,8 +143,9 @@ constexpr int TR_W2 = TR_W1 + BYTES_W1;
 constexpr int TR_W3 = TR_W2 + BYTES_W2;
 constexpr int TR_W3T = TR_W3 + BYTES_W3;
 constexpr int TR_W2T = TR_W3T + BYTES_W3T;
-constexpr int TR_GB = TR_W2T + BYTES_W2T;  // bias-gradient accumulators db1[128] db2[128] db3[48]
-constexpr int TR_MISC = TR_GB + (HID + HID + NOUTP) * 4;
+constexpr int TR_GBN = HID + HID + NOUTP;  // bias-gradient columns db1[128] db2[128] db3[48]
+constexpr int TR_GB = TR_W2T + BYTES_W2T;  // per-warp column sums [4][TR_GBN], added in warp order
+constexpr int TR_MISC = TR_GB + 4 * TR_GBN * 4;
 constexpr int TR_BYTES = TR_MISC + 64;
 
 // One 128-sample tile: forward, loss, backward; writes this CTA's parameter-gradient partial
@@ -162,7 +169,8 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     copy_to_smem(sm + TR_W3, net.w3img, BYTES_W3);
     copy_to_smem(sm + TR_W3T, net.w3timg, BYTES_W3T);
     copy_to_smem(sm + TR_W2T, net.w2timg, BYTES_W2T);
-    for (int k = tid; k < HID + HID + NOUTP; k += blockDim.x) gb[k] = 0.0f;
+    for (int k = tid; k < 4 * TR_GBN; k += blockDim.x) gb[k] = 0.0f;
+    float* gbw = gb + warp * TR_GBN;  // this warp's slots: each written once per tile, no atomics
     if (tid == 0) {
         tc::mbar_init(bar, 1);
         *abort_flag = 0;
@@ -283,11 +291,11 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             float cs[32];
 #pragma unroll
             for (int j = 0; j < 32; ++j) cs[j] = dy[j];
-            atomicAdd(&gb[2 * HID + (tid & 31)], warp_column_sums(cs));
+            gbw[2 * HID + (tid & 31)] = warp_column_sums(cs);
 #pragma unroll
             for (int j = 0; j < 32; ++j) cs[j] = j < NOUTP - 32 ? dy[32 + j] : 0.0f;
             const float c2 = warp_column_sums(cs);
-            if ((tid & 31) < NOUTP - 32) atomicAdd(&gb[2 * HID + 32 + (tid & 31)], c2);
+            if ((tid & 31) < NOUTP - 32) gbw[2 * HID + 32 + (tid & 31)] = c2;
             for (int o = 16; o > 0; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
             if ((tid & 31) == 0) atomicAdd(loss_sm, lsum);
         }
@@ -303,7 +311,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(z[j] + b2[c + j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
-            atomicAdd(&gb[HID + c + (tid & 31)], warp_column_sums(v));
+            gbw[HID + c + (tid & 31)] = warp_column_sums(v);
         }
         {
             float g[NOUTP];
@@ -325,7 +333,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(z[j] + b1[c + j]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
-            atomicAdd(&gb[c + (tid & 31)], warp_column_sums(v));
+            gbw[c + (tid & 31)] = warp_column_sums(v);
         }
         {
             float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W2 + (size_t)tid * HID;  // row o
@@ -352,11 +360,14 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     __syncthreads();
     if (ok) {
         float* out = partial + (size_t)blockIdx.x * PART_STRIDE;
+        auto col = [&](int k) {  // the four warps' column sums, added in warp order
+            return ((gb[k] + gb[TR_GBN + k]) + gb[2 * TR_GBN + k]) + gb[3 * TR_GBN + k];
+        };
         for (int k = tid; k < HID; k += blockDim.x) {
-            out[OFF_B1 + k] = gb[k];
-            out[OFF_B2 + k] = gb[HID + k];
+            out[OFF_B1 + k] = col(k);
+            out[OFF_B2 + k] = col(HID + k);
         }
-        for (int k = tid; k < NOUT; k += blockDim.x) out[OFF_B3 + k] = gb[2 * HID + k];
+        for (int k = tid; k < NOUT; k += blockDim.x) out[OFF_B3 + k] = col(2 * HID + k);
         if (tid == 0) atomicAdd(loss_acc, (double)*loss_sm);
     } else if (tid == 0) {
         atomicOr(flag, ERR_TIMEOUT);
@@ -1033,15 +1044,19 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
     if (st != LB_OK) return st;
     // normalisation statistics from the data (FP64 sums on the device)
     {
-        double* acc = nullptr;
-        L_CUDA(cudaMalloc((void**)&acc, 4 * NIN * sizeof(double)));
-        cudaMemsetAsync(acc, 0, 4 * NIN * sizeof(double), s);
-        stats_kernel<<<4 * sm_count(), 256, 0, s>>>(pre, post, n, acc);
-        std::vector<double> h(4 * NIN);
-        cudaError_t e = cudaMemcpyAsync(h.data(), acc, 4 * NIN * sizeof(double), cudaMemcpyDeviceToHost, s);
+        const int blocks = 4 * sm_count();
+        double* part = nullptr;
+        L_CUDA(cudaMalloc((void**)&part, (size_t)blocks * 4 * NIN * sizeof(double)));
+        stats_kernel<<<blocks, STATS_THREADS, 0, s>>>(pre, post, n, part);
+        std::vector<double> hp((size_t)blocks * 4 * NIN), h(4 * NIN, 0.0);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(hp.data(), part, hp.size() * sizeof(double), cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-        cudaFree(acc);
+        cudaFree(part);
         if (e != cudaSuccess) return fail_l(e, "normalisation statistics");
+        for (int b = 0; b < blocks; ++b)  // block order: the same sums on every run
+            for (int k = 0; k < 4 * NIN; ++k) h[k] += hp[(size_t)b * 4 * NIN + k];
         std::vector<float> norm(4 * NIN);
         for (int i = 0; i < NIN; ++i) {
             const double mx = h[i] / n, vx = std::max(0.0, h[NIN + i] / n - mx * mx);

@@ -121,6 +121,20 @@ def test_training_reduces_loss(L):
     net.close()
 
 
+def test_training_is_deterministic(L):
+    """Two trainings from the same seed on the same pairs give the same parameters bit for bit:
+    every reduction in the training path (bias-gradient column sums, per-tile gradient partials,
+    normalisation statistics) adds in a fixed order."""
+    pre, post = collect_pairs(L, steps=12, every=3)
+    nets = [L.MLP(seed=4) for _ in range(2)]
+    for net in nets:
+        net.train(pre, post, epochs=2, batch=2048, lr=1e-3, seed=9)
+    (pa, na), (pb, nb) = nets[0].get_params(), nets[1].get_params()
+    assert np.array_equal(pa, pb) and np.array_equal(na, nb)
+    for net in nets:
+        net.close()
+
+
 def test_bound_zero_falls_back_everywhere_and_equals_plain(L):
     st = inputs.rayleigh_taylor(64, 128, R=2.0, seed=2)
     net = L.MLP(seed=2)
