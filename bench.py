@@ -44,6 +44,12 @@ NPOP = 37
 # SM x f_max (the 1.25 TFLOP/s nominal FP64 rate counts an FMA as 2 flops).
 FP64_INST_PER_SITE = 293
 FP64_FLOP_PER_SITE = 470
+# The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
+# equilibrium written per population, BGK relaxation with the gravity shift): 2763 flops, counted
+# by compiling the oracle's collide with an operation-counting scalar type
+# (oracle/count_collide_flops.cpp; tests/test_oracle_flops.py re-derives the number). The
+# kernel's factored formulation needs 470 of them in FP64.
+ORACLE_FLOP_PER_SITE = 2763
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 SM_COUNT = 152
@@ -404,6 +410,8 @@ def main():
                                  "FMA = 2 flops; measured by the library's FMA probe below",
                     "algorithmic_fp64_inst_per_site": FP64_INST_PER_SITE,
                     "achieved_tflops": round(FP64_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
+                    "oracle_flop_per_site": ORACLE_FLOP_PER_SITE,
+                    "achieved_tflops_oracle_formulation": round(ORACLE_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
                     "peak_tflops": round(2 * peak, 4),
                     "probe_fp64_tflops": round(probe_tf, 4),
                     "probe_fp64_varying_tflops": round(probe_var_tf, 4),
