@@ -1159,9 +1159,10 @@ lb_status learned_info(const LearnedState* ls, const lb_mlp** net, double* bound
     return LB_OK;
 }
 
+// The caller has synchronised the stream that last used the state (lb_free and the collide
+// setters do), so freeing does not need a device-wide synchronisation.
 void learned_destroy(LearnedState* ls) {
     if (!ls) return;
-    cudaDeviceSynchronize();
     if (ls->mem) cudaFree(ls->mem);
     delete ls;
 }

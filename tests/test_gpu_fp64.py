@@ -290,3 +290,31 @@ def test_nan_in_the_initial_fields_is_reported(L):
         lat.sync()
     lat.sync()
     lat.close()
+
+
+def test_api_edge_cases(L):
+    """lb_step(0) is a no-op, a negative count is an argument error, moments accept NULL outputs,
+    and a population round trip through the host is exact (FP64) or within FP32 storage rounding
+    of the deviations (FP32 forms)."""
+    import ctypes as C
+    st = inputs.rayleigh_taylor(40, 48, R=2.0, seed=8)
+    lat = L.Lattice.from_fields(st, tau=0.9)
+    f0 = lat.get_populations()
+    lat.step(0)
+    assert lat.steps_done == 0 and np.array_equal(lat.get_populations(), f0)
+    assert L.lib().lb_step(lat._ctx, -1) == 1
+    rho = np.empty((48, 40))
+    assert L.lib().lb_moments(lat._ctx, rho.ctypes.data, None, None, None) == 0
+    assert np.allclose(rho, st.rho, rtol=1e-14, atol=0)
+    lat.set_populations(f0)
+    assert np.array_equal(lat.get_populations(), f0)
+    lat.close()
+    cx, cy, w, _ = L.velocity_set()
+    for form in ("fp32dev", "fp32split"):
+        lat = L.Lattice.from_fields(st, tau=0.9, precision=form)
+        f = lat.get_populations()
+        lat.set_populations(f)
+        g = lat.get_populations()
+        dev = np.abs(f - w[:, None, None])
+        assert np.all(np.abs(g - f) <= dev * 2.0**-24 + 1e-300), form
+        lat.close()
