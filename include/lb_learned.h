@@ -34,7 +34,8 @@ typedef struct lb_mlp lb_mlp;
 /* New network on the current device: weights and biases uniform in +-1/sqrt(fan_in) from a
  * SplitMix64 stream seeded with `seed`, identity normalisation. The library allocates its memory. */
 lb_status lb_mlp_create(uint64_t seed, lb_mlp** out);
-void lb_mlp_free(lb_mlp* net); /* NULL-safe */
+void lb_mlp_free(lb_mlp* net); /* NULL-safe; waits for the device's queued work first, since the
+                                  network may be in use on any stream */
 
 /* Host copies of the FP32 parameters (LB_MLP_NPARAM floats) and normalisation (148 floats). */
 lb_status lb_mlp_get_params(const lb_mlp* net, float* params, float* norm);
