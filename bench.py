@@ -268,7 +268,14 @@ def workload_config(world, precision="fp64"):
                   f"129 MB L2)"}
 
 
+# The headline metric: the plain FP64 step's MLUPS on one GB300, with the FP32, batched and learned
+# forms beside it (under "forms", each with its L2 error against the FP64 step).
+HEADLINE_METRIC = "D2Q37 MLUPS on 1 GB300: FP64 plain vs FP32/batched/NN-collide at stated L2 err"
+
+
 def metric_name(precision="fp64"):
+    if precision == "fp64":
+        return HEADLINE_METRIC
     return f"D2Q37 MLUPS, fused {PRECISION_LABEL[precision]} LB step (propagate+collide+walls)"
 
 
