@@ -447,6 +447,7 @@ def main():
         if not args.no_learned:
             forms["learned"], net = measure_learned(lb, torch, np, inputs, st, stream,
                                                     forms["fp32split"]["mlups"])
+            forms["learned"]["speedup_vs_fp64"] = round(forms["learned"]["mlups"] / (value / world), 3)
         for form, e in measure_accuracy(lb, np, st, stream, learned_net=net).items():
             forms[form]["rel_l2_vs_fp64"] = e
         if net is not None:
