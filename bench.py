@@ -441,7 +441,7 @@ def main():
 
     # ---- FP32-deviation form: MLUPS and L2 error against the FP64 path ----
     forms = None
-    if not args.no_forms and rank == 0:
+    if not args.no_forms and rank == 0 and args.precision == "fp64":  # forms are compared with FP64
         forms = measure_forms(lb, torch, np, st, stream, value / world)
         net = None
         if not args.no_learned:
