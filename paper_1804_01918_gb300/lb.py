@@ -489,7 +489,7 @@ def moments_noalloc(Lx: int, Ly: int, f_device_ptr: int, precision=LB_FP64, stre
 
 
 class Ensemble:
-    """Independent D2Q37 lattices advanced together by one persistent launch per step
+    """Independent D2Q37 lattices advanced together by one launch per step
     (include/lb_ensemble.h). members: list of dicts with Lx, Ly, tau and optional gx, gy, T_top,
     T_bottom, y_periodic, plus host fields rho, ux, uy, T ([Ly][Lx] float64) -- or, for every
     member, a temperature ratio R and a seed instead of fields (lb_ensemble_init_rt)."""
