@@ -68,9 +68,11 @@ __host__ __device__ constexpr int shell_of(int i) { return i <= NPAIR ? shellh(i
 // expansion, regrouped by powers of a.
 struct ShellCoef {
     double w, alpha, beta, gamma, delta, eps;
-    // the same coefficients times w (and w/24, w/6): the FP64 step folds the prefactor
-    // w rho / tau into each shell's coefficients so that a pair costs one multiply and 7 FMAs
-    double aw, bw, gw, dw, ew, w24, w6;
+    // constants of the FP64 step's relaxation (step_fp64.cu, relax_coefficients), X = xi^2:
+    // W A0 = q_a0 R0 + q_a1 P1 + q_a2 P2,  16 W A2 = q_e0 Ra + q_e1 t,  4 W B1 = q_b0 Rb + q_b1 t,
+    // C = q_c rho / tau, with q_a0 = 2w, q_a1 = 2wX, q_a2 = wX^2/2, q_e0 = 16w, q_e1 = 8wX,
+    // q_b0 = 8w, q_b1 = 4wX, q_c = 32w/3
+    double q_a0, q_a1, q_a2, q_e0, q_e1, q_b0, q_b1, q_c;
 };
 
 // FP32 copies of the shell coefficients for the FP32 kernels (converting doubles on the device
@@ -92,6 +94,9 @@ struct StepParams {
     double gx, gy;         // gravity
     double tgx, tgy;       // tau * g
     double dT_force;       // tau (1 - tau) |g|^2 / D
+    // FP64 step (relax_coefficients, lambda = 1/4): lambda r^2, lambda r tau g, (dT_force - 1) / 2,
+    // -1 / (4 lambda^2 r^2), 2^-48 / tau
+    double lr2, lrtgx, lrtgy, hdT, mu4, om48;
     double T_bot, T_top;   // wall temperatures below row 0 and above row Ly - 1
     ShellCoef sh[NSHELL];
     double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population

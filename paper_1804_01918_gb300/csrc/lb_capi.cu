@@ -117,14 +117,23 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh[s].gamma = (X * X - 2.0 * (DIM + 2.0) * X + DIM * (DIM + 2.0)) / 8.0;
         sp.sh[s].delta = (X - DIM - 4.0) / 4.0;
         sp.sh[s].eps = (X - DIM - 2.0) / 2.0;
-        sp.sh[s].aw = sp.sh[s].alpha * sp.sh[s].w;
-        sp.sh[s].bw = sp.sh[s].beta * sp.sh[s].w;
-        sp.sh[s].gw = sp.sh[s].gamma * sp.sh[s].w;
-        sp.sh[s].dw = sp.sh[s].delta * sp.sh[s].w;
-        sp.sh[s].ew = sp.sh[s].eps * sp.sh[s].w;
-        sp.sh[s].w24 = sp.sh[s].w / 24.0;
-        sp.sh[s].w6 = sp.sh[s].w / 6.0;
+        const double w = sp.sh[s].w;
+        sp.sh[s].q_a0 = 2.0 * w;
+        sp.sh[s].q_a1 = 2.0 * w * X;
+        sp.sh[s].q_a2 = 0.5 * w * X * X;
+        sp.sh[s].q_e0 = 16.0 * w;
+        sp.sh[s].q_e1 = 8.0 * w * X;
+        sp.sh[s].q_b0 = 8.0 * w;
+        sp.sh[s].q_b1 = 4.0 * w * X;
+        sp.sh[s].q_c = 32.0 * w / 3.0;
     }
+    constexpr double lambda = 0.25;
+    sp.lr2 = lambda * sp.r2;
+    sp.lrtgx = lambda * r * sp.tgx;
+    sp.lrtgy = lambda * r * sp.tgy;
+    sp.hdT = 0.5 * (sp.dT_force - 1.0);
+    sp.mu4 = -1.0 / (4.0 * lambda * lambda * sp.r2);
+    sp.om48 = std::ldexp(sp.omega, -48);
     sp.r_f = (float)sp.r;
     sp.r2_f = (float)sp.r2;
     sp.omega_f = (float)sp.omega;

@@ -13,8 +13,9 @@
 //   3. store to dst with evict-first hints (write-once stream; GPU stores do no read-for-ownership,
 //      the effect the paper gets from non-temporal stores, Sec. 4);
 //   4. threads of rows 0..2 and Ly-3..Ly-1 also write the wall halo rows of dst.
-// On GB300 this kernel is bound by the FP64 pipe (about 380 FP64 operations per site against 592
-// bytes of traffic), so the code minimises FP64 operations; index math is integer-only.
+// On GB300 this kernel is bound by the FP64 pipe (FP64 instructions per site against 592 bytes of
+// traffic), so the code minimises FP64 operations: moment sums on the integer pipe, equilibrium
+// coefficients shared per shell (relax_coefficients), integer-only index math.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -71,16 +72,15 @@ struct PullAll<-1> {
                                                long long) {}
 };
 
-struct SiteMoments {
-    double rho, ux, uy, T;
+// The four moment sums of one site in units of 2^-48: n0 = sum f, nx = sum f c_x, ny = sum f c_y,
+// ne = sum f |c|^2. They are exact 96-bit fixed-point sums on the integer pipe (fixed96.cuh) over
+// bins of equal c_x and equal c_y, each rounded to FP64 once. *bad gets the status-word bit of a
+// population outside the exact range: 1 for an infinity or NaN, 2 for a finite |f| >= 16, else 0.
+struct SiteSums {
+    double n0, nx, ny, ne;
 };
 
-// rho, u, T of one site from bins of equal c_x and equal c_y:
-//   rho = sum f, rho u = r sum f c, rho (u^2 + D T) = r^2 sum f |c|^2.
-// The bins and their combinations are exact 96-bit fixed-point sums on the integer pipe
-// (fixed96.cuh); each of the four sums is rounded to FP64 once. *bad gets the status-word bit of a
-// population outside the exact range: 1 for an infinity or NaN, 2 for a finite |f| >= 16, else 0.
-__device__ __forceinline__ SiteMoments site_moments(const double* f, double r, double r2, int* bad) {
+__device__ __forceinline__ SiteSums site_sums(const double* f, int* bad) {
     using namespace fx;
     I96 bx[7], by[7];
 #pragma unroll
@@ -102,76 +102,150 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
                           minus96(by[4], by[2]));
     const I96 ne = plus96(plus96(plus96(times9(px3), times4(px2)), px1),
                           plus96(plus96(times9(py3), times4(py2)), py1));
-    // the four sums in units of 2^-48: the scale cancels in u and T
-    const double n0d = to_double48(n0);
-    const double inv = 1.0 / n0d;
+    return SiteSums{to_double48(n0), to_double48(nx), to_double48(ny), to_double48(ne)};
+}
+
+struct SiteMoments {
+    double rho, ux, uy, T;
+};
+
+// rho, u, T of one site (Sec. 3): rho = sum f, rho u = r sum f c, rho (u^2 + D T) = r^2 sum f |c|^2.
+// The 2^-48 scale of the sums cancels in u and T.
+__device__ __forceinline__ SiteMoments site_moments(const double* f, double r, double r2, int* bad) {
+    const SiteSums s = site_sums(f, bad);
+    const double inv = 1.0 / s.n0;
     const double rinv = r * inv;
     SiteMoments m;
-    m.rho = n0d * 0x1p-48;
-    m.ux = to_double48(nx) * rinv;
-    m.uy = to_double48(ny) * rinv;
+    m.rho = s.n0 * 0x1p-48;
+    m.ux = s.nx * rinv;
+    m.uy = s.ny * rinv;
     const double u2 = m.ux * m.ux + m.uy * m.uy;
-    m.T = 0.5 * fma(r2 * inv, to_double48(ne), -u2);
+    m.T = 0.5 * fma(r2 * inv, s.ne, -u2);
     return m;
 }
 
-// xi.u of pair I from the multiples U[k] = k r u_x, V[k] = k r u_y (k = 1, 2, 3): a copy for the
-// axis pairs, one add or subtract for the others.
+// The relaxation of one site toward the shifted equilibrium f_eq(rho, u*, T*), u* = u + tau g,
+// T* = T + tau (1 - tau) |g|^2 / D (Sec. 3 model; ShellCoef gives the polynomial), written so that
+// the FP64 pipe does as little as possible:
+//   - pair variable b = lambda xi.u* with lambda = 1/4, from the multiples U[k] = k lambda r u*_x,
+//     V[k] = k lambda r u*_y (k = 0..3); with W = w rho / tau per shell,
+//       W E = WA0 + b^2 (WA2 + C b^2),  W O = b (WB1 + C b^2),
+//       WA0 = W A0, WA2 = 16 W A2, WB1 = 4 W B1, C = (32/3) W
+//     (lambda = 1/4 makes the b^4 coefficient of E and the b^3 coefficient of O the same number C);
+//   - the shell coefficients grouped by powers of xi^2 (D = 2, h = theta / 2, m = 1/2 - |u*|^2 / 4):
+//       A0 = 2 m^2 + 1/2 + 2h (1 - 4m + 2h) + xi^2 h (2m - 4h) + xi^4 h^2 / 2,
+//       A2 = m - 3h + xi^2 h / 2,  B1 = 2m - 4h + xi^2 h,
+//     so that each shell costs 8 operations on site values shared by all shells;
+//   - the 2^-48 scale of the sums folded into the constants of StepParams (om48, lr2).
+// Per pair, f'(+-c) = (1 - 1/tau) f(+-c) + W E +- W O: one multiply (b^2) and 7 FMAs.
+struct Relax64 {
+    double U[4], V[4];
+    double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], C[NSHELL];
+    double X;  // temperature_sum: T = r^2 X / (2 n0) before the forcing shift
+};
+
+// X and a = 1 / n0 of the sums (the temperature is T = r^2 a X / 2), computed first so that the
+// caller can check them before the coefficients.
+__device__ __forceinline__ double temperature_sum(const SiteSums& s, double a) {
+    return fma(-a, fma(s.nx, s.nx, s.ny * s.ny), s.ne);
+}
+
+__device__ __forceinline__ void relax_coefficients(const StepParams& P, const SiteSums& s, double a,
+                                                   Relax64& R) {
+    const double k = P.lr2 * a;                        // lambda r^2 / N0
+    const double U1 = fma(s.nx, k, P.lrtgx);           // lambda r u*_x
+    const double V1 = fma(s.ny, k, P.lrtgy);
+    const double h = fma(R.X, k, P.hdT);               // (T* - 1) / 2
+    const double m = fma(fma(U1, U1, V1 * V1), P.mu4, 0.5);
+    const double rw = s.n0 * P.om48;                   // rho / tau
+    const double t = rw * h;
+    const double bq = fma(h, -2.0, m);                 // m - 2h
+    const double Rb = rw * bq;
+    const double Ra2 = Rb - t;                         // rw (m - 3h)
+    const double P1 = t * bq;
+    const double P2 = t * h;
+    const double R0h = fma(t, fma(h, 2.0, fma(m, -4.0, 1.0)), rw * fma(m, m, 0.25));
+    R.WA0[0] = P.sh[0].q_a0 * R0h;
+#pragma unroll
+    for (int q = 1; q < NSHELL; ++q) {
+        const ShellCoef& c = P.sh[q];
+        R.WA0[q] = fma(c.q_a2, P2, fma(c.q_a1, P1, c.q_a0 * R0h));
+        R.WA2[q] = fma(c.q_e1, t, c.q_e0 * Ra2);
+        R.WB1[q] = fma(c.q_b1, t, c.q_b0 * Rb);
+        R.C[q] = c.q_c * rw;
+    }
+    R.U[0] = R.V[0] = 0.0;
+    R.U[1] = U1;
+    R.V[1] = V1;
+    R.U[2] = U1 + U1;
+    R.V[2] = V1 + V1;
+    R.U[3] = R.U[2] + U1;
+    R.V[3] = R.V[2] + V1;
+}
+
+// b of pair I: a copy for the axis pairs, one add or subtract for the others.
 template <int I>
-__device__ __forceinline__ double pair_a(const double* U, const double* V) {
+__device__ __forceinline__ double pair_b(const double* U, const double* V) {
     constexpr int cx = cxh(I), cy = cyh(I);
     if (cy == 0) return U[cx];
     if (cx == 0) return cy > 0 ? V[cy] : -V[-cy];
     return cy > 0 ? U[cx] + V[cy] : U[cx] - V[-cy];
 }
 
-// Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S. With the prefactor
-// W = w rho / tau folded into the shell coefficients (WA0 = W A0, WA2 = W A2, WB1 = W B1,
-// W24 = W / 24, W6 = W / 6):  W E = WA0 + a^2 (WA2 + a^2 W24),  W O = a (WB1 + a^2 W6),
-// W f_eq(+-c) = W E +- W O, and f' = (1 - 1/tau) f + W f_eq -- one multiply (a^2) and 7 FMAs.
-template <int I>
-__device__ __forceinline__ void relax_pair(const double* f, double* __restrict__ dst, long long dsto,
-                                           long long plane, const double* U, const double* V,
-                                           const double* WA0, const double* WA2, const double* WB1,
-                                           const double* W24, const double* W6, double omc) {
+// Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S; store(i, v) writes
+// population i.
+template <int I, class Store>
+__device__ __forceinline__ void relax_pair(const double* f, const Relax64& R, double omc, Store& store) {
     constexpr int S = shellh(I);
-    const double a = pair_a<I>(U, V);
-    const double a2 = a * a;
-    const double we = fma(a2, fma(a2, W24[S], WA2[S]), WA0[S]);
-    const double q = fma(a2, W6[S], WB1[S]);
-    const double gp = fma(a, q, we);
-    const double gm = fma(-a, q, we);
-    __stcs(dst + plane_off(I, plane) + dsto, fma(omc, f[I], gp));
-    __stcs(dst + plane_off(I + NPAIR, plane) + dsto, fma(omc, f[I + NPAIR], gm));
+    const double b = pair_b<I>(R.U, R.V);
+    const double b2 = b * b;
+    const double we = fma(b2, fma(b2, R.C[S], R.WA2[S]), R.WA0[S]);
+    const double q = fma(b2, R.C[S], R.WB1[S]);
+    store(I, fma(omc, f[I], fma(b, q, we)));
+    store(I + NPAIR, fma(omc, f[I + NPAIR], fma(-b, q, we)));
 }
 
 template <int I>
 struct RelaxAll {
-    __device__ __forceinline__ static void run(const double* f, double* __restrict__ dst,
-                                               long long dsto, long long plane, const double* U,
-                                               const double* V, const double* WA0, const double* WA2,
-                                               const double* WB1, const double* W24, const double* W6,
-                                               double omc) {
-        RelaxAll<I - 1>::run(f, dst, dsto, plane, U, V, WA0, WA2, WB1, W24, W6, omc);
-        relax_pair<I>(f, dst, dsto, plane, U, V, WA0, WA2, WB1, W24, W6, omc);
+    template <class Store>
+    __device__ __forceinline__ static void run(const double* f, const Relax64& R, double omc, Store& store) {
+        RelaxAll<I - 1>::run(f, R, omc, store);
+        relax_pair<I>(f, R, omc, store);
     }
 };
 template <>
 struct RelaxAll<0> {
-    __device__ __forceinline__ static void run(const double*, double*, long long, long long, const double*,
-                                               const double*, const double*, const double*, const double*,
-                                               const double*, const double*, double) {}
+    template <class Store>
+    __device__ __forceinline__ static void run(const double*, const Relax64&, double, Store&) {}
 };
 
-// The multiples k r u (k = 1, 2, 3) of the shifted velocity, for pair_a.
-__device__ __forceinline__ void velocity_multiples(double urx, double ury, double* U, double* V) {
-    U[0] = V[0] = 0.0;
-    U[1] = urx;
-    V[1] = ury;
-    U[2] = urx + urx;
-    V[2] = ury + ury;
-    U[3] = U[2] + urx;
-    V[3] = V[2] + ury;
+// Collide site (x, y) with populations f (Sec. 3: moments, shifted equilibrium, BGK relaxation):
+// store(i, o, v) writes population i at element offset o of its plane (the site's own offset,
+// then the wall halo rows the site feeds). Shared by the fused step and the collide kernel, so the
+// two give the same bits.
+template <class Store>
+__device__ __forceinline__ void collide_site(const double* f, const StepParams& P, int x, int y,
+                                             int* __restrict__ flag, Store&& store) {
+    int bad;
+    const SiteSums s = site_sums(f, &bad);
+    const double a = 1.0 / s.n0;
+    Relax64 R;
+    R.X = temperature_sum(s, a);
+    if (bad_positive(s.n0) || bad_positive(R.X) || bad) atomicOr(flag, bad ? bad : 1);
+    relax_coefficients(P, s, a, R);
+
+    const long long o = (long long)(y + HALO) * P.Lx + x;
+    auto own = [&](int i, double v) { store(i, o, v); };
+    own(0, fma(P.omc, f[0], R.WA0[0]));
+    RelaxAll<NPAIR>::run(f, R, P.omc, own);
+
+    // wall halo rows from this site's post-collision fields (rho, u + g, T)
+    if (!P.y_periodic && (y < HALO || y >= P.Ly - HALO)) {
+        const double ra = P.r * a;
+        const double T = (P.r2 * 0.5) * a * R.X;
+        write_wall_rows(P, x, y, s.n0 * 0x1p-48, fma(s.nx, ra, P.gx), fma(s.ny, ra, P.gy), T, flag,
+                        store);
+    }
 }
 
 // Per-shell coefficients of the equilibrium at (theta, u2) scaled by prefactor W_s = wscale w_s.
@@ -192,27 +266,6 @@ __device__ __forceinline__ void shell_coefficients(const StepParams& P, double t
     }
 }
 
-// The same coefficients already multiplied by W_s = rw w_s, from site quantities scaled by rw:
-//   W A0 = w rw a00 + (alpha w) rw theta + (beta w) rw theta u2 + (gamma w) rw theta^2, etc.
-__device__ __forceinline__ void shell_coefficients_scaled(const StepParams& P, double th, double u2,
-                                                          double rw, double* WA0, double* WA2,
-                                                          double* WB1, double* W24, double* W6) {
-    const double r0 = rw * fma(u2, fma(u2, 0.125, -0.5), 1.0);
-    const double r20 = rw * fma(u2, -0.25, 0.5);
-    const double r10 = rw * fma(u2, -0.5, 1.0);
-    const double r1 = rw * th;
-    const double ru = r1 * u2;
-    const double r2 = r1 * th;
-#pragma unroll
-    for (int s = 0; s < NSHELL; ++s) {
-        WA0[s] = fma(P.sh[s].gw, r2, fma(P.sh[s].bw, ru, fma(P.sh[s].aw, r1, P.sh[s].w * r0)));
-        WA2[s] = fma(P.sh[s].dw, r1, P.sh[s].w * r20);
-        WB1[s] = fma(P.sh[s].ew, r1, P.sh[s].w * r10);
-        W24[s] = rw * P.sh[s].w24;
-        W6[s] = rw * P.sh[s].w6;
-    }
-}
-
 __global__ void __launch_bounds__(SITE_BLOCK)
 step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P,
                  int* __restrict__ flag) {
@@ -225,28 +278,8 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
 
     double f[NPOP];
     PullAll<NPOP - 1>::run(src, f, x, y, Lx, Ly, P.y_periodic, plane);
-
-    int bad;
-    const SiteMoments m = site_moments(f, P.r, P.r2, &bad);
-    if (bad_positive(m.rho) || bad_positive(m.T) || bad) atomicOr(flag, bad ? bad : 1);
-
-    // forcing: equilibrium at u + tau g, T + tau (1 - tau) |g|^2 / D
-    const double uxs = m.ux + P.tgx;
-    const double uys = m.uy + P.tgy;
-    const double th = (m.T + P.dT_force) - 1.0;
-    const double u2 = uxs * uxs + uys * uys;
-    double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], W24[NSHELL], W6[NSHELL];
-    shell_coefficients_scaled(P, th, u2, m.rho * P.omega, WA0, WA2, WB1, W24, W6);
-
-    const long long dsto = (long long)(y + HALO) * Lx + x;
-    __stcs(dst + dsto, fma(P.omc, f[0], WA0[0]));
-    double U[4], V[4];
-    velocity_multiples(P.r * uxs, P.r * uys, U, V);
-    RelaxAll<NPAIR>::run(f, dst, dsto, plane, U, V, WA0, WA2, WB1, W24, W6, P.omc);
-
-    // wall halo rows of dst from this site's post-collision fields (rho, u + g, T)
-    write_wall_rows(P, x, y, m.rho, m.ux + P.gx, m.uy + P.gy, m.T, flag,
-                    [&](int i, long long o, double v) { __stcs(dst + plane_off(i, plane) + o, v); });
+    collide_site(f, P, x, y, flag,
+                 [&](int i, long long o, double v) { __stcs(dst + plane_off(i, plane) + o, v); });
 }
 
 // Collide only, in place (the paper's separate collide kernel, Sec. 3-5 and Table 1): each thread
@@ -265,21 +298,8 @@ collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict_
     double v[NPOP];
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, plane) + o];
-    int bad;
-    const SiteMoments m = site_moments(v, P.r, P.r2, &bad);
-    if (bad_positive(m.rho) || bad_positive(m.T) || bad) atomicOr(flag, bad ? bad : 1);
-    const double uxs = m.ux + P.tgx;
-    const double uys = m.uy + P.tgy;
-    const double th = (m.T + P.dT_force) - 1.0;
-    const double u2 = uxs * uxs + uys * uys;
-    double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], W24[NSHELL], W6[NSHELL];
-    shell_coefficients_scaled(P, th, u2, m.rho * P.omega, WA0, WA2, WB1, W24, W6);
-    __stcs(f + o, fma(P.omc, v[0], WA0[0]));
-    double U[4], V[4];
-    velocity_multiples(P.r * uxs, P.r * uys, U, V);
-    RelaxAll<NPAIR>::run(v, f, o, plane, U, V, WA0, WA2, WB1, W24, W6, P.omc);
-    write_wall_rows(P, x, y, m.rho, m.ux + P.gx, m.uy + P.gy, m.T, flag,
-                    [&](int i, long long oh, double val) { __stcs(f + plane_off(i, plane) + oh, val); });
+    collide_site(v, P, x, y, flag,
+                 [&](int i, long long oh, double val) { __stcs(f + plane_off(i, plane) + oh, val); });
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
