@@ -87,6 +87,9 @@ struct StepParams {
     int y_periodic;
     int wall_mode;         // lb_wall_mode: 0 rest-equilibrium halo rows, 1 mirror closure
     long long plane;       // elements per population plane, (Ly + 2*HALO) * Lx
+    // row of a site index n < 2^31 without a division: y = (n * row_m) >> row_s (row_of)
+    unsigned row_m;
+    int row_s;
     double r;              // thermal scale, xi = r c
     double r2;             // r^2
     double omega;          // 1 / tau
@@ -109,6 +112,13 @@ struct StepParams {
     long long pull_b32[NPOP];
     long long plane_b32[NPOP];
 };
+
+// y = n / Lx for 0 <= n < 2^31 by a multiply and a shift (Granlund & Montgomery 1994, Thm. 4.2:
+// with l = ceil(log2 Lx) and m = ceil(2^(31 + l) / Lx) < 2^32, floor(n m / 2^(31 + l)) = floor(n / Lx)
+// for all n < 2^31). Keeps the integer division's float conversions off the FP64 pipe.
+__device__ __forceinline__ int row_of(int n, const StepParams& P) {
+    return (int)(((unsigned long long)(unsigned)n * P.row_m) >> P.row_s);
+}
 
 // The equilibrium of one site (Sec. 3 model: 4th-order Hermite expansion, D = 2) in FP64, handed
 // population by population to sink(i, f_eq_i) in the library's order. With theta = T - 1,

@@ -9,7 +9,7 @@
 //                        multiple of 2^-80);
 //   N = m >> (995 - e)   for |f| < 2^-28 (truncated toward zero: error below q ~ 8e-25).
 // Sums of such N are exact in 96 bits (|sum |c|^2 N| < 18 x 37 x 16 x 2^80 < 2^95). A sum is
-// rounded to FP64 at the end (to_double48, error <= 1 ulp), so the moments are at least as
+// rounded to FP64 at the end (to_double48, correctly rounded), so the moments are at least as
 // accurate as any FP64 summation order. Populations of magnitude >= 16, infinities and NaN are
 // reported through the maximum exponent that to96 collects.
 #pragma once
@@ -78,13 +78,35 @@ __device__ __forceinline__ I96 to96(double f, unsigned& emax) {
 // The biased exponent limit of to96's exact range (|f| < 16).
 constexpr unsigned EXP_LIMIT = 1026u;
 
-// v in units of 2^-48 (i.e. 2^48 times the value v 2^-80) rounded to FP64: the top 64 bits converted at
-// once (one rounding), then the low word added (a second rounding; total error <= 1 ulp). Two
-// integer-to-FP64 conversions and one FMA, all on the FP64 pipe; callers fold the 2^-48 scale
-// into later arithmetic where it cancels.
+// v in units of 2^-48 (i.e. 2^48 times the value v 2^-80) rounded to FP64 on the integer pipe, with
+// no FP64 instruction: |v| is shifted so that its leading one lands on bit 63 of a 64-bit window,
+// the window's leading 53 bits are rounded to nearest, ties to even (round bit: the next bit;
+// sticky: the rest of the window and the bits of v shifted out below it), and sign, exponent and
+// significand are assembled into the IEEE-754 bit pattern. The result is the correctly rounded
+// value. Callers fold the 2^-48 scale into later arithmetic where it cancels.
 __device__ __forceinline__ double to_double48(const I96& v) {
-    const long long top = (long long)(((unsigned long long)v.w2 << 32) | v.w1);
-    return fma((double)v.w0, 0x1p-32, (double)top);
+    const unsigned s = (unsigned)((int)v.w2 >> 31);
+    const I96 m = minus96(I96{v.w0 ^ s, v.w1 ^ s, v.w2 ^ s}, I96{s, s, s});  // |v| < 2^95
+    // the most significant nonzero word of |v| (x2) and the two words below it
+    const bool t2 = m.w2 != 0u, t1 = m.w1 != 0u;
+    const unsigned x2 = t2 ? m.w2 : (t1 ? m.w1 : m.w0);
+    const unsigned x1 = t2 ? m.w1 : (t1 ? m.w0 : 0u);
+    const unsigned x0 = t2 ? m.w0 : 0u;
+    const int base = t2 ? 64 : (t1 ? 32 : 0);  // the bit of v that is bit 0 of x2
+    const int z = __clz(x2);                   // 32 only for v = 0
+    const unsigned lo = __funnelshift_l(x0, x1, z);
+    const unsigned long long W = ((unsigned long long)__funnelshift_l(x1, x2, z) << 32) | lo;
+    // t = the leading 53 bits and the round bit; x = 1 rounds up a set round bit (sticky or odd)
+    const unsigned long long t = W >> 10;
+    const unsigned sticky = (lo & 0x3FFu) | (x0 << (z & 31));  // x0 = 0 unless z < 32
+    const unsigned long long x = (sticky != 0u ? 1ull : 0ull) | ((t >> 1) & 1ull);
+    const unsigned long long sig = (t + x) >> 1;  // 53 bits (2^53 if rounding carried)
+    // leading one of |v| at bit base + 31 - z, i.e. 2^(base - 1 - z) in units of 2^-48: biased
+    // exponent base + 1022 - z; adding sig (implicit one at bit 52) to (exponent - 1) << 52 sets
+    // the exponent field, and a rounding carry moves it up by one
+    const unsigned long long e1 = (unsigned long long)(base + 1021 - z);
+    const unsigned long long bits = ((e1 << 52) + sig) | ((unsigned long long)(s & 0x80000000u) << 32);
+    return z == 32 ? 0.0 : __longlong_as_double((long long)bits);
 }
 
 }  // namespace fx

@@ -99,6 +99,13 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
     sp.T_bot = p.T_bottom;
     sp.T_top = p.T_top;
     sp.plane = (long long)p.Lx * ((long long)p.Ly + 2 * HALO);
+    {
+        int l = 0;
+        while ((1ll << l) < (long long)p.Lx) ++l;
+        const unsigned long long num = 1ull << (31 + l);
+        sp.row_m = (unsigned)((num + (unsigned long long)p.Lx - 1) / (unsigned long long)p.Lx);
+        sp.row_s = 31 + l;
+    }
     const double r = thermal_scale();
     sp.r = r;
     sp.r2 = r * r;

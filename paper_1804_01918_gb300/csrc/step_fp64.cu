@@ -272,7 +272,7 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
-    const int y = site / Lx;
+    const int y = row_of(site, P);
     const int x = site - y * Lx;
     const long long plane = P.plane;
 
@@ -291,7 +291,7 @@ collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict_
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
-    const int y = site / Lx;
+    const int y = row_of(site, P);
     const int x = site - y * Lx;
     const long long plane = P.plane;
     const long long o = (long long)(y + HALO) * Lx + x;
@@ -307,7 +307,7 @@ propagate_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, 
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
-    const int y = site / Lx;
+    const int y = row_of(site, P);
     const int x = site - y * Lx;
     const long long plane = P.plane;
     double f[NPOP];
@@ -352,7 +352,7 @@ init_fp64_kernel(const double* __restrict__ rho, const double* __restrict__ ux,
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
-    const int y = site / Lx;
+    const int y = row_of(site, P);
     const int x = site - y * Lx;
     double fe[NPOP];
     site_equilibrium(P, rho[site], ux[site], uy[site], T[site], fe);
@@ -392,7 +392,7 @@ moments_fp64_kernel(const double* __restrict__ f, const StepParams P, double* __
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= Lx * Ly) return;
-    const int y = site / Lx;
+    const int y = row_of(site, P);
     const int x = site - y * Lx;
     const long long o = (long long)(y + HALO) * Lx + x;
     double v[NPOP];

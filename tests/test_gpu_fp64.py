@@ -110,6 +110,42 @@ def test_moments_match_oracle(L, orc):
     assert np.max(np.abs(ux - oux)) < 1e-15 and np.max(np.abs(uy - ouy)) < 1e-15
 
 
+def test_density_is_the_correctly_rounded_sum(L):
+    """lb_moments' rho is the exact sum of a site's 37 populations rounded once to FP64 (round to
+    nearest, ties to even): the moment sums are exact fixed-point sums, rounded on the integer
+    pipe. Populations of mixed sign and magnitude in [2^-28, 16), including sites whose exact sum
+    needs many more than 53 bits, and dyadic sites whose sums land on rounding ties. A site whose
+    populations are symmetric under c -> -c has zero momentum exactly."""
+    from fractions import Fraction
+    Lx, Ly = 24, 10
+    rng = np.random.default_rng(17)
+    cx, cy, w, _ = L.velocity_set()
+    f = w[:, None, None] * (1.0 + 0.3 * rng.uniform(-1, 1, (37, Ly, Lx)))
+    # rows 2-3: magnitudes spread over 2^-28 .. 2^0 with random signs (positive site sums)
+    spread = 2.0 ** rng.uniform(-28, 0, (37, 2, Lx)) * rng.choice([-1.0, 1.0], (37, 2, Lx))
+    spread[0] = np.abs(spread[1:]).sum(axis=0) + 0.5
+    assert spread[0].max() < 16.0
+    f[:, 2:4] = spread
+    # rows 4-5: dyadic values whose sums hit exact ties of the 53-bit rounding
+    big = rng.integers(1, 2**20, (37, 2, Lx)).astype(np.float64)
+    f[:, 4:6] = big * 2.0**-18
+    s0 = f[:, 4:6].sum(axis=0)  # exact: every term is a multiple of 2^-18 below 2^2
+    f[0, 4:6] += np.spacing(s0) * 0.5 * rng.choice([1.0, 3.0], (2, Lx))  # half an ulp, or 1.5
+    # row 6: symmetric populations (zero momentum)
+    half = w[1:19, None] * (1.0 + 0.2 * rng.uniform(-1, 1, (18, Lx)))
+    f[1:19, 6] = half
+    f[19:37, 6] = half
+    lat = L.Lattice(Lx, Ly, 0.9, np.ones((Ly, Lx)), np.zeros((Ly, Lx)), np.zeros((Ly, Lx)),
+                    np.ones((Ly, Lx)))
+    lat.set_populations(f)
+    rho, ux, uy, _ = lat.moments()
+    for y in range(Ly):
+        for x in range(Lx):
+            exact = sum((Fraction(float(v)) for v in f[:, y, x]), Fraction(0))
+            assert rho[y, x] == float(exact), (y, x, rho[y, x], float(exact))
+    assert np.all(ux[6] == 0.0) and np.all(uy[6] == 0.0)
+
+
 def test_graph_replay_equals_single_launches(L):
     st = inputs.rayleigh_taylor(64, 64, R=2.0, seed=4)
     a = L.Lattice.from_fields(st, tau=0.9)
