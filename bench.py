@@ -66,11 +66,11 @@ TRAFFIC_FP64 = {"bytes_per_site": (698.454016e6 + 644.638976e6) / 2359296,
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
-# (profiles/step_fp32split_1152x2048_full.md), 349.249 MB + 302.633 MB for 2359296 sites.
-TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.248768e6 + 302.632960e6) / 2359296,
+# (profiles/step_fp32split_1152x2048_full.md), 349.264 MB + 302.659 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.264384e6 + 302.658560e6) / 2359296,
                      "sources": {"step_fp32dev.cu": "f7bea2d3cbbe2d04fe483e7128f764fa264de6526fc29eb26adead235e1bd8fd",
-                                 "site_fp32dev.cuh": "f4542e2a08c5072a0ae055c99012edf604399ac0cb580e2041a22c3c7185ac0b",
-                                 "d2q37_gpu.cuh": "fed5fcb20f9537344f8f89d12761818b47ba38132aedcbf1187b1b59ed286c1d"}}
+                                 "site_fp32dev.cuh": "2bec55bb0c8093653f3119da19e18338764c7916e04862214191eac268db6e21",
+                                 "d2q37_gpu.cuh": "347da3abc1f8c248f42854da96be6351e00becaae0150b5407077648a12204b8"}}
 
 
 def sources_match(table):

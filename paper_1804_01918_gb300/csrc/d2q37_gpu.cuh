@@ -79,6 +79,9 @@ struct ShellCoef {
 // would run on GB300's narrow FP64 pipe).
 struct ShellCoef32 {
     float w, alpha, beta, gamma, delta, eps;
+    // constants of the FP32 relaxation (site_fp32dev.cuh, relax_coefficients32), X = xi^2:
+    // q_a0 = w, q_a1 = 2wX, q_a2 = wX^2/2, q_e0 = 16w, q_e1 = 8wX, q_b0 = 8w, q_b1 = 4wX, q_c = 32w/3
+    float q_a0, q_a1, q_a2, q_e0, q_e1, q_b0, q_b1, q_c;
 };
 
 // Everything a step kernel needs, passed by value as a kernel parameter.
@@ -105,7 +108,7 @@ struct StepParams {
     double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population
     double wall_top[NPOP]; // same at T_top
     // FP32 copies of the scalars above and of the shell coefficients
-    float r_f, r2_f, omega_f, omc_f, gx_f, gy_f, tgx_f, tgy_f, dT_force_f, pad_f;
+    float r_f, r2_f, omega_f, omc_f, gx_f, gy_f, tgx_f, tgy_f, dT_force_f, lr_f;  // lr_f = r / 4
     ShellCoef32 sh32[NSHELL];
     // byte offsets for 4-byte populations: pull_b32[i] = 4 (i plane - c_iy Lx - c_ix) from a site's
     // own element (valid where the pull does not wrap), plane_b32[i] = 4 i plane

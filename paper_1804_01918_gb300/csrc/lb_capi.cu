@@ -150,6 +150,7 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
     sp.tgx_f = (float)sp.tgx;
     sp.tgy_f = (float)sp.tgy;
     sp.dT_force_f = (float)sp.dT_force;
+    sp.lr_f = (float)(0.25 * sp.r);
     for (int s = 0; s < NSHELL; ++s) {
         sp.sh32[s].w = (float)sp.sh[s].w;
         sp.sh32[s].alpha = (float)sp.sh[s].alpha;
@@ -157,6 +158,15 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh32[s].gamma = (float)sp.sh[s].gamma;
         sp.sh32[s].delta = (float)sp.sh[s].delta;
         sp.sh32[s].eps = (float)sp.sh[s].eps;
+        const double w = sp.sh[s].w, X = sp.r2 * shell_c2(s);
+        sp.sh32[s].q_a0 = (float)w;
+        sp.sh32[s].q_a1 = (float)(2.0 * w * X);
+        sp.sh32[s].q_a2 = (float)(0.5 * w * X * X);
+        sp.sh32[s].q_e0 = (float)(16.0 * w);
+        sp.sh32[s].q_e1 = (float)(8.0 * w * X);
+        sp.sh32[s].q_b0 = (float)(8.0 * w);
+        sp.sh32[s].q_b1 = (float)(4.0 * w * X);
+        sp.sh32[s].q_c = (float)(32.0 * w / 3.0);
     }
     for (int i = 0; i < NPOP; ++i) {
         sp.plane_b32[i] = 4ll * i * sp.plane;

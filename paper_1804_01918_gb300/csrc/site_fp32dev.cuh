@@ -96,44 +96,92 @@ __device__ __forceinline__ Macro macro_of(const DevSums& s, double r, double r2)
     return m;
 }
 
-// FP32 collide of pair I: deviations of the post-collision populations I and I + NPAIR.
-template <int I>
-__device__ __forceinline__ void collide_pair32(float* d, float urx, float ury, const float* A0m1,
-                                               const float* A2, const float* B1, const float* K,
-                                               const float* D, float omc) {
-    constexpr int S = shellh(I);
-    constexpr float cx = (float)cxh(I);
-    constexpr float cy = (float)cyh(I);
-    float a;
-    if (cyh(I) == 0)
-        a = cx * urx;
-    else if (cxh(I) == 0)
-        a = cy * ury;
-    else
-        a = fmaf(cx, urx, cy * ury);
-    const float a2 = a * a;
-    const float em1 = fmaf(a2, fmaf(a2, 1.0f / 24.0f, A2[S]), A0m1[S]);
-    const float o = a * fmaf(a2, 1.0f / 6.0f, B1[S]);
-    const float pp = em1 + o, pm = em1 - o;
-    // (w / tau) (rho P - 1) = (w rho / tau) p + (w / tau) drho = K p + D, P = 1 + p
-    d[I] = fmaf(omc, d[I], fmaf(K[S], pp, D[S]));
-    d[I + NPAIR] = fmaf(omc, d[I + NPAIR], fmaf(K[S], pm, D[S]));
+// FP32 relaxation of deviations d = f - w toward the shifted equilibrium, regrouped as in the
+// FP64 step (step_fp64.cu, relax_coefficients): pair variable b = xi.u*/4 from multiples
+// U[k] = k r u*_x / 4, V[k] = k r u*_y / 4, and per shell (W = w / tau)
+//   (f_eq(+-c) - w) / tau = WA0 + b^2 (WA2 + C b^2) +- b (WB1 + C b^2),
+//   WA0 = W (rho (A0 - 1) + rho - 1),  WA2 = 16 W rho A2,  WB1 = 4 W rho B1,  C = (32/3) W rho,
+// with A0 - 1, A2, B1 polynomials in xi^2 whose site coefficients are shared by all shells (h =
+// theta/2, m = 1/2 - u*^2/4): A0 - 1 = (u*^4/8 - u*^2/2) + 2h (u*^2 - 1 + 2h) + xi^2 2h (m - 2h)
+// + xi^4 h^2 / 2, A2 = m - 3h + xi^2 h / 2, B1 = 2 (m - 2h) + xi^2 h. A0 - 1 is formed from its
+// small terms, so the deviation form loses nothing to cancellation. Per pair: one multiply and 7
+// FMAs; per shell 8 operations.
+struct Relax32 {
+    float U[4], V[4];
+    float WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], C[NSHELL];
+};
+
+// rho and s0 = rho - 1 (kept apart for accuracy), omega = 1/tau, (uxs, uys) = u*, h = (T* - 1)/2.
+__device__ __forceinline__ void relax_coefficients32(const StepParams& P, float rho, float s0,
+                                                     float omega, float uxs, float uys, float h,
+                                                     Relax32& R) {
+    const float u2 = fmaf(uxs, uxs, uys * uys);
+    const float rr = omega * rho, rs = omega * s0;
+    const float a00m1 = u2 * fmaf(u2, 0.125f, -0.5f);
+    const float R0 = fmaf(h + h, fmaf(2.0f, h, u2 - 1.0f), a00m1);  // A0 - 1 at xi = 0
+    const float bq = fmaf(u2, -0.25f, fmaf(h, -2.0f, 0.5f));         // m - 2h
+    const float t = rr * h;
+    const float Q0 = fmaf(rr, R0, rs);
+    const float Q1 = t * bq;
+    const float Q2 = t * h;
+    const float Rb = rr * bq;
+    const float Ra = Rb - t;                                          // rho (m - 3h)
+    R.WA0[0] = P.sh32[0].q_a0 * Q0;
+#pragma unroll
+    for (int q = 1; q < NSHELL; ++q) {
+        const ShellCoef32& c = P.sh32[q];
+        R.WA0[q] = fmaf(c.q_a2, Q2, fmaf(c.q_a1, Q1, c.q_a0 * Q0));
+        R.WA2[q] = fmaf(c.q_e1, t, c.q_e0 * Ra);
+        R.WB1[q] = fmaf(c.q_b1, t, c.q_b0 * Rb);
+        R.C[q] = c.q_c * rr;
+    }
+    const float U1 = P.lr_f * uxs, V1 = P.lr_f * uys;
+    R.U[0] = R.V[0] = 0.0f;
+    R.U[1] = U1;
+    R.V[1] = V1;
+    R.U[2] = U1 + U1;
+    R.V[2] = V1 + V1;
+    R.U[3] = R.U[2] + U1;
+    R.V[3] = R.V[2] + V1;
 }
 
 template <int I>
-struct Collide32 {
-    __device__ __forceinline__ static void run(float* d, float urx, float ury, const float* A0m1,
-                                               const float* A2, const float* B1, const float* K,
-                                               const float* D, float omc) {
-        Collide32<I - 1>::run(d, urx, ury, A0m1, A2, B1, K, D, omc);
-        collide_pair32<I>(d, urx, ury, A0m1, A2, B1, K, D, omc);
+__device__ __forceinline__ float pair_b32(const float* U, const float* V) {
+    constexpr int cx = cxh(I), cy = cyh(I);
+    if (cy == 0) return U[cx];
+    if (cx == 0) return cy > 0 ? V[cy] : -V[-cy];
+    return cy > 0 ? U[cx] + V[cy] : U[cx] - V[-cy];
+}
+
+// Relax pair I (populations I and I + NPAIR) in place.
+template <int I>
+__device__ __forceinline__ void relax_pair32(float* d, const Relax32& R, float omc) {
+    constexpr int S = shellh(I);
+    const float b = pair_b32<I>(R.U, R.V);
+    const float b2 = b * b;
+    const float we = fmaf(b2, fmaf(b2, R.C[S], R.WA2[S]), R.WA0[S]);
+    const float q = fmaf(b2, R.C[S], R.WB1[S]);
+    d[I] = fmaf(omc, d[I], fmaf(b, q, we));
+    d[I + NPAIR] = fmaf(omc, d[I + NPAIR], fmaf(-b, q, we));
+}
+
+template <int I>
+struct Relax32All {
+    __device__ __forceinline__ static void run(float* d, const Relax32& R, float omc) {
+        Relax32All<I - 1>::run(d, R, omc);
+        relax_pair32<I>(d, R, omc);
     }
 };
 template <>
-struct Collide32<0> {
-    __device__ __forceinline__ static void run(float*, float, float, const float*, const float*,
-                                               const float*, const float*, const float*, float) {}
+struct Relax32All<0> {
+    __device__ __forceinline__ static void run(float*, const Relax32&, float) {}
 };
+
+// All 37 deviations relaxed in place.
+__device__ __forceinline__ void relax32(float* d, const Relax32& R, float omc) {
+    d[0] = fmaf(omc, d[0], R.WA0[0]);
+    Relax32All<NPAIR>::run(d, R, omc);
+}
 
 }  // namespace
 
@@ -200,29 +248,10 @@ __device__ __forceinline__ void fp32dev_site(const float* __restrict__ src, floa
     if (bad_positive64(m.rho) || bad_positive64(m.T)) atomicOr(flag, 1);
 
     // shifted equilibrium (forcing), coefficients in FP32 from FP64 moments
-    const double uxs = m.ux + P.tgx;
-    const double uys = m.uy + P.tgy;
-    const double th = (m.T + P.dT_force) - 1.0;
-    const double u2 = uxs * uxs + uys * uys;
-    const float thf = (float)th, u2f = (float)u2;
-    const float a00m1 = (float)(u2 * fma(u2, 0.125, -0.5));  // (1 - u2/2 + u2^2/8) - 1
-    const float a20 = fmaf(u2f, -0.25f, 0.5f);
-    const float b10 = fmaf(u2f, -0.5f, 1.0f);
-    const float thu2 = thf * u2f, th2 = thf * thf;
-    const float orho = P.omega_f * (float)m.rho, odrho = P.omega_f * (float)pre.s0;
-    float A0m1[NSHELL], A2[NSHELL], B1[NSHELL], K[NSHELL], D[NSHELL];
-#pragma unroll
-    for (int s = 0; s < NSHELL; ++s) {
-        A0m1[s] = fmaf(P.sh32[s].gamma, th2,
-                       fmaf(P.sh32[s].beta, thu2, fmaf(P.sh32[s].alpha, thf, a00m1)));
-        A2[s] = fmaf(P.sh32[s].delta, thf, a20);
-        B1[s] = fmaf(P.sh32[s].eps, thf, b10);
-        K[s] = orho * P.sh32[s].w;
-        D[s] = odrho * P.sh32[s].w;
-    }
-    const float omc = P.omc_f;
-    d[0] = fmaf(omc, d[0], fmaf(K[0], A0m1[0], D[0]));
-    Collide32<NPAIR>::run(d, (float)(P.r * uxs), (float)(P.r * uys), A0m1, A2, B1, K, D, omc);
+    Relax32 R;
+    relax_coefficients32(P, (float)m.rho, (float)pre.s0, P.omega_f, (float)(m.ux + P.tgx),
+                         (float)(m.uy + P.tgy), (float)(0.5 * ((m.T + P.dT_force) - 1.0)), R);
+    relax32(d, R, P.omc_f);
 
     // FP64 projection onto the exact post-collision moments (c units):
     //   sum d' = rho - 1,  sum d' c = sum d c + rho g / r,
@@ -371,31 +400,10 @@ __device__ __forceinline__ void split_pre(const float* d, const StepParams& P, S
 // relaxation time and gravity; single lattices pass the same parameters twice.
 __device__ __forceinline__ void split_collide(float* d, const StepParams& C, const StepParams& M,
                                               const SplitPre& s) {
-    const StepParams& P = C;
-    const float r = C.r_f;
-    const float uxs = s.ux + M.tgx_f, uys = s.uy + M.tgy_f;
-    const float th = (s.T + M.dT_force_f) - 1.0f;
-    const float u2 = uxs * uxs + uys * uys;
-    const float a00m1 = u2 * fmaf(u2, 0.125f, -0.5f);
-    const float a20 = fmaf(u2, -0.25f, 0.5f);
-    const float b10 = fmaf(u2, -0.5f, 1.0f);
-    const float thu2 = th * u2, th2 = th * th;
-    // K_k = (w_k / tau) rho and D_k = (w_k / tau) (rho - 1): the relaxed equilibrium deviation of
-    // population i in shell k is K_k p_i + D_k with f_eq = w rho (1 + p)
-    const float orho = M.omega_f * s.rho, odrho = M.omega_f * s.s0;
-    float A0m1[NSHELL], A2[NSHELL], B1c[NSHELL], K[NSHELL], D[NSHELL];
-#pragma unroll
-    for (int k = 0; k < NSHELL; ++k) {
-        A0m1[k] = fmaf(P.sh32[k].gamma, th2,
-                       fmaf(P.sh32[k].beta, thu2, fmaf(P.sh32[k].alpha, th, a00m1)));
-        A2[k] = fmaf(P.sh32[k].delta, th, a20);
-        B1c[k] = fmaf(P.sh32[k].eps, th, b10);
-        K[k] = orho * P.sh32[k].w;
-        D[k] = odrho * P.sh32[k].w;
-    }
-    const float omc = M.omc_f;
-    d[0] = fmaf(omc, d[0], fmaf(K[0], A0m1[0], D[0]));
-    Collide32<NPAIR>::run(d, r * uxs, r * uys, A0m1, A2, B1c, K, D, omc);
+    Relax32 R;
+    relax_coefficients32(C, s.rho, s.s0, M.omega_f, s.ux + M.tgx_f, s.uy + M.tgy_f,
+                         0.5f * ((s.T + M.dT_force_f) - 1.0f), R);
+    relax32(d, R, M.omc_f);
 }
 
 // Project candidate post-collision deviations d (in place) onto the exact post-collision moments:
