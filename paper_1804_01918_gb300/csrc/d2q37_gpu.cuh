@@ -44,6 +44,12 @@ __host__ __device__ constexpr int shell_c2(int s) {
     constexpr int t[NSHELL] = {0, 1, 2, 4, 5, 8, 9, 10};
     return t[s];
 }
+// Per shell, the factor kappa between the pair variable of the FP64 step and the base variable it
+// is evaluated from (1 except the shells (2,0), (2,2), (3,0); step_fp64.cu, pair_base).
+__host__ __device__ constexpr int shell_kappa(int s) {
+    constexpr int t[NSHELL] = {1, 1, 1, 2, 1, 2, 3, 1};
+    return t[s];
+}
 // D2Q37 quadrature weights per shell.
 __host__ __device__ constexpr double shell_w(int s) {
     constexpr double t[NSHELL] = {
@@ -68,11 +74,12 @@ __host__ __device__ constexpr int shell_of(int i) { return i <= NPAIR ? shellh(i
 // expansion, regrouped by powers of a.
 struct ShellCoef {
     double w, alpha, beta, gamma, delta, eps;
-    // constants of the FP64 step's relaxation (step_fp64.cu, relax_coefficients), X = xi^2:
-    // W A0 = q_a0 R0 + q_a1 P1 + q_a2 P2,  16 W A2 = q_e0 Ra + q_e1 t,  4 W B1 = q_b0 Rb + q_b1 t,
-    // C = q_c rho / tau, with q_a0 = 2w, q_a1 = 2wX, q_a2 = wX^2/2, q_e0 = 16w, q_e1 = 8wX,
-    // q_b0 = 8w, q_b1 = 4wX, q_c = 32w/3
-    double q_a0, q_a1, q_a2, q_e0, q_e1, q_b0, q_b1, q_c;
+    // constants of the FP64 step's relaxation (step_fp64.cu, shell_relax), X = xi^2 and
+    // k = shell_kappa: W A0 = q_a0 R0 + q_a1 P1 + q_a2 P2, 16 k^2 W A2 = q_e0 Ra + q_e1 t,
+    // 4 k W B1 = q_b0 Rb + q_b1 t, k^4 C = q_c rho / tau, k^3 C = q_co rho / tau, with q_a0 = 2w,
+    // q_a1 = 2wX, q_a2 = wX^2/2, q_e0 = 16 k^2 w, q_e1 = 8 k^2 wX, q_b0 = 8 k w, q_b1 = 4 k wX,
+    // q_c = 32 k^4 w/3, q_co = 32 k^3 w/3
+    double q_a0, q_a1, q_a2, q_e0, q_e1, q_b0, q_b1, q_c, q_co;
 };
 
 // FP32 copies of the shell coefficients for the FP32 kernels (converting doubles on the device
@@ -100,7 +107,7 @@ struct StepParams {
     double gx, gy;         // gravity
     double tgx, tgy;       // tau * g
     double dT_force;       // tau (1 - tau) |g|^2 / D
-    // FP64 step (relax_coefficients, lambda = 1/4): lambda r^2, lambda r tau g, (dT_force - 1) / 2,
+    // FP64 step (relax_site_terms, lambda = 1/4): lambda r^2, lambda r tau g, (dT_force - 1) / 2,
     // -1 / (4 lambda^2 r^2), 2^-48 / tau
     double lr2, lrtgx, lrtgy, hdT, mu4, om48;
     double T_bot, T_top;   // wall temperatures below row 0 and above row Ly - 1

@@ -124,15 +124,16 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh[s].gamma = (X * X - 2.0 * (DIM + 2.0) * X + DIM * (DIM + 2.0)) / 8.0;
         sp.sh[s].delta = (X - DIM - 4.0) / 4.0;
         sp.sh[s].eps = (X - DIM - 2.0) / 2.0;
-        const double w = sp.sh[s].w;
+        const double w = sp.sh[s].w, k = shell_kappa(s);
         sp.sh[s].q_a0 = 2.0 * w;
         sp.sh[s].q_a1 = 2.0 * w * X;
         sp.sh[s].q_a2 = 0.5 * w * X * X;
-        sp.sh[s].q_e0 = 16.0 * w;
-        sp.sh[s].q_e1 = 8.0 * w * X;
-        sp.sh[s].q_b0 = 8.0 * w;
-        sp.sh[s].q_b1 = 4.0 * w * X;
-        sp.sh[s].q_c = 32.0 * w / 3.0;
+        sp.sh[s].q_e0 = 16.0 * k * k * w;
+        sp.sh[s].q_e1 = 8.0 * k * k * w * X;
+        sp.sh[s].q_b0 = 8.0 * k * w;
+        sp.sh[s].q_b1 = 4.0 * k * w * X;
+        sp.sh[s].q_c = 32.0 * k * k * k * k * w / 3.0;
+        sp.sh[s].q_co = 32.0 * k * k * k * w / 3.0;
     }
     constexpr double lambda = 0.25;
     sp.lr2 = lambda * sp.r2;

@@ -97,7 +97,7 @@ __device__ __forceinline__ Macro macro_of(const DevSums& s, double r, double r2)
 }
 
 // FP32 relaxation of deviations d = f - w toward the shifted equilibrium, regrouped as in the
-// FP64 step (step_fp64.cu, relax_coefficients): pair variable b = xi.u*/4 from multiples
+// FP64 step (step_fp64.cu, relax_site_terms): pair variable b = xi.u*/4 from multiples
 // U[k] = k r u*_x / 4, V[k] = k r u*_y / 4, and per shell (W = w / tau)
 //   (f_eq(+-c) - w) / tau = WA0 + b^2 (WA2 + C b^2) +- b (WB1 + C b^2),
 //   WA0 = W (rho (A0 - 1) + rho - 1),  WA2 = 16 W rho A2,  WB1 = 4 W rho B1,  C = (32/3) W rho,

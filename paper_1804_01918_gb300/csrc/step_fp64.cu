@@ -15,7 +15,7 @@
 //   4. threads of rows 0..2 and Ly-3..Ly-1 also write the wall halo rows of dst.
 // On GB300 this kernel is bound by the FP64 pipe (FP64 instructions per site against 592 bytes of
 // traffic), so the code minimises FP64 operations: moment sums on the integer pipe, equilibrium
-// coefficients shared per shell (relax_coefficients), integer-only index math.
+// coefficients shared per shell (relax_site_terms, shell_relax), integer-only index math.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -127,8 +127,7 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
 // The relaxation of one site toward the shifted equilibrium f_eq(rho, u*, T*), u* = u + tau g,
 // T* = T + tau (1 - tau) |g|^2 / D (Sec. 3 model; ShellCoef gives the polynomial), written so that
 // the FP64 pipe does as little as possible:
-//   - pair variable b = lambda xi.u* with lambda = 1/4, from the multiples U[k] = k lambda r u*_x,
-//     V[k] = k lambda r u*_y (k = 0..3); with W = w rho / tau per shell,
+//   - pair variable b = lambda xi.u* with lambda = 1/4; with W = w rho / tau per shell,
 //       W E = WA0 + b^2 (WA2 + C b^2),  W O = b (WB1 + C b^2),
 //       WA0 = W A0, WA2 = 16 W A2, WB1 = 4 W B1, C = (32/3) W
 //     (lambda = 1/4 makes the b^4 coefficient of E and the b^3 coefficient of O the same number C);
@@ -136,12 +135,18 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
 //       A0 = 2 m^2 + 1/2 + 2h (1 - 4m + 2h) + xi^2 h (2m - 4h) + xi^4 h^2 / 2,
 //       A2 = m - 3h + xi^2 h / 2,  B1 = 2m - 4h + xi^2 h,
 //     so that each shell costs 8 operations on site values shared by all shells;
+//   - b from U1 = lambda r u*_x and V1 = lambda r u*_y: for the shells (2,0), (2,2) and (3,0) the
+//     pair variable is kappa beta with kappa = 2, 2, 3 and beta = U1, V1 or U1 +- V1, whose squares
+//     are already at hand, and the powers of kappa are folded into that shell's constants
+//     (W E = WA0 + beta^2 (k^2 WA2 + k^4 C beta^2), W O = beta (k WB1 + k^3 C beta^2)); the other
+//     diagonal pairs take b from one FMA (2 U1 + V1, U1 + 3 V1, ...);
 //   - the 2^-48 scale of the sums folded into the constants of StepParams (om48, lr2).
-// Per pair, f'(+-c) = (1 - 1/tau) f(+-c) + W E +- W O: one multiply (b^2) and 7 FMAs.
+// Per pair, f'(+-c) = (1 - 1/tau) f(+-c) + W E +- W O: 7 FMAs after beta and beta^2.
 struct Relax64 {
-    double U[4], V[4];
-    double WA0[NSHELL], WA2[NSHELL], WB1[NSHELL], C[NSHELL];
-    double X;  // temperature_sum: T = r^2 X / (2 n0) before the forcing shift
+    double U1, V1, U1s, V1s;  // lambda r u*_x, lambda r u*_y and their squares
+    double B11[2], S11[2];    // beta and beta^2 of the pairs (1, 1) and (1, -1)
+    double rw, t, Rb, Ra2, P1, P2, R0h;  // site terms of the shell coefficients
+    double X;                 // temperature_sum: T = r^2 X / (2 n0) before the forcing shift
 };
 
 // X and a = 1 / n0 of the sums (the temperature is T = r^2 a X / 2), computed first so that the
@@ -150,74 +155,120 @@ __device__ __forceinline__ double temperature_sum(const SiteSums& s, double a) {
     return fma(-a, fma(s.nx, s.nx, s.ny * s.ny), s.ne);
 }
 
-__device__ __forceinline__ void relax_coefficients(const StepParams& P, const SiteSums& s, double a,
-                                                   Relax64& R) {
+// The site terms (everything shared by the shells).
+__device__ __forceinline__ void relax_site_terms(const StepParams& P, const SiteSums& s, double a,
+                                                 Relax64& R) {
     const double k = P.lr2 * a;                        // lambda r^2 / N0
-    const double U1 = fma(s.nx, k, P.lrtgx);           // lambda r u*_x
-    const double V1 = fma(s.ny, k, P.lrtgy);
+    R.U1 = fma(s.nx, k, P.lrtgx);                      // lambda r u*_x
+    R.V1 = fma(s.ny, k, P.lrtgy);
+    R.U1s = R.U1 * R.U1;
+    R.V1s = R.V1 * R.V1;
     const double h = fma(R.X, k, P.hdT);               // (T* - 1) / 2
-    const double m = fma(fma(U1, U1, V1 * V1), P.mu4, 0.5);
-    const double rw = s.n0 * P.om48;                   // rho / tau
-    const double t = rw * h;
+    const double m = fma(R.U1s + R.V1s, P.mu4, 0.5);   // 1/2 - |u*|^2 / 4
+    R.rw = s.n0 * P.om48;                              // rho / tau
+    R.t = R.rw * h;
     const double bq = fma(h, -2.0, m);                 // m - 2h
-    const double Rb = rw * bq;
-    const double Ra2 = Rb - t;                         // rw (m - 3h)
-    const double P1 = t * bq;
-    const double P2 = t * h;
-    const double R0h = fma(t, fma(h, 2.0, fma(m, -4.0, 1.0)), rw * fma(m, m, 0.25));
-    R.WA0[0] = P.sh[0].q_a0 * R0h;
-#pragma unroll
-    for (int q = 1; q < NSHELL; ++q) {
-        const ShellCoef& c = P.sh[q];
-        R.WA0[q] = fma(c.q_a2, P2, fma(c.q_a1, P1, c.q_a0 * R0h));
-        R.WA2[q] = fma(c.q_e1, t, c.q_e0 * Ra2);
-        R.WB1[q] = fma(c.q_b1, t, c.q_b0 * Rb);
-        R.C[q] = c.q_c * rw;
-    }
-    R.U[0] = R.V[0] = 0.0;
-    R.U[1] = U1;
-    R.V[1] = V1;
-    R.U[2] = U1 + U1;
-    R.V[2] = V1 + V1;
-    R.U[3] = R.U[2] + U1;
-    R.V[3] = R.V[2] + V1;
+    R.Rb = R.rw * bq;
+    R.Ra2 = R.Rb - R.t;                                // rw (m - 3h)
+    R.P1 = R.t * bq;
+    R.P2 = R.t * h;
+    R.R0h = fma(R.t, fma(h, 2.0, fma(m, -4.0, 1.0)), R.rw * fma(m, m, 0.25));
 }
 
-// b of pair I: a copy for the axis pairs, one add or subtract for the others.
+// The coefficients of shell S (S >= 1).
+struct ShellRelax {
+    double WA0, WA2, WB1, CE, CO;
+};
+
+template <int S>
+__device__ __forceinline__ ShellRelax shell_relax(const StepParams& P, const Relax64& R) {
+    const ShellCoef& c = P.sh[S];
+    ShellRelax q;
+    q.WA0 = fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h));
+    q.WA2 = fma(c.q_e1, R.t, c.q_e0 * R.Ra2);
+    q.WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);
+    q.CE = c.q_c * R.rw;
+    q.CO = shell_kappa(S) == 1 ? q.CE : c.q_co * R.rw;
+    return q;
+}
+
+// beta and beta^2 of pair I (b = kappa beta, kappa = shell_kappa of its shell).
 template <int I>
-__device__ __forceinline__ double pair_b(const double* U, const double* V) {
-    constexpr int cx = cxh(I), cy = cyh(I);
-    if (cy == 0) return U[cx];
-    if (cx == 0) return cy > 0 ? V[cy] : -V[-cy];
-    return cy > 0 ? U[cx] + V[cy] : U[cx] - V[-cy];
+__device__ __forceinline__ void pair_base(const Relax64& R, double& b, double& b2) {
+    constexpr int cx = cxh(I), cy = cyh(I);  // cx >= 0 for populations 1..18
+    if constexpr (cy == 0) {
+        b = R.U1;
+        b2 = R.U1s;
+    } else if constexpr (cx == 0) {
+        b = R.V1;
+        b2 = R.V1s;
+    } else if constexpr (cx == cy || cx == -cy) {
+        b = R.B11[cy > 0 ? 0 : 1];
+        b2 = R.S11[cy > 0 ? 0 : 1];
+    } else {
+        if constexpr (cx == 1)
+            b = fma(R.V1, (double)cy, R.U1);
+        else
+            b = fma(R.U1, (double)cx, cy > 0 ? R.V1 : -R.V1);
+        b2 = b * b;
+    }
 }
 
-// Relax pair I (populations I and I + NPAIR, opposite vectors) of shell S; store(i, v) writes
-// population i.
+// Relax pair I (populations I and I + NPAIR, opposite vectors) with its shell's coefficients;
+// store(i, v) writes population i.
 template <int I, class Store>
-__device__ __forceinline__ void relax_pair(const double* f, const Relax64& R, double omc, Store& store) {
-    constexpr int S = shellh(I);
-    const double b = pair_b<I>(R.U, R.V);
-    const double b2 = b * b;
-    const double we = fma(b2, fma(b2, R.C[S], R.WA2[S]), R.WA0[S]);
-    const double q = fma(b2, R.C[S], R.WB1[S]);
+__device__ __forceinline__ void relax_pair(const double* f, const Relax64& R, const ShellRelax& c,
+                                           double omc, Store& store) {
+    double b, b2;
+    pair_base<I>(R, b, b2);
+    const double we = fma(b2, fma(b2, c.CE, c.WA2), c.WA0);
+    const double q = fma(b2, c.CO, c.WB1);
     store(I, fma(omc, f[I], fma(b, q, we)));
     store(I + NPAIR, fma(omc, f[I + NPAIR], fma(-b, q, we)));
 }
 
-template <int I>
-struct RelaxAll {
+// All pairs I <= N of shell S.
+template <int S, int N>
+struct ShellPairs {
     template <class Store>
-    __device__ __forceinline__ static void run(const double* f, const Relax64& R, double omc, Store& store) {
-        RelaxAll<I - 1>::run(f, R, omc, store);
-        relax_pair<I>(f, R, omc, store);
+    __device__ __forceinline__ static void run(const double* f, const Relax64& R, const ShellRelax& c,
+                                               double omc, Store& store) {
+        ShellPairs<S, N - 1>::run(f, R, c, omc, store);
+        if constexpr (shellh(N) == S) relax_pair<N>(f, R, c, omc, store);
     }
 };
-template <>
-struct RelaxAll<0> {
+template <int S>
+struct ShellPairs<S, 0> {
     template <class Store>
-    __device__ __forceinline__ static void run(const double*, const Relax64&, double, Store&) {}
+    __device__ __forceinline__ static void run(const double*, const Relax64&, const ShellRelax&, double,
+                                               Store&) {}
 };
+
+template <int S, class Store>
+__device__ __forceinline__ void relax_shell(const double* f, const StepParams& P, const Relax64& R,
+                                            Store& store) {
+    const ShellRelax c = shell_relax<S>(P, R);
+    ShellPairs<S, NPAIR>::run(f, R, c, P.omc, store);
+}
+
+// All 37 populations, shell by shell in an order that ends the live ranges of U1^2, V1^2 and the
+// (1, +-1) betas early: the axis shells, then (1,1) with (2,2), then the rest.
+template <class Store>
+__device__ __forceinline__ void relax_all(const double* f, const StepParams& P, Relax64& R,
+                                          Store& store) {
+    store(0, fma(P.omc, f[0], P.sh[0].q_a0 * R.R0h));
+    relax_shell<1>(f, P, R, store);
+    relax_shell<3>(f, P, R, store);
+    relax_shell<6>(f, P, R, store);
+    R.B11[0] = R.U1 + R.V1;
+    R.B11[1] = R.U1 - R.V1;
+    R.S11[0] = R.B11[0] * R.B11[0];
+    R.S11[1] = R.B11[1] * R.B11[1];
+    relax_shell<2>(f, P, R, store);
+    relax_shell<5>(f, P, R, store);
+    relax_shell<4>(f, P, R, store);
+    relax_shell<7>(f, P, R, store);
+}
 
 // Collide site (x, y) with populations f (Sec. 3: moments, shifted equilibrium, BGK relaxation):
 // store(i, o, v) writes population i at element offset o of its plane (the site's own offset,
@@ -232,12 +283,11 @@ __device__ __forceinline__ void collide_site(const double* f, const StepParams& 
     Relax64 R;
     R.X = temperature_sum(s, a);
     if (bad_positive(s.n0) || bad_positive(R.X) || bad) atomicOr(flag, bad ? bad : 1);
-    relax_coefficients(P, s, a, R);
+    relax_site_terms(P, s, a, R);
 
     const long long o = (long long)(y + HALO) * P.Lx + x;
     auto own = [&](int i, double v) { store(i, o, v); };
-    own(0, fma(P.omc, f[0], R.WA0[0]));
-    RelaxAll<NPAIR>::run(f, R, P.omc, own);
+    relax_all(f, P, R, own);
 
     // wall halo rows from this site's post-collision fields (rho, u + g, T)
     if (!P.y_periodic && (y < HALO || y >= P.Ly - HALO)) {
