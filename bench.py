@@ -66,11 +66,11 @@ TRAFFIC_FP64 = {"bytes_per_site": (698.432000e6 + 645.569024e6) / 2359296,
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
-# (profiles/step_fp32split_1152x2048_full.md), 349.264 MB + 302.659 MB for 2359296 sites.
-TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.264384e6 + 302.658560e6) / 2359296,
+# (profiles/step_fp32split_1152x2048_full.md), 349.252 MB + 303.333 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.251840e6 + 303.333376e6) / 2359296,
                      "sources": {"step_fp32dev.cu": "f7bea2d3cbbe2d04fe483e7128f764fa264de6526fc29eb26adead235e1bd8fd",
-                                 "site_fp32dev.cuh": "2bec55bb0c8093653f3119da19e18338764c7916e04862214191eac268db6e21",
-                                 "d2q37_gpu.cuh": "347da3abc1f8c248f42854da96be6351e00becaae0150b5407077648a12204b8"}}
+                                 "site_fp32dev.cuh": "7b5c71ad25c7fa5eb6656114b7d77d377549e5e43d55abbd6f7d4ecbc1aab053",
+                                 "d2q37_gpu.cuh": "0f71f64285f06f1024691ff1c9d798f37322e5fbb083f045a19e27cc35a755e2"}}
 
 
 def sources_match(table):
