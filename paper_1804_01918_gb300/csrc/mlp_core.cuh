@@ -61,23 +61,46 @@ __host__ __device__ constexpr int elem_off(int r, int k, int K) {
     return ((r >> 3) * (K >> 3) + (k >> 3)) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
 
-// erf(x) by the rational approximation of Abramowitz & Stegun, Handbook of Mathematical Functions
-// (1964), eq. 7.1.26: erf(x) = 1 - (a1 t + ... + a5 t^5) exp(-x^2), t = 1 / (1 + p x), x >= 0,
-// |error| <= 1.5e-7, extended to x < 0 by oddness. The activations it feeds are rounded to
-// bfloat16 (relative 4e-3), so this error is invisible; it is several times cheaper than erff.
-__device__ __forceinline__ float erf_as(float x) {
-    const float ax = fabsf(x);
-    const float t = __fdividef(1.0f, fmaf(0.3275911f, ax, 1.0f));  // argument >= 1: no special cases
-    const float poly =
-        t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f),
-                 0.254829592f);
-    const float e = 1.0f - poly * __expf(-ax * ax);
-    return copysignf(e, x);
+// GELU(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2, with erf from the rational approximation
+// of Abramowitz & Stegun, Handbook of Mathematical Functions (1964), eq. 7.1.26:
+//   erf(x) = 1 - P(t) exp(-x^2),  P(t) = a1 t + ... + a5 t^5,  t = 1 / (1 + p x),  x >= 0,
+// |error| <= 1.5e-7, extended to x < 0 by oddness. With x = |z| / sqrt 2 and E = exp(-z^2 / 2):
+//   Phi(z) = [z >= 0] - sign(z) P E / 2,  GELU(z) = max(z, 0) - |z| P E / 2,
+//   GELU'(z) = Phi(z) + z phi(z) = [z >= 0] + E (z / sqrt(2 pi) - sign(z) P / 2),
+// so the sign handling is a max or a select. The reciprocal and the exponential are the hardware
+// approximations (rcp.approx, ex2.approx: relative error ~2^-22); the activations they feed are
+// rounded to bfloat16 (relative 4e-3), so neither error is visible.
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
 }
-// GELU(z) = z Phi(z), Phi(z) = (1 + erf(z / sqrt 2)) / 2;  GELU'(z) = Phi(z) + z phi(z).
-__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erf_as(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+// P(t) / 2 and E for |z| = a
+__device__ __forceinline__ void gelu_parts(float a, float& half_p, float& e) {
+    constexpr float kP = (float)(0.3275911 * 0.70710678118654752);  // p / sqrt 2
+    constexpr float c1 = 0.5f * 0.254829592f, c2 = 0.5f * -0.284496736f, c3 = 0.5f * 1.421413741f,
+                    c4 = 0.5f * -1.453152027f, c5 = 0.5f * 1.061405429f;
+    constexpr float kE = (float)(-0.5 * 1.4426950408889634);         // -log2(e) / 2
+    const float t = rcp_approx(fmaf(kP, a, 1.0f));                   // argument >= 1
+    half_p = t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, c5, c4), c3), c2), c1);
+    e = ex2_approx(a * a * kE);
+}
+__device__ __forceinline__ float gelu(float z) {
+    const float a = fabsf(z);
+    float hp, e;
+    gelu_parts(a, hp, e);
+    return fmaxf(z, 0.0f) - a * hp * e;
+}
 __device__ __forceinline__ float gelu_grad(float z) {
-    return 0.5f * (1.0f + erf_as(z * 0.70710678118654752f)) + z * 0.39894228040143268f * __expf(-0.5f * z * z);
+    float hp, e;
+    gelu_parts(fabsf(z), hp, e);
+    const float step = z >= 0.0f ? 1.0f : 0.0f;
+    return fmaf(e, fmaf(z, 0.39894228040143268f, -copysignf(hp, z)), step);
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
