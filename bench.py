@@ -225,7 +225,9 @@ def run_reference(args):
         return 0
     from oracle import oracle as orc
     nthreads = orc.default_threads()
-    rate, _ = oracle_mlups(64, 1, nthreads)
+    # calibration on a 512-row band: large enough (~0.7 GB of populations) to run at the
+    # memory-bound rate of the full lattice rather than from the caches
+    rate, _ = oracle_mlups(512, 1, nthreads)
     per_step = 150.0 / max(1, args.steps + args.warmup)
     rows = int(max(16, min(LY, rate * 1e6 * per_step / LX)))
     from paper_1804_01918_gb300 import inputs
