@@ -627,8 +627,25 @@ def measure_learned(lb, torch, np, inputs, st, stream, fp32split_mlups, epochs=2
     lat.close()
     mlups = sites * steps / (ms * 1e-3) / 1e6
     kept = 1.0 - stats["tiles_fallback"] / max(1, stats["tiles_checked"])
+    # the same network with the check amortised over 10 steps (tiles keep their last decision in
+    # between): what the learned collide costs when it does not also run the plain one every step
+    lat = lb.Lattice.from_fields(st, tau=TAU, stream=stream, precision="fp32split")
+    lat.set_collide_learned(net, bound=1e-4, check_every=10)
+    lat.step(10)
+    lat.sync()
+    e0.record(stream)
+    lat.step(steps)
+    e1.record(stream)
+    e1.synchronize()
+    ms10 = e0.elapsed_time(e1)
+    lat.sync()
+    stats10 = lat.learned_stats()
+    lat.close()
+    kept10 = 1.0 - stats10["tiles_fallback"] / max(1, stats10["tiles_checked"])
     out = {"mlups": round(mlups, 1), "speedup_vs_fp32split": round(mlups / fp32split_mlups, 3),
            "tiles_kept_learned": round(kept, 4), "max_tile_residual": stats["max_residual"],
+           "mlups_check_every_10": round(sites * steps / (ms10 * 1e-3) / 1e6, 1),
+           "tiles_kept_learned_check_every_10": round(kept10, 4),
            "bound": 1e-4, "check_every": 1, "train_pairs": npairs, "epochs": epochs,
            "final_loss": float(losses[-1]), "first_epoch_loss": float(losses[0]),
            "train_s": round(t_train, 1), "pair_generation_s": round(t_data, 1),
