@@ -115,7 +115,8 @@ def test_density_is_the_correctly_rounded_sum(L):
     nearest, ties to even): the moment sums are exact fixed-point sums, rounded on the integer
     pipe. Populations of mixed sign and magnitude in [2^-28, 16), including sites whose exact sum
     needs many more than 53 bits, and dyadic sites whose sums land on rounding ties. A site whose
-    populations are symmetric under c -> -c has zero momentum exactly."""
+    populations are symmetric under c -> -c has zero momentum exactly, and sites with rho = 1
+    exactly and dyadic populations of either sign give u = r sum f c with a single rounding."""
     from fractions import Fraction
     Lx, Ly = 24, 10
     rng = np.random.default_rng(17)
@@ -135,6 +136,12 @@ def test_density_is_the_correctly_rounded_sum(L):
     half = w[1:19, None] * (1.0 + 0.2 * rng.uniform(-1, 1, (18, Lx)))
     f[1:19, 6] = half
     f[19:37, 6] = half
+    # rows 7-8: dyadic populations of either sign with rho = 1 exactly, so that u = r sum f c is
+    # one rounding of an exact value: checks the signed rounding of the momentum sums
+    wq = np.round(w[1:] * 2.0**24)[:, None, None]
+    k = rng.integers(-2**18, 2**18, (36, 2, Lx)).astype(np.float64)
+    f[1:, 7:9] = (wq + k) * 2.0**-24
+    f[0, 7:9] = 1.0 - f[1:, 7:9].sum(axis=0)  # exact: every term is a multiple of 2^-24 below 1
     lat = L.Lattice(Lx, Ly, 0.9, np.ones((Ly, Lx)), np.zeros((Ly, Lx)), np.zeros((Ly, Lx)),
                     np.ones((Ly, Lx)))
     lat.set_populations(f)
@@ -144,6 +151,11 @@ def test_density_is_the_correctly_rounded_sum(L):
             exact = sum((Fraction(float(v)) for v in f[:, y, x]), Fraction(0))
             assert rho[y, x] == float(exact), (y, x, rho[y, x], float(exact))
     assert np.all(ux[6] == 0.0) and np.all(uy[6] == 0.0)
+    _, _, _, r = L.velocity_set()
+    assert np.all(rho[7:9] == 1.0)
+    jx = np.einsum("i,iyx->yx", cx.astype(np.float64), f[:, 7:9])  # exact dyadic sums
+    jy = np.einsum("i,iyx->yx", cy.astype(np.float64), f[:, 7:9])
+    assert np.array_equal(ux[7:9], r * jx) and np.array_equal(uy[7:9], r * jy)
 
 
 def test_graph_replay_equals_single_launches(L):
