@@ -90,6 +90,9 @@ double thermal_scale() {
     return 1.0 / std::sqrt(m2);
 }
 
+// StepParams is passed by value as a kernel parameter: it must fit the classic 4 KB parameter space.
+static_assert(sizeof(StepParams) <= 4096, "StepParams must fit the 4 KB kernel parameter space");
+
 void fill_step_params(const lb_params& p, StepParams& sp) {
     std::memset(&sp, 0, sizeof sp);
     sp.Lx = p.Lx;
