@@ -66,10 +66,10 @@ TRAFFIC_FP64 = {"bytes_per_site": (698.432000e6 + 645.569024e6) / 2359296,
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
-# (profiles/step_fp32split_1152x2048_full.md), 349.252 MB + 303.333 MB for 2359296 sites.
-TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.251840e6 + 303.333376e6) / 2359296,
+# (profiles/step_fp32split_1152x2048_full.md), 349.250 MB + 302.968 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.249536e6 + 302.968064e6) / 2359296,
                      "sources": {"step_fp32dev.cu": "f7bea2d3cbbe2d04fe483e7128f764fa264de6526fc29eb26adead235e1bd8fd",
-                                 "site_fp32dev.cuh": "7b5c71ad25c7fa5eb6656114b7d77d377549e5e43d55abbd6f7d4ecbc1aab053",
+                                 "site_fp32dev.cuh": "79880d772491419efb29321c41a5b6a76327c14b3b56f0c7ebe0d37a2d56afa7",
                                  "d2q37_gpu.cuh": "0f71f64285f06f1024691ff1c9d798f37322e5fbb083f045a19e27cc35a755e2"}}
 
 

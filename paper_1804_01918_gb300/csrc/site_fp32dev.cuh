@@ -51,6 +51,23 @@ __device__ __forceinline__ bool bad_positive64(double v) {
     return (b - 1ull) >= 0x7FEFFFFFFFFFFFFFull;
 }
 
+// The FP64 value of an FP32 number, assembled on the integer pipe (the conversion instruction
+// issues on GB300's narrow FP64 pipe, twice per population and step here): sign kept, exponent
+// rebiased by 1023 - 127, significand shifted into place; a subnormal input is normalised by a
+// leading-zero count. Exact, as the conversion is (every FP32 value is an FP64 value); infinities
+// and NaN map to infinities and NaN.
+__device__ __forceinline__ double exact_double(float f) {
+    const unsigned b = __float_as_uint(f);
+    const unsigned e = (b >> 23) & 0xFFu;
+    const unsigned m = b & 0x7FFFFFu;
+    const unsigned lz = __clz(m | 1u) - 8u;  // brings a subnormal's leading one to bit 23
+    const bool sub = e == 0u;
+    const unsigned mm = sub ? (m << lz) & 0x7FFFFFu : m;
+    const unsigned E = e == 0xFFu ? 0x7FFu : (sub ? (m == 0u ? 0u : 897u - lz) : e + 896u);
+    const unsigned hi = (b & 0x80000000u) | (E << 20) | (mm >> 3);
+    return __hiloint2double((int)hi, (int)(mm << 29));
+}
+
 // FP64 sums of FP32 deviations: s0 = sum d, sx = sum d c_x, sy = sum d c_y, se = sum d |c|^2.
 struct DevSums {
     double s0, sx, sy, se;
@@ -65,7 +82,7 @@ __device__ __forceinline__ DevSums dev_sums(const float* d) {
     }
 #pragma unroll
     for (int i = 0; i < NPOP; ++i) {
-        const double v = (double)d[i];
+        const double v = exact_double(d[i]);
         bx[cx_of(i) + 3] += v;
         by[cy_of(i) + 3] += v;
     }
