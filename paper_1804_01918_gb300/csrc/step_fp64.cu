@@ -134,7 +134,7 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
 //   - the shell coefficients grouped by powers of xi^2 (D = 2, h = theta / 2, m = 1/2 - |u*|^2 / 4):
 //       A0 = 2 m^2 + 1/2 + 2h (1 - 4m + 2h) + xi^2 h (2m - 4h) + xi^4 h^2 / 2,
 //       A2 = m - 3h + xi^2 h / 2,  B1 = 2m - 4h + xi^2 h,
-//     so that each shell costs 8 operations on site values shared by all shells;
+//     so that each shell costs 7-9 operations on site values shared by all shells (ShellRelax);
 //   - b from U1 = lambda r u*_x and V1 = lambda r u*_y: for the shells (2,0), (2,2) and (3,0) the
 //     pair variable is kappa beta with kappa = 2, 2, 3 and beta = U1, V1 or U1 +- V1, whose squares
 //     are already at hand, and the powers of kappa are folded into that shell's constants
@@ -172,12 +172,15 @@ __device__ __forceinline__ void relax_site_terms(const StepParams& P, const Site
     R.Ra2 = R.Rb - R.t;                                // rw (m - 3h)
     R.P1 = R.t * bq;
     R.P2 = R.t * h;
-    R.R0h = fma(R.t, fma(h, 2.0, fma(m, -4.0, 1.0)), R.rw * fma(m, m, 0.25));
+    // rw A0(xi = 0) / 2 = rw (2 m^2 + 1/2 + 2h (1 - 4m + 2h)) / 2 = rw / 4 + t + Rb bq - 2 P2
+    R.R0h = fma(-2.0, R.P2, fma(R.Rb, bq, fma(R.rw, 0.25, R.t)));
 }
 
-// The coefficients of shell S (S >= 1).
+// The coefficients of shell S (S >= 1). For kappa = 1, WA2 - WB1 = WB1 - 16 w t (from the
+// groupings of A2 and B1), so the shell keeps DA = WA2 - WB1 (one FMA) instead of WA2 (two), and a
+// pair forms WA2 + C b^2 as (WB1 + C b^2) + DA from the odd part's factor q.
 struct ShellRelax {
-    double WA0, WA2, WB1, CE, CO;
+    double WA0, WA2, WB1, CE, CO;  // WA2 holds DA for kappa = 1
 };
 
 template <int S>
@@ -185,8 +188,11 @@ __device__ __forceinline__ ShellRelax shell_relax(const StepParams& P, const Rel
     const ShellCoef& c = P.sh[S];
     ShellRelax q;
     q.WA0 = fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h));
-    q.WA2 = fma(c.q_e1, R.t, c.q_e0 * R.Ra2);
     q.WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);
+    if constexpr (shell_kappa(S) == 1)
+        q.WA2 = fma(-c.q_e0, R.t, q.WB1);  // DA: q_e0 = 16 w for kappa = 1
+    else
+        q.WA2 = fma(c.q_e1, R.t, c.q_e0 * R.Ra2);
     q.CE = c.q_c * R.rw;
     q.CO = shell_kappa(S) == 1 ? q.CE : c.q_co * R.rw;
     return q;
@@ -221,8 +227,13 @@ __device__ __forceinline__ void relax_pair(const double* f, const Relax64& R, co
                                            double omc, Store& store) {
     double b, b2;
     pair_base<I>(R, b, b2);
-    const double we = fma(b2, fma(b2, c.CE, c.WA2), c.WA0);
     const double q = fma(b2, c.CO, c.WB1);
+    double e2;  // WA2 + C b^2
+    if constexpr (shell_kappa(shellh(I)) == 1)
+        e2 = q + c.WA2;
+    else
+        e2 = fma(b2, c.CE, c.WA2);
+    const double we = fma(b2, e2, c.WA0);
     store(I, fma(omc, f[I], fma(b, q, we)));
     store(I + NPAIR, fma(omc, f[I + NPAIR], fma(-b, q, we)));
 }
