@@ -75,11 +75,10 @@ __host__ __device__ constexpr int shell_of(int i) { return i <= NPAIR ? shellh(i
 struct ShellCoef {
     double w, alpha, beta, gamma, delta, eps;
     // constants of the FP64 step's relaxation (step_fp64.cu, shell_relax), X = xi^2 and
-    // k = shell_kappa: W A0 = q_a0 R0 + q_a1 P1 + q_a2 P2, 16 k^2 W A2 = q_e0 Ra + q_e1 t,
-    // 4 k W B1 = q_b0 Rb + q_b1 t, k^4 C = q_c rho / tau, k^3 C = q_co rho / tau, with q_a0 = 2w,
-    // q_a1 = 2wX, q_a2 = wX^2/2, q_e0 = 16 k^2 w, q_e1 = 8 k^2 wX, q_b0 = 8 k w, q_b1 = 4 k wX,
-    // q_c = 32 k^4 w/3, q_co = 32 k^3 w/3
-    double q_a0, q_a1, q_a2, q_e0, q_e1, q_b0, q_b1, q_c, q_co;
+    // k = shell_kappa: W A0 = q_a0 R0 + q_a1 P1 + q_a2 P2, 4 k W B1 = q_b0 Rb + q_b1 t,
+    // 16 k^2 W (A2 - B1 / 4) = k (4 k W B1) - q_e0 t, k^3 C = q_co rho / tau, with q_a0 = 2w,
+    // q_a1 = 2wX, q_a2 = wX^2/2, q_b0 = 8 k w, q_b1 = 4 k wX, q_e0 = 16 k^2 w, q_co = 32 k^3 w/3
+    double q_a0, q_a1, q_a2, q_b0, q_b1, q_e0, q_co;
 };
 
 // FP32 copies of the shell coefficients for the FP32 kernels (converting doubles on the device

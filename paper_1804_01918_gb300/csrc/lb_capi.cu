@@ -131,11 +131,9 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         sp.sh[s].q_a0 = 2.0 * w;
         sp.sh[s].q_a1 = 2.0 * w * X;
         sp.sh[s].q_a2 = 0.5 * w * X * X;
-        sp.sh[s].q_e0 = 16.0 * k * k * w;
-        sp.sh[s].q_e1 = 8.0 * k * k * w * X;
         sp.sh[s].q_b0 = 8.0 * k * w;
         sp.sh[s].q_b1 = 4.0 * k * w * X;
-        sp.sh[s].q_c = 32.0 * k * k * k * k * w / 3.0;
+        sp.sh[s].q_e0 = 16.0 * k * k * w;
         sp.sh[s].q_co = 32.0 * k * k * k * w / 3.0;
     }
     constexpr double lambda = 0.25;

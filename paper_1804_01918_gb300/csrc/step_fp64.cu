@@ -145,7 +145,7 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
 struct Relax64 {
     double U1, V1, U1s, V1s;  // lambda r u*_x, lambda r u*_y and their squares
     double B11[2], S11[2];    // beta and beta^2 of the pairs (1, 1) and (1, -1)
-    double rw, t, Rb, Ra2, P1, P2, R0h;  // site terms of the shell coefficients
+    double rw, t, Rb, P1, P2, R0h;  // site terms of the shell coefficients
     double X;                 // temperature_sum: T = r^2 X / (2 n0) before the forcing shift
 };
 
@@ -169,18 +169,19 @@ __device__ __forceinline__ void relax_site_terms(const StepParams& P, const Site
     R.t = R.rw * h;
     const double bq = fma(h, -2.0, m);                 // m - 2h
     R.Rb = R.rw * bq;
-    R.Ra2 = R.Rb - R.t;                                // rw (m - 3h)
     R.P1 = R.t * bq;
     R.P2 = R.t * h;
     // rw A0(xi = 0) / 2 = rw (2 m^2 + 1/2 + 2h (1 - 4m + 2h)) / 2 = rw / 4 + t + Rb bq - 2 P2
     R.R0h = fma(-2.0, R.P2, fma(R.Rb, bq, fma(R.rw, 0.25, R.t)));
 }
 
-// The coefficients of shell S (S >= 1). For kappa = 1, WA2 - WB1 = WB1 - 16 w t (from the
-// groupings of A2 and B1), so the shell keeps DA = WA2 - WB1 (one FMA) instead of WA2 (two), and a
-// pair forms WA2 + C b^2 as (WB1 + C b^2) + DA from the odd part's factor q.
+// The coefficients of shell S (S >= 1). The groupings of A2 and B1 give WA2 - WB1 = WB1 - 16 w t,
+// so a pair forms its even factor from the odd one: with k = kappa and the shell's scaled
+// constants (k WB1, k^2 WA2, k^3 C, k^4 C),
+//   k^2 WA2 + k^4 C beta^2 = k q + DA,  q = k WB1 + k^3 C beta^2,  DA = k^2 (WA2 - WB1),
+// and the shell keeps DA (one or two operations) instead of WA2 (two) and k^4 C (one).
 struct ShellRelax {
-    double WA0, WA2, WB1, CE, CO;  // WA2 holds DA for kappa = 1
+    double WA0, DA, WB1, CO;  // CO = k^3 C
 };
 
 template <int S>
@@ -188,13 +189,10 @@ __device__ __forceinline__ ShellRelax shell_relax(const StepParams& P, const Rel
     const ShellCoef& c = P.sh[S];
     ShellRelax q;
     q.WA0 = fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h));
-    q.WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);
-    if constexpr (shell_kappa(S) == 1)
-        q.WA2 = fma(-c.q_e0, R.t, q.WB1);  // DA: q_e0 = 16 w for kappa = 1
-    else
-        q.WA2 = fma(c.q_e1, R.t, c.q_e0 * R.Ra2);
-    q.CE = c.q_c * R.rw;
-    q.CO = shell_kappa(S) == 1 ? q.CE : c.q_co * R.rw;
+    q.WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);                       // k WB1
+    constexpr double k = shell_kappa(S);
+    q.DA = fma(-c.q_e0, R.t, k == 1.0 ? q.WB1 : k * q.WB1);        // q_e0 = 16 k^2 w
+    q.CO = c.q_co * R.rw;
     return q;
 }
 
@@ -228,11 +226,8 @@ __device__ __forceinline__ void relax_pair(const double* f, const Relax64& R, co
     double b, b2;
     pair_base<I>(R, b, b2);
     const double q = fma(b2, c.CO, c.WB1);
-    double e2;  // WA2 + C b^2
-    if constexpr (shell_kappa(shellh(I)) == 1)
-        e2 = q + c.WA2;
-    else
-        e2 = fma(b2, c.CE, c.WA2);
+    constexpr double k = shell_kappa(shellh(I));
+    const double e2 = k == 1.0 ? q + c.DA : fma(k, q, c.DA);  // k^2 WA2 + k^4 C beta^2
     const double we = fma(b2, e2, c.WA0);
     store(I, fma(omc, f[I], fma(b, q, we)));
     store(I + NPAIR, fma(omc, f[I + NPAIR], fma(-b, q, we)));
