@@ -36,19 +36,19 @@ if ROOT not in sys.path:
 
 LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
 NPOP = 37
-# FP64 work of the fused step per site in this kernel's formulation: 225 FP64-pipe instructions
-# (166 FMA + 42 mul + 17 add; ncu's opcode counters on step_fp64_kernel, per site), i.e. 391 flops
+# FP64 work of the fused step per site in this kernel's formulation: 224 FP64-pipe instructions
+# (165 FMA + 42 mul + 17 add; ncu's opcode counters on step_fp64_kernel, per site), i.e. 389 flops
 # with FMA = 2. The moment sums run as exact 96-bit integer sums on the integer pipe, rounded to
 # FP64 there too. The FP64 pipe issues one such instruction per lane-slot whatever its kind, so the
 # ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per SM x f_max (the 1.25 TFLOP/s
 # nominal FP64 rate counts an FMA as 2 flops).
-FP64_INST_PER_SITE = 225
-FP64_FLOP_PER_SITE = 391
+FP64_INST_PER_SITE = 224
+FP64_FLOP_PER_SITE = 389
 # The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
 # equilibrium written per population, BGK relaxation with the gravity shift): 2763 flops, counted
 # by compiling the oracle's collide with an operation-counting scalar type
 # (oracle/count_collide_flops.cpp; tests/test_oracle_flops.py re-derives the number). The
-# kernel's factored formulation needs 391 of them in FP64.
+# kernel's factored formulation needs 389 of them in FP64.
 ORACLE_FLOP_PER_SITE = 2763
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
@@ -57,10 +57,10 @@ FP64_INST_PER_CLK_SM = 2
 SM_MAX_MHZ = 2070.0
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 698.476 MB + 645.840 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# 698.450 MB + 646.185 MB for 2359296 sites, scaled per site. Valid only for the kernel source
 # it was taken on (sha256 of the files below); otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (698.475776e6 + 645.840128e6) / 2359296,
-                "sources": {"step_fp64.cu": "0e47e02e4b15b89b13b499c2297e5c880a21ad99a1f8dcff65f7515b3d62e21a",
+TRAFFIC_FP64 = {"bytes_per_site": (698.449664e6 + 646.185216e6) / 2359296,
+                "sources": {"step_fp64.cu": "c64dd8d7c031103b33ccdd78c5668d01e4809fc55e96135db120ec5bc51c95cb",
                             "d2q37_gpu.cuh": "908a3a2cb3bb6d90edeb309568b1235dbabc2f724c7c0196dab23c67a2c1f3ec",
                             "fixed96.cuh": "bd085b595db76f18b25d2d7f06cb732c39e23c93f51134251d4befa1ba86a55e"}}
 
@@ -657,7 +657,7 @@ def measure_table1(lb, torch, np, inputs, reps=20):
     """The paper's per-kernel metrics (Table 1) on GB300 at its 1024 x 8192 lattice, FP64:
     separate propagate and collide kernels timed launch by launch (CUDA events), propagate GB/s
     with 592 B per site, collide MLUPS and GF/s (with the paper's ~6600 flop/site, as Table 1
-    derives it, and with this kernel's 391), and Global MLUPS of the two-kernel step and of the
+    derives it, and with this kernel's 389), and Global MLUPS of the two-kernel step and of the
     fused step."""
     Lx, Ly = 1024, 8192
     sites = Lx * Ly
@@ -693,7 +693,7 @@ def measure_table1(lb, torch, np, inputs, reps=20):
             "propagate_GBs": round(FP64_BYTES_PER_SITE * sites / (t_prop * 1e-3) / 1e9, 1),
             "collide_MLUPS": round(coll_mlups, 1),
             "collide_GFs_at_6600_flop_per_site": round(coll_mlups * 6600 / 1e3, 1),
-            "collide_GFs_at_391_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
+            "collide_GFs_at_389_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
             "global_MLUPS_two_kernel": round(sites / ((t_prop + t_coll) * 1e-3) / 1e6, 1),
             "global_MLUPS_fused": round(sites / (t_fused * 1e-3) / 1e6, 1),
             "paper_KNL_7230_flat": {"T_prop_ms": 12.5, "T_coll_ms": 50.3, "propagate_GBs": 398,

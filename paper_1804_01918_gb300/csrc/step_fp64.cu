@@ -149,6 +149,17 @@ struct Relax64 {
     double X;                 // temperature_sum: T = r^2 X / (2 n0) before the forcing shift
 };
 
+// 1 / x for a positive normal x (the site's n0, a density times 2^48): the hardware approximation
+// (rcp.approx.ftz.f64, exact in its leading ~20 bits) refined by two Newton-Raphson steps
+// y <- y + y (1 - x y), each of which squares the relative error, so the result is within about
+// one ulp of 1 / x. Non-positive or non-finite x are flagged by the caller and the value unused.
+__device__ __forceinline__ double recip_nr(double x) {
+    double y;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    y = fma(y, fma(-x, y, 1.0), y);
+    return fma(y, fma(-x, y, 1.0), y);
+}
+
 // X and a = 1 / n0 of the sums (the temperature is T = r^2 a X / 2), computed first so that the
 // caller can check them before the coefficients.
 __device__ __forceinline__ double temperature_sum(const SiteSums& s, double a) {
@@ -285,7 +296,7 @@ __device__ __forceinline__ void collide_site(const double* f, const StepParams& 
                                              int* __restrict__ flag, Store&& store) {
     int bad;
     const SiteSums s = site_sums(f, &bad);
-    const double a = 1.0 / s.n0;
+    const double a = recip_nr(s.n0);
     Relax64 R;
     R.X = temperature_sum(s, a);
     if (bad_positive(s.n0) || bad_positive(R.X) || bad) atomicOr(flag, bad ? bad : 1);
