@@ -58,29 +58,40 @@ SM_MAX_MHZ = 2070.0
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
 # 698.450 MB + 646.185 MB for 2359296 sites, scaled per site. Valid only for the kernel source
-# it was taken on (sha256 of the files below); otherwise reported as null.
+# it was taken on (code_digest of the files below: sha256 of the code without comments);
+# otherwise reported as null.
 TRAFFIC_FP64 = {"bytes_per_site": (698.449664e6 + 646.185216e6) / 2359296,
-                "sources": {"step_fp64.cu": "c64dd8d7c031103b33ccdd78c5668d01e4809fc55e96135db120ec5bc51c95cb",
-                            "d2q37_gpu.cuh": "908a3a2cb3bb6d90edeb309568b1235dbabc2f724c7c0196dab23c67a2c1f3ec",
-                            "fixed96.cuh": "bd085b595db76f18b25d2d7f06cb732c39e23c93f51134251d4befa1ba86a55e"}}
+                "sources": {"step_fp64.cu": "53caed22cf06649ae7f7b05bba55e6e1f7f769ee6d1f22ec792ca42ca8654936",
+                            "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437",
+                            "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}}
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
 # (profiles/step_fp32split_1152x2048_full.md), 349.249 MB + 303.177 MB for 2359296 sites.
 TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.249280e6 + 303.177472e6) / 2359296,
-                     "sources": {"step_fp32dev.cu": "f7bea2d3cbbe2d04fe483e7128f764fa264de6526fc29eb26adead235e1bd8fd",
-                                 "site_fp32dev.cuh": "79880d772491419efb29321c41a5b6a76327c14b3b56f0c7ebe0d37a2d56afa7",
-                                 "d2q37_gpu.cuh": "908a3a2cb3bb6d90edeb309568b1235dbabc2f724c7c0196dab23c67a2c1f3ec"}}
+                     "sources": {"step_fp32dev.cu": "4524dfb55e07da66efe8f8c7a888a953c4869fc1e41e52e92c927577afb018a4",
+                                 "site_fp32dev.cuh": "fd45111f7e8b33d635222b860c17888a3e1857abc7898c0d1af8bd2ef0f12af3",
+                                 "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437"}}
+
+
+def code_digest(path):
+    """sha256 of a CUDA source with its comments and whitespace removed: the measured counters stay
+    valid across comment edits but not across any change of the code itself."""
+    import hashlib
+    import re
+    with open(path, encoding="utf-8") as fh:
+        text = fh.read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return hashlib.sha256(" ".join(text.split()).encode()).hexdigest()
 
 
 def sources_match(table):
-    import hashlib
     csrc = os.path.join(ROOT, "paper_1804_01918_gb300", "csrc")
     for name, digest in table["sources"].items():
         try:
-            with open(os.path.join(csrc, name), "rb") as fh:
-                if hashlib.sha256(fh.read()).hexdigest() != digest:
-                    return False
+            if code_digest(os.path.join(csrc, name)) != digest:
+                return False
         except OSError:
             return False
     return True
