@@ -60,8 +60,9 @@ typedef enum {
 
 typedef enum {
     LB_FP64 = 0,   /* populations stored and collided in FP64; the moment sums are accumulated
-                      exactly in 96-bit fixed point on the integer pipe and rounded to FP64 once
-                      (at least as accurate as FP64 summation; GB300's FP64 pipe binds the step) */
+                      exactly in 96-bit fixed point on the integer pipe and correctly rounded to
+                      FP64 once (at least as accurate as any FP64 summation order; GB300's FP64
+                      pipe binds the step) */
     LB_FP32DEV = 1,  /* populations stored as FP32 deviations f - w; FP32 collide, FP64 moment
                         accumulation and FP64 conservation projection */
     LB_FP32SPLIT = 2 /* same storage and FP32 collide; the moment sums and the projection residual
