@@ -67,9 +67,9 @@ TRAFFIC_FP64 = {"bytes_per_site": (698.449664e6 + 646.185216e6) / 2359296,
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
-# (profiles/step_fp32split_1152x2048_full.md), 349.249 MB + 303.177 MB for 2359296 sites.
-TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.249280e6 + 303.177472e6) / 2359296,
-                     "sources": {"step_fp32dev.cu": "4524dfb55e07da66efe8f8c7a888a953c4869fc1e41e52e92c927577afb018a4",
+# (profiles/step_fp32split_1152x2048_full.md), 349.322 MB + 302.927 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.322496e6 + 302.927104e6) / 2359296,
+                     "sources": {"step_fp32dev.cu": "c3851df7f987638f59aa4678fecd1aae308352d8e3fe108c25bfb87cb46c501a",
                                  "site_fp32dev.cuh": "fd45111f7e8b33d635222b860c17888a3e1857abc7898c0d1af8bd2ef0f12af3",
                                  "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437"}}
 

@@ -32,7 +32,7 @@ step_fp32dev_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
                     int* __restrict__ flag) {
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= P.Lx * P.Ly) return;
-    const int y = site / P.Lx;
+    const int y = row_of(site, P);
     fp32dev_site(src, dst, P, site - y * P.Lx, y, flag);
 }
 
@@ -41,7 +41,7 @@ step_fp32split_kernel(const float* __restrict__ src, float* __restrict__ dst, co
                       int* __restrict__ flag) {
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
     if (site >= P.Lx * P.Ly) return;
-    const int y = site / P.Lx;
+    const int y = row_of(site, P);
     fp32split_site(src, dst, P, P, site - y * P.Lx, y, flag);
 }
 
