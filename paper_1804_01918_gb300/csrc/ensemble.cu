@@ -2,8 +2,10 @@
 //
 // Device data: every member's two FP32-deviation population copies (same layout as a single
 // lattice), a member table (kernel parameters + buffer pointers), a global list of work items
-// (member, x0, y0) covering all members with tile_x x tile_y tiles, a host-exchange staging area
-// sized for the largest member, and a status word.
+// (member, x0, y0, log2 of the tile width) covering all members with tiles of tile_x x tile_y
+// sites -- narrowed to the widest power of two >= 32 that divides a member's Lx, and heightened to
+// keep the tile's site count, so that no tile overhangs a member's right edge -- a host-exchange
+// staging area sized for the largest member, and a status word.
 //
 // One launch of the step kernel covers every member: block b handles work items b, b + grid, ...
 // It is launched with one block per item (measured 6 % faster than a persistent grid of the
@@ -45,8 +47,8 @@ inline size_t align_up(size_t v) { return (v + ALIGN - 1) / ALIGN * ALIGN; }
 template <bool kSplit>
 __global__ void __launch_bounds__(ENS_BLOCK, kSplit ? 5 : 1)  // split: 20 warps per SM, <= 102 registers
 ensemble_step_kernel(const StepParams Pc, const MemberDesc* __restrict__ members,
-                     const int4* __restrict__ items, int nitems, int tx_log2, int tile_sites,
-                     int parity, int* __restrict__ flag) {
+                     const int4* __restrict__ items, int nitems, int tile_sites, int parity,
+                     int* __restrict__ flag) {
     __shared__ __align__(16) StepParams sP;
     __shared__ const float* s_src;
     __shared__ float* s_dst;
@@ -66,10 +68,10 @@ ensemble_step_kernel(const StepParams Pc, const MemberDesc* __restrict__ members
             __syncthreads();
             staged = it.x;
         }
-        const int xmask = (1 << tx_log2) - 1;
+        const int xmask = (1 << it.w) - 1;  // it.w: log2 of this item's tile width
         for (int k = threadIdx.x; k < tile_sites; k += ENS_BLOCK) {
             const int x = it.y + (k & xmask);
-            const int y = it.z + (k >> tx_log2);
+            const int y = it.z + (k >> it.w);
             if (x < sP.Lx && y < sP.Ly) {
                 if (kSplit)
                     fp32split_site<false>(s_src, s_dst, Pc, sP, x, y, flag);  // constants from Pc
@@ -107,9 +109,20 @@ std::vector<Candidate> candidates() {
     return out;
 }
 
+// The tile width used for a member of width Lx: the widest power of two in [32, tx] that divides
+// Lx (no partial tiles at the right edge), else tx; the height keeps tx * ty sites per tile.
+int member_tile_x(int Lx, int tx) {
+    for (int w = tx; w >= 32; w >>= 1)
+        if (Lx % w == 0) return w;
+    return tx;
+}
+
 long long count_items(const std::vector<lb_params>& m, int tx, int ty) {
     long long n = 0;
-    for (const auto& p : m) n += (long long)((p.Lx + tx - 1) / tx) * ((p.Ly + ty - 1) / ty);
+    for (const auto& p : m) {
+        const int w = member_tile_x(p.Lx, tx), h = tx * ty / w;
+        n += (long long)((p.Lx + w - 1) / w) * ((p.Ly + h - 1) / h);
+    }
     return n;
 }
 
@@ -210,8 +223,9 @@ lb_status upload_items(lb_ensemble* e, int tx, int ty) {
     items.reserve((size_t)count_items(e->params, tx, ty));
     for (int k = 0; k < (int)e->params.size(); ++k) {
         const lb_params& p = e->params[k];
-        for (int y0 = 0; y0 < p.Ly; y0 += ty)
-            for (int x0 = 0; x0 < p.Lx; x0 += tx) items.push_back(make_int4(k, x0, y0, 0));
+        const int w = member_tile_x(p.Lx, tx), h = tx * ty / w, wl = log2_exact(w);
+        for (int y0 = 0; y0 < p.Ly; y0 += h)
+            for (int x0 = 0; x0 < p.Lx; x0 += w) items.push_back(make_int4(k, x0, y0, wl));
     }
     if ((long long)items.size() > e->max_items) return LB_ERR_STATE;
     ENS_CUDA(cudaMemcpyAsync(e->d_items, items.data(), items.size() * sizeof(int4),
@@ -230,7 +244,6 @@ lb_status upload_items(lb_ensemble* e, int tx, int ty) {
 }
 
 cudaError_t launch_ensemble(lb_ensemble* e, int parity) {
-    const int txl = log2_exact(e->tile_x);
     // the lattice constants (r, shell coefficients) are the same for every member: they travel as
     // a kernel parameter (constant bank); each member's own values are staged in shared memory
     // one block per work item: measured 6 % faster than a persistent grid of the co-resident
@@ -238,10 +251,10 @@ cudaError_t launch_ensemble(lb_ensemble* e, int parity) {
     const int grid = std::max(1, e->nitems);
     if (e->precision == LB_FP32SPLIT)
         ensemble_step_kernel<true><<<grid, ENS_BLOCK, 0, e->stream>>>(
-            e->sp[0], e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
+            e->sp[0], e->d_members, e->d_items, e->nitems, e->tile_x * e->tile_y, parity, e->flag);
     else
         ensemble_step_kernel<false><<<grid, ENS_BLOCK, 0, e->stream>>>(
-            e->sp[0], e->d_members, e->d_items, e->nitems, txl, e->tile_x * e->tile_y, parity, e->flag);
+            e->sp[0], e->d_members, e->d_items, e->nitems, e->tile_x * e->tile_y, parity, e->flag);
     return cudaGetLastError();
 }
 
