@@ -28,7 +28,9 @@ extern "C" {
 typedef struct lb_ensemble lb_ensemble;
 
 typedef struct {
-    int tile_x, tile_y;  /* sites per work item; 0, 0 = 64 x 4 until lb_ensemble_autotune */
+    int tile_x, tile_y;  /* sites per work item; 0, 0 = 64 x 4 until lb_ensemble_autotune. A
+                            member whose Lx is not a multiple of tile_x gets tiles of the widest
+                            power of two >= 32 dividing its Lx (same site count), when there is one */
     int graph_steps;     /* steps per captured CUDA graph; even, 0 = 100 */
     int precision;       /* LB_FP32SPLIT (0 is read as this) or LB_FP32DEV */
     void* stream;        /* cudaStream_t or NULL (library-owned non-blocking stream) */
