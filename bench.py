@@ -704,7 +704,7 @@ def measure_table1(lb, torch, np, inputs, reps=20):
             "propagate_GBs": round(FP64_BYTES_PER_SITE * sites / (t_prop * 1e-3) / 1e9, 1),
             "collide_MLUPS": round(coll_mlups, 1),
             "collide_GFs_at_6600_flop_per_site": round(coll_mlups * 6600 / 1e3, 1),
-            "collide_GFs_at_389_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
+            f"collide_GFs_at_{FP64_FLOP_PER_SITE}_flop_per_site": round(coll_mlups * FP64_FLOP_PER_SITE / 1e3, 1),
             "global_MLUPS_two_kernel": round(sites / ((t_prop + t_coll) * 1e-3) / 1e6, 1),
             "global_MLUPS_fused": round(sites / (t_fused * 1e-3) / 1e6, 1),
             "paper_KNL_7230_flat": {"T_prop_ms": 12.5, "T_coll_ms": 50.3, "propagate_GBs": 398,
