@@ -35,6 +35,30 @@ FORMS = ["fp32dev", "fp32split"]
 
 
 @pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("tau", [0.55, 2.5])
+def test_fp32_forms_strong_flow_vs_fp64_oracle(L, orc, form, tau):
+    """The FP64 step's strong-flow regime (uncorrelated velocities to 0.15, densities 0.7-1.3,
+    temperatures 0.8-1.2, gravity 3e-3 on both axes): after 20 steps every population is within
+    20 x 16 FP32 ulps of a unit deviation, relative to its weight, of the FP64 oracle (each step
+    rounds every stored deviation once and the FP32 collide adds a few roundings more)."""
+    Lx, Ly, n = 40, 36, 20
+    st = inputs.random_state(Lx, Ly, seed=7, du=0.15, dT=0.2, drho=0.3)
+    lat = L.Lattice(Lx, Ly, tau, st.rho, st.ux, st.uy, st.T, gx=3e-3, gy=-3e-3, T_top=0.9,
+                    T_bottom=1.1, precision=form)
+    lat.step(n)
+    lat.sync()
+    cx, cy, _, _ = L.velocity_set()
+    got = orc.from_planes(lat.get_populations(), cx, cy)
+    lat.close()
+    want = orc.run(orc.init_fields(st), tau=tau, nsteps=n, gx=3e-3, gy=-3e-3, T_top=0.9,
+                   T_bottom=1.1)
+    _, _, w, _ = orc.velocity_set()
+    err = float(np.max(np.abs(got - want) / w))
+    print(f"{form} strong flow tau {tau}: max |f - f_oracle| / w = {err:.2e}")
+    assert err <= n * 16 * 2.0**-24
+
+
+@pytest.mark.parametrize("form", FORMS)
 def test_fp32dev_rayleigh_taylor_l2_error_vs_fp64_oracle(L, orc, form):
     Lx, Ly, steps = 64, 256, 100
     st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
