@@ -134,7 +134,7 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
 //   - the shell coefficients grouped by powers of xi^2 (D = 2, h = theta / 2, m = 1/2 - |u*|^2 / 4):
 //       A0 = 2 m^2 + 1/2 + 2h (1 - 4m + 2h) + xi^2 h (2m - 4h) + xi^4 h^2 / 2,
 //       A2 = m - 3h + xi^2 h / 2,  B1 = 2m - 4h + xi^2 h,
-//     so that each shell costs 7-9 operations on site values shared by all shells (ShellRelax);
+//     so that each shell costs 7-8 operations on site values shared by all shells (ShellRelax);
 //   - b from U1 = lambda r u*_x and V1 = lambda r u*_y: for the shells (2,0), (2,2) and (3,0) the
 //     pair variable is kappa beta with kappa = 2, 2, 3 and beta = U1, V1 or U1 +- V1, whose squares
 //     are already at hand, and the powers of kappa are folded into that shell's constants
