@@ -94,6 +94,13 @@ lb_status lb_set_collide_plain(lb_ctx* c);
  * tile residual seen. Synchronous. */
 lb_status lb_learned_stats(lb_ctx* c, long long* checked, long long* fallback, double* max_residual);
 
+/* The current decision of every 32 x 32-site tile (the per-tile fallback above): modes[t] = 1 if
+ * tile t (row-major over tiles, t = (y / 32) * (Lx / 32) + x / 32) was rewritten with the plain
+ * collide at its last check, 0 if it keeps the network's result. n must equal the number of
+ * tiles (LB_ERR_ARG otherwise); modes is caller-owned host memory. LB_ERR_STATE without a learned
+ * collide. Synchronous. */
+lb_status lb_learned_tiles(lb_ctx* c, unsigned char* modes, int n);
+
 #ifdef __cplusplus
 }
 #endif

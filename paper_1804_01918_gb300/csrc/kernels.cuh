@@ -76,6 +76,8 @@ cudaError_t launch_step_learned(const float* src, float* dst, const StepParams& 
                                 int* flag, cudaStream_t s);
 cudaError_t launch_pairs(const float* src, const StepParams& P, const int* sites, int n, float* pre,
                          float* post, int* flag, cudaStream_t s);
+// host copy of the per-tile decisions (1 = plain collide) of a learned state with ntiles tiles
+lb_status learned_tiles(LearnedState* ls, int ntiles, unsigned char* modes, cudaStream_t s);
 lb_status learned_stats(LearnedState* ls, long long* checked, long long* fallback, double* max_res,
                         cudaStream_t s);
 

@@ -686,6 +686,14 @@ lb_status lb_learned_stats(lb_ctx* c, long long* checked, long long* fallback, d
     return learned_stats(c->learned, checked, fallback, max_residual, c->stream);
 }
 
+lb_status lb_learned_tiles(lb_ctx* c, unsigned char* modes, int n) {
+    if (!c || !modes) return LB_ERR_ARG;
+    if (!c->learned) return LB_ERR_STATE;
+    const int ntiles = (c->p.Lx / 32) * (c->p.Ly / 32);
+    if (n != ntiles) return LB_ERR_ARG;
+    return learned_tiles(c->learned, ntiles, modes, c->stream);
+}
+
 lb_status lb_steps_done(const lb_ctx* c, long long* n) {
     if (!c || !n) return LB_ERR_ARG;
     *n = c->steps;

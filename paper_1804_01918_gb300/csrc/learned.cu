@@ -35,7 +35,7 @@ using namespace lbg::mlp;
 namespace lbg {
 namespace learn {
 
-constexpr uint32_t WAIT_LIMIT = 1u << 22;  // bounded mbarrier waits
+constexpr uint64_t WAIT_LIMIT = tc::WAIT_LIMIT_NS;  // bounded mbarrier waits (time)
 constexpr int ERR_TIMEOUT = 8;             // status-word bit: a tensor-core wait gave up
 
 // Device view of a network: FP32 master parameters (for biases), BF16 operand images of the
@@ -374,8 +374,10 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     }
     tc::fence_before_sync();
     __syncthreads();
+    // TMEM must be released before the block exits; the barrier is invalidated only when no
+    // product can still be pending on it (a wait that gave up leaves it alone)
     if (warp == 0) tc::tmem_dealloc(tm, 512);
-    if (tid == 0) tc::mbar_inval(bar);
+    if (tid == 0 && ok) tc::mbar_inval(bar);
 }
 
 // Sum the per-tile gradient partials, take an Adam step on the FP32 master parameters and
@@ -519,11 +521,13 @@ __device__ __forceinline__ void fwd_setup(FwdCtx& f, const NetDev& net, char* sm
     f.ph = 0;
 }
 
-__device__ __forceinline__ void fwd_teardown(FwdCtx& f) {
+// ok = false after a wait that gave up: the barrier is then left alone, since a product may still
+// be pending on it (TMEM must be released before the block exits either way).
+__device__ __forceinline__ void fwd_teardown(FwdCtx& f, bool ok = true) {
     tc::fence_before_sync();
     __syncthreads();
     if (f.warp == 0) tc::tmem_dealloc(f.tm, 256);
-    if (f.tid == 0) tc::mbar_inval(f.bar);
+    if (f.tid == 0 && ok) tc::mbar_inval(f.bar);
 }
 
 // y[n][37] = network(x[n][37]) on normalised inputs; n a multiple of 128; persistent over tiles.
@@ -532,6 +536,7 @@ mlp_eval_kernel(NetDev net, const float* __restrict__ x, float* __restrict__ y, 
     extern __shared__ __align__(1024) char sm[];
     FwdCtx f;
     fwd_setup(f, net, sm);
+    bool ok = true;
     for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const long long row = (long long)t * TILE + f.tid;
         float xn[KIN];
@@ -544,12 +549,13 @@ mlp_eval_kernel(NetDev net, const float* __restrict__ x, float* __restrict__ y, 
         float out[NOUT];
         if (!mlp_forward_tile(f, net, out)) {
             if (f.tid == 0) atomicOr(flag, ERR_TIMEOUT);
+            ok = false;
             break;
         }
 #pragma unroll
         for (int j = 0; j < NOUT; ++j) y[row * NOUT + j] = out[j];
     }
-    fwd_teardown(f);
+    fwd_teardown(f, ok);
 }
 
 // The learned LB step (see the file header). Lx and Ly are multiples of 32.
@@ -637,7 +643,7 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
         }
     }
     if (!alive && f.tid == 0) atomicOr(flag, ERR_TIMEOUT);
-    fwd_teardown(f);
+    fwd_teardown(f, alive);
 }
 
 // ---- FP32 debug mode of the loss and gradient ------------------------------------------------
@@ -1182,6 +1188,12 @@ cudaError_t launch_pairs(const float* src, const StepParams& P, const int* sites
                          int* flag, cudaStream_t s) {
     pairs_kernel<<<(n + 127) / 128, 128, 0, s>>>(src, P, sites, n, pre, post, flag);
     return cudaGetLastError();
+}
+
+lb_status learned_tiles(LearnedState* ls, int ntiles, unsigned char* modes, cudaStream_t s) {
+    L_CUDA(cudaMemcpyAsync(modes, ls->tile_mode, (size_t)ntiles, cudaMemcpyDeviceToHost, s));
+    L_CUDA(cudaStreamSynchronize(s));
+    return LB_OK;
 }
 
 lb_status learned_stats(LearnedState* ls, long long* checked, long long* fallback, double* max_res,

@@ -176,3 +176,29 @@ def rayleigh_taylor_splitmix(Lx: int, Ly: int, R: float = 2.0, seed: int = 0) ->
     zero = np.zeros((Ly, Lx), dtype=np.float64)
     return RTFields(rho=np.ascontiguousarray(rho), ux=zero.copy(), uy=zero.copy(),
                     T=np.ascontiguousarray(T), T_top=T_top, T_bottom=T_bottom, gy=-g)
+
+
+# ---- seeded network parameters for the learned collide's tests --------------------------------
+# Packed like the library's network (W1[128][37] b1[128] W2[128][128] b2[128] W3[37][128] b3[37]);
+# plain random numbers, no lattice-Boltzmann arithmetic.
+MLP_SIZES = [(128, 37), (128,), (128, 128), (128,), (37, 128), (37,)]
+MLP_FAN_IN = [37, 37, 128, 128, 128, 128]
+
+
+def mlp_params(seed: int = 0, scale: float = 1.0) -> np.ndarray:
+    """float32 parameters, each uniform in +-scale / sqrt(fan_in) (PCG64 seeded with ``seed``)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    parts = [rng.uniform(-1.0, 1.0, shape) * (scale / np.sqrt(fan))
+             for shape, fan in zip(MLP_SIZES, MLP_FAN_IN)]
+    return np.concatenate([p.ravel() for p in parts]).astype(np.float32)
+
+
+def mlp_norm(unit, seed: int = 0, mu_x: float = 0.02, sd_x: float = 0.05, mu_t: float = 1e-6,
+             sd_t: float = 1e-5) -> np.ndarray:
+    """float32 normalisation [4][37] (input mean and standard deviation, target mean and standard
+    deviation), each entry the given level times unit[i] times a seeded factor in [0.5, 1.5);
+    ``unit`` (37 values, in the network's population order) sets each population's scale."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    unit = np.asarray(unit, dtype=np.float64)
+    levels = np.array([mu_x, sd_x, mu_t, sd_t])[:, None]
+    return (levels * unit[None, :] * (0.5 + rng.random((4, 37)))).astype(np.float32)

@@ -2,8 +2,9 @@
 
 The network's products run on tcgen05 tensor cores with BF16 operands and FP32 accumulation; the
 oracle mirrors the BF16 rounding points in FP64, so remaining differences come from FP32 vs FP64
-accumulation, FP32 GELU and rare BF16 rounding flips of hidden activations: the bar is 1e-2
-relative per output or gradient block.
+accumulation, FP32 GELU and rare BF16 rounding flips of hidden activations: the bar is 1e-2 of
+the largest output, and 1e-2 of the largest entry of a parameter block for every gradient entry.
+Network parameters come from the seeded generator shared with the oracle (inputs.mlp_params).
 """
 import numpy as np
 import pytest
@@ -35,7 +36,7 @@ def dev(a):
 def test_forward_matches_oracle(L):
     import torch
     rng = np.random.default_rng(0)
-    p = omlp.init_params(3, scale=2.0).astype(np.float32)
+    p = inputs.mlp_params(3, scale=2.0)
     net = L.MLP(seed=0)
     net.set_params(p)
     x = rng.standard_normal((384, 37)).astype(np.float32)
@@ -50,9 +51,15 @@ def test_forward_matches_oracle(L):
     net.close()
 
 
+def entry_error(g, gref, a, b):
+    """max over the entries of a block of |g - g_ref| / max |g_ref| of that block."""
+    return float(np.max(np.abs(g[a:b] - gref[a:b])) / np.max(np.abs(gref[a:b])))
+
+
 def test_gradients_match_oracle(L):
+    """Every gradient entry of the tensor-core path within 1e-2 of its block's largest entry."""
     rng = np.random.default_rng(1)
-    p = omlp.init_params(5, scale=2.0).astype(np.float32)
+    p = inputs.mlp_params(5, scale=2.0)
     net = L.MLP(seed=0)
     net.set_params(p)
     x = rng.standard_normal((256, 37)).astype(np.float32)
@@ -61,8 +68,9 @@ def test_gradients_match_oracle(L):
     lref, gref = omlp.loss_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64), bf16=True)
     assert loss == pytest.approx(lref, rel=1e-3)
     for name, a, b in BLOCKS:
-        rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
-        assert rel < 1e-2, (name, rel)
+        err = entry_error(g, gref, a, b)
+        print(f"{name}: max entry error {err:.2e} of the block's largest entry")
+        assert err < 1e-2, (name, err)
     net.close()
 
 
@@ -70,9 +78,10 @@ def test_gradients_match_oracle(L):
 def test_fp32_debug_gradients_match_fp64_oracle(L, n):
     """The FP32 debug mode (no BF16 rounding) against the FP64 oracle MLP without rounding: loss
     and every parameter block within 1e-6 relative -- a tight check of packing, loss scaling and
-    the backward formulas that the BF16 tensor-core path can only be held to 1e-2."""
+    the backward formulas that the BF16 tensor-core path can only be held to 1e-2. Every entry is
+    also held to 1e-5 of its block's largest entry."""
     rng = np.random.default_rng(7)
-    p = omlp.init_params(9, scale=2.0).astype(np.float32)
+    p = inputs.mlp_params(9, scale=2.0)
     net = L.MLP(seed=0)
     net.set_params(p)
     x = rng.standard_normal((n, 37)).astype(np.float32)
@@ -83,11 +92,12 @@ def test_fp32_debug_gradients_match_fp64_oracle(L, n):
     for name, a, b in BLOCKS:
         rel = np.linalg.norm(g[a:b] - gref[a:b]) / np.linalg.norm(gref[a:b])
         assert rel < 1e-6, (name, rel)
-    # and the tensor-core path agrees with the debug mode to its own (BF16) tolerance
+        assert entry_error(g, gref, a, b) < 1e-5, name
+    # and the tensor-core path agrees with the debug mode entry by entry to its own (BF16) bar
     if n % 128 == 0:
         loss_tc, g_tc = net.loss_grad(dev(x), dev(t))
         for name, a, b in BLOCKS:
-            assert np.linalg.norm(g_tc[a:b] - g[a:b]) / np.linalg.norm(g[a:b]) < 2e-2, name
+            assert entry_error(g_tc, g, a, b) < 2e-2, name
     net.close()
 
 
