@@ -26,6 +26,17 @@ extern "C" {
  * threads > 1024 or an unknown kind. */
 lb_status lb_probe_fma(int kind, void* stream, int blocks, int threads, int iters, void* out);
 
+/* Self-check of the failure path of the library's asynchronous waits (the paper has no
+ * counterpart). Every wait of the tensor-core and TMA kernels on a shared-memory barrier gives up
+ * after a time limit (2 s of the GPU's global timer), sets a status bit that the host reads and
+ * lets the kernel return, so a stuck operation never hangs the GPU. This call runs that wait
+ * alone in a one-thread kernel: with arrive = 0 on a barrier that nothing ever completes (no
+ * asynchronous operation targets it, so nothing is left in flight), with arrive = 1 on one the
+ * thread completes first. limit_ns: 1 .. 1e10. out: device memory of two unsigned 64-bit values,
+ * caller-owned: out[0] = 1 if the wait gave up (0 if it succeeded), out[1] = the nanoseconds it
+ * waited. Asynchronous on `stream`; LB_ERR_ARG for a NULL out or a limit out of range. */
+lb_status lb_probe_wait(unsigned long long limit_ns, int arrive, void* stream, unsigned long long* out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -1,9 +1,11 @@
 // probe.cu -- FMA-throughput probe (roofline denominator of the ALU-bound kernels).
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <cstdio>
 
 #include "../../include/lb_probe.h"
+#include "tc_helpers.cuh"
 
 namespace {
 
@@ -35,7 +37,32 @@ __global__ void fma_chains_varying_kernel(T* __restrict__ out, int iters, T m, T
     out[t] = ((x0 + x1) + (x2 + x3)) + ((x4 + x5) + (x6 + x7));
 }
 
+// The bounded-wait path of the library's tensor-core and TMA kernels, checked on its own: one
+// thread initialises an mbarrier expecting one arrival and waits on it with the library's bounded
+// wait. With arrive = 0 nothing ever arrives (no asynchronous operation targets the barrier, so
+// nothing is in flight when the wait gives up); with arrive = 1 the thread arrives first and the
+// wait succeeds at once. out[0] = 1 if the wait gave up, out[1] = nanoseconds it took.
+__global__ void wait_probe_kernel(unsigned long long limit_ns, int arrive, unsigned long long* out) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    lbg::tc::mbar_init(&bar, 1);
+    if (arrive) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(lbg::tc::smem_u32(&bar)) : "memory");
+    const uint64_t t0 = lbg::tc::globaltimer_ns();
+    const bool got = lbg::tc::mbar_wait_bounded(&bar, 0u, limit_ns);
+    const uint64_t t1 = lbg::tc::globaltimer_ns();
+    if (got) lbg::tc::mbar_inval(&bar);
+    out[0] = got ? 0ull : 1ull;
+    out[1] = t1 - t0;
+}
+
 }  // namespace
+
+extern "C" lb_status lb_probe_wait(unsigned long long limit_ns, int arrive, void* stream,
+                                   unsigned long long* out) {
+    if (!out || limit_ns == 0 || limit_ns > 10000000000ull || (arrive != 0 && arrive != 1)) return LB_ERR_ARG;
+    wait_probe_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(limit_ns, arrive, out);
+    return cudaGetLastError() == cudaSuccess ? LB_OK : LB_ERR_CUDA;
+}
 
 extern "C" lb_status lb_probe_fma(int kind, void* stream, int blocks, int threads, int iters,
                                   void* out) {

@@ -31,7 +31,7 @@ constexpr int BOX_FLOATS = BOXW * TY;        // 160 floats = 640 bytes per popul
 constexpr int STAGE_BYTES = NPOP * BOX_FLOATS * 4;
 constexpr int STAGES = 2;
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 64;
-constexpr uint32_t WAIT_LIMIT = 1u << 22;
+constexpr uint64_t WAIT_LIMIT = tc::WAIT_LIMIT_NS;
 constexpr int ERR_TIMEOUT = 8;
 
 __device__ __forceinline__ void arrive_expect_tx(uint64_t* mbar, uint32_t bytes) {
@@ -162,15 +162,17 @@ step_fp32split_tma_kernel(const __grid_constant__ CUtensorMap tsrc, const float*
             split_store(dst, P, x, y, d, sp, flag);
         }
     }
-    // drain: wait (bounded) for copies still in flight before the block's shared memory goes away
+    // drain: wait (bounded) for copies still in flight before the block's shared memory goes away;
+    // a stage whose copy did not arrive in time keeps its barrier valid (the copy may still land)
     __syncthreads();
     if (tid == 0) {
         for (int s = 0; s < STAGES; ++s) {
-            const int kk = k + s;  // the next uses of each stage, if they were issued
+            const int kk = k + s;  // the next use of each stage, if it was issued
             const int tt = blockIdx.x + kk * gridDim.x;
-            if (tt < ntiles) tc::mbar_wait_bounded(&full[kk % STAGES], (uint32_t)((kk / STAGES) & 1), WAIT_LIMIT);
+            const bool idle = tt >= ntiles ||
+                              tc::mbar_wait_bounded(&full[kk % STAGES], (uint32_t)((kk / STAGES) & 1), WAIT_LIMIT);
+            if (idle) tc::mbar_inval(&full[kk % STAGES]);
         }
-        for (int s = 0; s < STAGES; ++s) tc::mbar_inval(&full[s]);
     }
 }
 

@@ -133,13 +133,29 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
-// Bounded wait for the phase with the given parity: false after `limit` unsuccessful tries
-// (each try_wait itself suspends for a hardware-defined interval).
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, uint32_t limit) {
-    for (uint32_t k = 0; k < limit; ++k)
-        if (mbar_try_wait(mbar, parity)) return true;
-    return false;
+// The GPU's global nanosecond timer.
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
+
+// Bounded wait for the phase with the given parity: false once limit_ns nanoseconds of the global
+// timer have passed without that phase completing. A time limit, not a count of tries, so that a
+// slow but healthy wait on a busy GPU never gives up; only a wait that is truly stuck does. After
+// a false return an asynchronous operation may still be pending on the barrier: callers then leave
+// the barrier alone (no mbarrier.inval) and report the status.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* mbar, uint32_t parity, uint64_t limit_ns) {
+    const uint64_t t0 = globaltimer_ns();
+    for (;;) {
+        if (mbar_try_wait(mbar, parity)) return true;
+        if (globaltimer_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Wait limit of the library's kernels: a tensor-core product or a tile copy takes microseconds,
+// so two seconds without completion means it will not complete.
+constexpr uint64_t WAIT_LIMIT_NS = 2000000000ull;
 
 }  // namespace tc
 }  // namespace lbg
