@@ -211,7 +211,7 @@ void lb_free(lb_ctx* c);
  *       LB_ERR_ARG with the reason in lb_last_error().
  *   f:  device pointer to one population copy in the library layout: 37 planes of (Ly + 6) x Lx
  *       elements (3 halo rows each side, x fastest), double for LB_FP64 or FP32 deviations f - w
- *       for LB_FP32DEV. A context's workspace holds copy A at offset 0 and copy B right after it
+ *       for LB_FP32DEV and LB_FP32SPLIT. A context's workspace holds copy A at offset 0 and copy B right after it
  *       (offset rounded up to 256 bytes); the current copy is A after an even number of steps.
  *   rho, ux, uy, T: caller-owned host arrays [Ly][Lx] (any may be NULL).
  * Synchronous (returns after the host arrays are written). The first call on a device looks up

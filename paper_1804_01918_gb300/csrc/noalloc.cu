@@ -7,7 +7,6 @@
 // every process that loads the library, and the kernel is the same moments kernel.
 #include <cuda_runtime.h>
 
-#include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -50,12 +49,6 @@ cudaError_t scratch_address(double** out) {
     return cudaSuccess;
 }
 
-double thermal_scale_noalloc() {
-    double m2 = 0.0;
-    for (int i = 0; i < NPOP; ++i) m2 += shell_w(shell_of(i)) * (double)(cx_of(i) * cx_of(i));
-    return 1.0 / std::sqrt(m2);
-}
-
 }  // namespace
 
 extern "C" lb_status lb_moments_noalloc(const lb_params* p, const void* f, double* rho, double* ux,
@@ -82,13 +75,19 @@ extern "C" lb_status lb_moments_noalloc(const lb_params* p, const void* f, doubl
         set_last_error(msg);
         return LB_ERR_CUDA;
     }
+    // the kernel parameters of the context path (lattice constants, row reciprocal for the site's
+    // row); the fields this call ignores get neutral values so that nothing the caller left in
+    // them reaches the kernel
+    lb_params q;
+    std::memset(&q, 0, sizeof q);
+    q.Lx = p->Lx;
+    q.Ly = p->Ly;
+    q.tau = 1.0;
+    q.T_top = q.T_bottom = 1.0;
+    q.precision = p->precision;
+    q.wall_mode = LB_WALL_REST;
     StepParams sp;
-    std::memset(&sp, 0, sizeof sp);
-    sp.Lx = p->Lx;
-    sp.Ly = p->Ly;
-    sp.plane = (long long)p->Lx * ((long long)p->Ly + 2 * HALO);
-    sp.r = thermal_scale_noalloc();
-    sp.r2 = sp.r * sp.r;
+    fill_step_params(q, sp);
     cudaStream_t s = (cudaStream_t)p->stream;
     if (p->precision == LB_FP64)
         e = launch_moments_fp64((const double*)f, sp, scratch, scratch + n, scratch + 2 * n,

@@ -26,9 +26,10 @@ def L():
     return lb
 
 
-@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32dev", 1e-14)])
-def test_noalloc_moments_match_context_moments_two_calls(L, precision, tol):
-    Lx, Ly = 64, 256                      # 16384 sites, within the 65536-site capacity
+@pytest.mark.parametrize("Lx,Ly", [(64, 256), (256, 256)])   # 16384 sites; exactly the capacity
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-14), ("fp32dev", 1e-14), ("fp32split", 1e-14)])
+def test_noalloc_moments_match_context_moments_two_calls(L, precision, tol, Lx, Ly):
+    assert Lx * Ly <= 65536
     st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
     lat = L.Lattice.from_fields(st, tau=0.9, precision=precision)
     base = lat._ws.data_ptr()             # population copy A: workspace offset 0
