@@ -36,6 +36,9 @@ typedef struct {
     void* stream;        /* cudaStream_t or NULL (library-owned non-blocking stream) */
     void* workspace;     /* caller-owned device memory or NULL */
     size_t workspace_bytes;
+    int persistent;      /* 0: one block per work item (default, the faster launch); 1: a
+                            persistent grid of the co-resident blocks (occupancy x SMs), each
+                            walking the work list with stride grid. Same results either way. */
 } lb_ensemble_opts;
 
 /* Device bytes needed by n members (members[k].Lx, .Ly used). */
@@ -44,7 +47,9 @@ lb_status lb_ensemble_workspace_bytes(int n, const lb_params* members, const lb_
 
 /* Create an ensemble of n >= 1 members. members[k]: Lx, Ly, tau, gx, gy, T_top, T_bottom,
  * y_periodic of member k (its precision, stream and workspace fields are ignored; wall_mode must
- * be LB_WALL_REST -- the ensemble kernel is built with the rest closure only -- else LB_ERR_ARG).
+ * be LB_WALL_REST -- the ensemble kernel is built with the rest closure only -- else LB_ERR_ARG;
+ * as for lb_init, tau must be finite and > 0.5, the wall temperatures finite and > 0 and the
+ * gravity finite, else LB_ERR_ARG).
  * rho[k], ux[k],
  * uy[k], T[k]: host fields [Ly][Lx] float64 of member k. Populations start at equilibrium with
  * wall halos written. Synchronous. */

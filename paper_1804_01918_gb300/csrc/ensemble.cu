@@ -16,6 +16,8 @@
 // pull's row offsets (up to 3 rows) hit in L2.
 #include <cuda_runtime.h>
 
+#include <cmath>
+
 #include <algorithm>
 #include <cstdio>
 #include <cstring>
@@ -162,7 +164,8 @@ struct lb_ensemble {
     int graph_steps = 100;
     cudaGraphExec_t graph[2] = {nullptr, nullptr};
     bool graph_failed = false;
-    int grid = 0;
+    int grid = 0;         // co-resident blocks of the step kernel (persistent launch)
+    bool persistent = false;
     long long total_sites = 0;
 };
 
@@ -207,7 +210,12 @@ lb_status check_members(int n, const lb_params* m) {
         const lb_params& p = m[k];
         if (p.Lx < 4 || p.Ly < 4 || (long long)p.Lx * ((long long)p.Ly + 2 * HALO) >= (1ll << 31) - 1)
             return LB_ERR_ARG;
-        if (!(p.tau > 0.5) || !(p.T_top > 0.0) || !(p.T_bottom > 0.0)) return LB_ERR_ARG;
+        // the single-lattice checks: finite relaxation time above 1/2, finite positive wall
+        // temperatures, finite gravity
+        if (!(p.tau > 0.5) || !std::isfinite(p.tau)) return LB_ERR_ARG;
+        if (!(p.T_top > 0.0) || !(p.T_bottom > 0.0) || !std::isfinite(p.T_top) || !std::isfinite(p.T_bottom))
+            return LB_ERR_ARG;
+        if (!std::isfinite(p.gx) || !std::isfinite(p.gy)) return LB_ERR_ARG;
         if (p.wall_mode != LB_WALL_REST) return LB_ERR_ARG;  // members use the rest closure
     }
     return LB_OK;
@@ -246,9 +254,10 @@ lb_status upload_items(lb_ensemble* e, int tx, int ty) {
 cudaError_t launch_ensemble(lb_ensemble* e, int parity) {
     // the lattice constants (r, shell coefficients) are the same for every member: they travel as
     // a kernel parameter (constant bank); each member's own values are staged in shared memory
-    // one block per work item: measured 6 % faster than a persistent grid of the co-resident
-    // blocks walking the list (the kernel accepts either: block b takes items b, b + grid, ...)
-    const int grid = std::max(1, e->nitems);
+    // default: one block per work item, measured 6 % faster than a persistent grid of the
+    // co-resident blocks walking the list; the persistent grid on request (the kernel accepts
+    // either: block b takes items b, b + grid, ...)
+    const int grid = e->persistent ? std::max(1, std::min(e->grid, e->nitems)) : std::max(1, e->nitems);
     if (e->precision == LB_FP32SPLIT)
         ensemble_step_kernel<true><<<grid, ENS_BLOCK, 0, e->stream>>>(
             e->sp[0], e->d_members, e->d_items, e->nitems, e->tile_x * e->tile_y, parity, e->flag);
@@ -340,6 +349,7 @@ lb_status lb_ensemble_init(int n, const lb_params* members, const double* const*
     e->precision = prec;
     e->graph_steps = gsteps;
     e->max_items = L.max_items;
+    e->persistent = opts && opts->persistent;
     if (opts && opts->stream) {
         e->stream = (cudaStream_t)opts->stream;
     } else {

@@ -47,7 +47,7 @@ class lb_params(C.Structure):
 class lb_ensemble_opts(C.Structure):
     _fields_ = [("tile_x", C.c_int), ("tile_y", C.c_int), ("graph_steps", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t)]
+                ("workspace_bytes", C.c_size_t), ("persistent", C.c_int)]
 
 
 _lib = None
@@ -89,6 +89,7 @@ def lib() -> C.CDLL:
         L.lb_free.argtypes = [vp]
         L.lb_free.restype = None
         L.lb_probe_fma.argtypes = [C.c_int, vp, C.c_int, C.c_int, C.c_int, vp]
+        L.lb_probe_wait.argtypes = [C.c_ulonglong, C.c_int, vp, vp]
         L.lb_moments_noalloc.argtypes = [C.POINTER(lb_params), vp, vp, vp, vp, vp]
         PP = C.POINTER(C.c_void_p)
         L.lb_ensemble_workspace_bytes.argtypes = [C.c_int, C.POINTER(lb_params),
@@ -121,6 +122,7 @@ def lib() -> C.CDLL:
         L.lb_set_collide_plain.argtypes = [vp]
         L.lb_learned_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                        C.POINTER(C.c_double)]
+        L.lb_learned_tiles.argtypes = [vp, vp, C.c_int]
         _lib = L
     return _lib
 
@@ -387,6 +389,12 @@ class Lattice:
         check(lib().lb_learned_stats(self._ctx, C.byref(a), C.byref(b), C.byref(r)), "lb_learned_stats")
         return {"tiles_checked": a.value, "tiles_fallback": b.value, "max_residual": r.value}
 
+    def learned_tiles(self) -> np.ndarray:
+        """Per-tile decisions [Ly/32, Lx/32] (1 = fell back to the plain collide at the last check)."""
+        out = np.zeros((self.Ly // 32, self.Lx // 32), np.uint8)
+        check(lib().lb_learned_tiles(self._ctx, out.ctypes.data, int(out.size)), "lb_learned_tiles")
+        return out
+
     def close(self) -> None:
         if getattr(self, "_ctx", None) and self._ctx.value:
             lib().lb_free(self._ctx)
@@ -477,6 +485,17 @@ def probe_fma(kind: str, blocks: int, threads: int, iters: int, out, stream=None
     check(lib().lb_probe_fma(k, sh, blocks, threads, iters, out.data_ptr()), "lb_probe_fma")
 
 
+def probe_wait(limit_ns: int, arrive: bool, stream=None):
+    """(gave_up, waited_ns) of the library's bounded barrier wait run alone (lb_probe_wait)."""
+    import torch
+    out = torch.zeros(2, dtype=torch.int64, device="cuda")
+    sh = None if stream is None else stream.cuda_stream
+    check(lib().lb_probe_wait(int(limit_ns), int(bool(arrive)), sh, out.data_ptr()), "lb_probe_wait")
+    torch.cuda.synchronize()
+    gave_up, ns = (int(v) for v in out.cpu())
+    return bool(gave_up), ns
+
+
 def moments_noalloc(Lx: int, Ly: int, f_device_ptr: int, precision=LB_FP64, stream=None):
     """(rho, ux, uy, T) host arrays of one caller-owned device population copy, computed without
     any device allocation (lb_moments_noalloc; at most LB_NOALLOC_MAX_SITES = 65536 sites)."""
@@ -494,7 +513,8 @@ class Ensemble:
     T_bottom, y_periodic, plus host fields rho, ux, uy, T ([Ly][Lx] float64) -- or, for every
     member, a temperature ratio R and a seed instead of fields (lb_ensemble_init_rt)."""
 
-    def __init__(self, members, precision="fp32split", tile=(0, 0), graph_steps=0, stream=None):
+    def __init__(self, members, precision="fp32split", tile=(0, 0), graph_steps=0, stream=None,
+                 persistent=False):
         import torch
         self._ctx = C.c_void_p()
         n = len(members)
@@ -517,7 +537,7 @@ class Ensemble:
         self.stream = torch.cuda.Stream() if stream is None else stream
         sh = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else self.stream
         opts = lb_ensemble_opts(int(tile[0]), int(tile[1]), int(graph_steps),
-                                _precision_code(precision), sh, None, 0)
+                                _precision_code(precision), sh, None, 0, int(bool(persistent)))
         nbytes = C.c_size_t()
         check(lib().lb_ensemble_workspace_bytes(n, params, C.byref(opts), C.byref(nbytes)),
               "lb_ensemble_workspace_bytes")

@@ -81,4 +81,13 @@ def test_invalid_arguments_are_rejected_without_a_gpu(L):
         assert lib.lb_init(C.byref(p), z.ctypes.data, z.ctypes.data, z.ctypes.data, z.ctypes.data,
                            C.byref(ctx)) == 1, field
     lib.lb_free(None)
+    # ensemble members get the single-lattice checks (no GPU needed: the workspace query validates)
+    for field, value in (("tau", float("inf")), ("tau", 0.5), ("T_top", float("inf")),
+                         ("T_bottom", float("nan")), ("gx", float("nan")), ("gy", float("-inf")),
+                         ("wall_mode", 1)):
+        members = (L.lb_params * 2)(L.make_params(64, 64, 0.9), L.make_params(32, 128, 0.8))
+        setattr(members[1], field, value)
+        assert lib.lb_ensemble_workspace_bytes(2, members, None, C.byref(n)) == 1, field
+    members = (L.lb_params * 2)(L.make_params(64, 64, 0.9), L.make_params(32, 128, 0.8))
+    assert lib.lb_ensemble_workspace_bytes(2, members, None, C.byref(n)) == 0
     assert lib.lb_status_str(4) == b"non-finite or non-positive density/temperature"
