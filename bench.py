@@ -44,6 +44,12 @@ NPOP = 37
 # nominal FP64 rate counts an FMA as 2 flops).
 FP64_INST_PER_SITE = 224
 FP64_FLOP_PER_SITE = 389
+# The kernel sources those counts were profiled on (code_digest, below): when the code differs the
+# counts are stale and the roofline's achieved and frac are reported as null
+# (tests/test_bench_host.py fails on a stale table, so a committed tree carries matching counts).
+FP64_INST_SOURCES = {"step_fp64.cu": "53caed22cf06649ae7f7b05bba55e6e1f7f769ee6d1f22ec792ca42ca8654936",
+                     "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437",
+                     "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}
 # The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
 # equilibrium written per population, BGK relaxation with the gravity shift): 2763 flops, counted
 # by compiling the oracle's collide with an operation-counting scalar type
@@ -52,9 +58,7 @@ FP64_FLOP_PER_SITE = 389
 ORACLE_FLOP_PER_SITE = 2763
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
-SM_COUNT = 152
 FP64_INST_PER_CLK_SM = 2
-SM_MAX_MHZ = 2070.0
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
 # 698.450 MB + 646.185 MB for 2359296 sites, scaled per site. Valid only for the kernel source
@@ -113,73 +117,213 @@ def measured_peaks():
         return None
 
 
-class ClockSampler:
-    """nvidia-smi clock/throttle samples during the timed region."""
+NVML_CLOCK_SM = 1
+# clock-event reason bits of NVML's current-clocks-event-reasons mask
+NVML_REASONS = {0x4: "sw_power_cap", 0x8: "hw_slowdown", 0x20: "sw_thermal_slowdown",
+                0x40: "hw_thermal_slowdown", 0x80: "hw_power_brake_slowdown"}
 
-    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
-             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
-             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, gpu_index=None):
-        self.proc = None
-        self.path = None
+class Nvml:
+    """Read-only NVML queries through ctypes (libnvidia-ml): SM clock, maximum SM clock, board
+    power, clock-event reasons and the cumulative energy counter of one GPU. Nothing is set."""
+
+    def __init__(self, uuid=None, index=0):
+        import ctypes as C
+        self.C = C
+        self.lib = C.CDLL("libnvidia-ml.so.1")
+        if self.lib.nvmlInit_v2() != 0:
+            raise OSError("nvmlInit failed")
+        self.h = C.c_void_p()
+        rc = 1
+        if uuid:
+            rc = self.lib.nvmlDeviceGetHandleByUUID(uuid.encode(), C.byref(self.h))
+        if rc != 0:
+            rc = self.lib.nvmlDeviceGetHandleByIndex_v2(C.c_uint(index), C.byref(self.h))
+        if rc != 0:
+            raise OSError("no NVML handle for the GPU")
+        self._reasons = (getattr(self.lib, "nvmlDeviceGetCurrentClocksEventReasons", None)
+                         or self.lib.nvmlDeviceGetCurrentClocksThrottleReasons)
+
+    def _uint(self, fn, *args):
+        v = self.C.c_uint()
+        return v.value if fn(self.h, *args, self.C.byref(v)) == 0 else None
+
+    def sm_mhz(self):
+        return self._uint(self.lib.nvmlDeviceGetClockInfo, self.C.c_int(NVML_CLOCK_SM))
+
+    def sm_max_mhz(self):
+        return self._uint(self.lib.nvmlDeviceGetMaxClockInfo, self.C.c_int(NVML_CLOCK_SM))
+
+    def power_w(self):
+        mw = self._uint(self.lib.nvmlDeviceGetPowerUsage)
+        return None if mw is None else mw / 1000.0
+
+    def reasons(self):
+        v = self.C.c_ulonglong()
+        return v.value if self._reasons(self.h, self.C.byref(v)) == 0 else None
+
+    def energy_mj(self):
+        v = self.C.c_ulonglong()
+        return v.value if self.lib.nvmlDeviceGetTotalEnergyConsumption(self.h, self.C.byref(v)) == 0 else None
+
+
+class GpuSampler:
+    """Samples (host monotonic time, SM MHz, max SM MHz, board W, reason names) of one GPU on a
+    background thread every `interval` s while running: through NVML, or through an nvidia-smi
+    CSV stream (100 ms, host-stamped on arrival) when NVML cannot be loaded. Only the samples
+    inside a window given later are used (samples_in_window)."""
+
+    QUERY = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, nvml=None, gpu_index=0, interval=0.02):
+        self.nvml = nvml
         self.gpu_index = gpu_index
+        self.interval = interval
+        self.samples = []
+        self._stop = None
+        self._thread = None
+        self._proc = None
 
     def start(self):
-        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
-        os.close(fd)
-        cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits", "-lms", "200"]
-        if self.gpu_index is not None:
-            cmd += ["-i", str(self.gpu_index)]
-        try:
-            self.out = open(self.path, "w")
-            self.proc = subprocess.Popen(cmd, stdout=self.out, stderr=subprocess.DEVNULL)
-        except OSError:
-            self.proc = None
+        import threading
+        self._stop = threading.Event()
+        if self.nvml is not None:
+            target = self._run_nvml
+        else:
+            cmd = ["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                   "-lms", "100", "-i", str(self.gpu_index)]
+            try:
+                self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL,
+                                              text=True)
+            except OSError:
+                self._proc = None
+                return
+            target = self._run_smi
+        self._thread = threading.Thread(target=target, daemon=True)
+        self._thread.start()
+
+    def _run_nvml(self):
+        n = self.nvml
+        while not self._stop.is_set():
+            mask = n.reasons()
+            names = [] if mask is None else [v for b, v in NVML_REASONS.items() if mask & b]
+            self.samples.append((time.monotonic(), n.sm_mhz(), n.sm_max_mhz(), n.power_w(), names))
+            self._stop.wait(self.interval)
+
+    def _run_smi(self):
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self._proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                vals = [float(parts[0]), float(parts[1]), float(parts[2])]
+            except ValueError:
+                continue
+            active = [nm for nm, v in zip(names, parts[3:7]) if v.lower().startswith("active")]
+            self.samples.append((time.monotonic(), *vals, active))
+            if self._stop.is_set():
+                break
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
-        self.out.close()
-        sm, smax, power, reasons = [], [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as fh:
-            for line in fh:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    smax.append(float(parts[2]))
-                    power.append(float(parts[3]))
-                except ValueError:
-                    continue
-                for n, v in zip(names, parts[5:9]):
-                    if v.lower().startswith("active"):
-                        reasons.add(n)
-        os.unlink(self.path)
-        if not sm:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
-        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
-                "power_w_median": statistics.median(power), "reasons": sorted(reasons)}
+        if self._stop is not None:
+            self._stop.set()
+        if self._proc is not None:
+            self._proc.terminate()
+            try:
+                self._proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self._proc.kill()
+        if self._thread is not None:
+            self._thread.join(timeout=5)
 
 
-def energy_of(clocks, ms_per_step, sites):
-    """Energy to solution per step from the board power sampled during the timed region (the
-    analog of the paper's RAPL package + DRAM energy per iteration, Sec. 5 and Fig. 5; on GB300 the
-    board power includes the HBM)."""
-    p = clocks.get("power_w_median")
-    if not p:
+def samples_in_window(samples, t0, t1):
+    """The samples taken at host times t0 <= t <= t1."""
+    return [s for s in samples if t0 <= s[0] <= t1]
+
+
+def summarize_clocks(samples, source):
+    """Clock record of a window's samples: median SM clock, the maximum clock, median board power
+    and every throttle reason seen."""
+    sm = [s[1] for s in samples if s[1] is not None]
+    if not sm:
+        return {"sm_mhz": None, "sm_max_mhz": None, "samples": 0, "reasons": ["no samples in the window"],
+                "source": source}
+    smax = [s[2] for s in samples if s[2] is not None]
+    power = [s[3] for s in samples if s[3] is not None]
+    reasons = sorted({r for s in samples for r in s[4]})
+    return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax) if smax else None,
+            "samples": len(sm), "power_w_median": statistics.median(power) if power else None,
+            "reasons": reasons, "source": source}
+
+
+def energy_from_counter(e0_mj, e1_mj, seconds, steps, sites):
+    """Energy to solution per step from a cumulative energy counter read before and after `steps`
+    steps that took `seconds` (the analog of the paper's RAPL package + DRAM energy per iteration,
+    Sec. 5 and Fig. 5; on GB300 the board energy includes the HBM)."""
+    if e0_mj is None or e1_mj is None or e1_mj <= e0_mj or steps <= 0 or seconds <= 0:
         return None
-    j = p * ms_per_step * 1e-3
-    return {"power_w_median": round(p, 1), "joules_per_step": round(j, 4),
-            "nJ_per_site_update": round(j / sites * 1e9, 3),
-            "source": "nvidia-smi power.draw samples every 200 ms during the timed region"}
+    j = (e1_mj - e0_mj) * 1e-3
+    return {"joules_per_step": round(j / steps, 4), "nJ_per_site_update": round(j / steps / sites * 1e9, 3),
+            "power_w": round(j / seconds, 1), "window_s": round(seconds, 3), "window_steps": steps}
+
+
+def energy_from_power(samples, seconds, steps, sites):
+    """The same from board-power samples inside the window (median power x window time)."""
+    power = [s[3] for s in samples if s[3] is not None]
+    if not power or steps <= 0 or seconds <= 0:
+        return None
+    j = statistics.median(power) * seconds
+    return {"joules_per_step": round(j / steps, 4), "nJ_per_site_update": round(j / steps / sites * 1e9, 3),
+            "power_w": round(statistics.median(power), 1), "window_s": round(seconds, 3),
+            "window_steps": steps, "samples": len(power)}
+
+
+def energy_window_steps(ms_per_step, min_seconds=2.0, at_least=1):
+    """Steps of the energy window: enough for min_seconds at the measured step time."""
+    return int(max(at_least, math.ceil(min_seconds * 1e3 / max(ms_per_step, 1e-6))))
+
+
+def measure_energy(run, sync, ms_per_step, sites, nvml, sampler):
+    """Energy per step over its own window of >= 2 s of steps (after the timed region), from NVML's
+    cumulative energy counter read before and after, else from the power samples in the window."""
+    steps = energy_window_steps(ms_per_step)
+    sync()
+    e0 = nvml.energy_mj() if nvml else None
+    t0 = time.monotonic()
+    run(steps)
+    sync()
+    t1 = time.monotonic()
+    e1 = nvml.energy_mj() if nvml else None
+    out = energy_from_counter(e0, e1, t1 - t0, steps, sites)
+    win = samples_in_window(sampler.samples, t0, t1)
+    if out is not None:
+        out["source"] = "NVML cumulative energy counter over a window of steps after the timed region"
+    else:
+        out = energy_from_power(win, t1 - t0, steps, sites)
+        if out is not None:
+            out["source"] = "median board power sampled in a window of steps after the timed region"
+    if out is not None:
+        out["clocks_in_window"] = summarize_clocks(win, "in the energy window")
+    return out
+
+
+def open_nvml(local_rank):
+    """NVML handle of this rank's GPU (by UUID from torch), or None if NVML is unavailable."""
+    try:
+        import torch
+        uuid = getattr(torch.cuda.get_device_properties(local_rank), "uuid", None)
+        uuid = f"GPU-{uuid}" if uuid is not None and not str(uuid).startswith("GPU-") else uuid
+        return Nvml(uuid=None if uuid is None else str(uuid), index=visible_gpu_index(local_rank))
+    except (OSError, AttributeError):
+        return None
+
+
+def sites_of(lx, ly):
+    return lx * ly
 
 
 def visible_gpu_index(local_rank):
@@ -294,10 +438,26 @@ def metric_name(precision="fp64"):
 
 # ----------------------------------------------------------------------------------------------
 
+def device_peak_terms(torch, local, nvml, clocks):
+    """(SM count, maximum SM clock in MHz, where they came from) of this rank's GPU: the SM count
+    from the CUDA device properties, the maximum SM clock from NVML (else from the clock samples,
+    else the recipe's 2070 MHz)."""
+    sms = int(torch.cuda.get_device_properties(local).multi_processor_count)
+    mhz, src = None, None
+    if nvml is not None:
+        mhz = nvml.sm_max_mhz()
+        src = "SM count from cudaDeviceProp, max SM clock from NVML"
+    if not mhz and clocks.get("sm_max_mhz"):
+        mhz, src = clocks["sm_max_mhz"], "SM count from cudaDeviceProp, max SM clock from the clock samples"
+    if not mhz:
+        mhz, src = 2070.0, "SM count from cudaDeviceProp, max SM clock the recipe's 2070 MHz"
+    return sms, float(mhz), src
+
+
 def fp64_probe(lb, torch, stream, kind="fp64"):
     """Achieved FP64 FMA rate of the library's probe (TFLOP/s, FMA = 2 flops). kind "fp64": chains
     that settle on a fixed point; "fp64_varying": operands that keep changing."""
-    blocks, threads, iters = SM_COUNT * 8, 256, 2048
+    blocks, threads, iters = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count * 8, 256, 2048
     out = torch.empty(blocks * threads, dtype=torch.float64, device="cuda")
     with torch.cuda.stream(stream):
         lb.probe_fma(kind, blocks, threads, iters, out, stream)   # warm-up
@@ -369,21 +529,27 @@ def main():
     probe_tf = fp64_probe(lb, torch, stream)
     probe_var_tf = fp64_probe(lb, torch, stream, "fp64_varying")
 
-    sampler = ClockSampler(visible_gpu_index(local))
+    nvml = open_nvml(local)
+    sampler = GpuSampler(nvml, visible_gpu_index(local))
+    sampler.start()
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t_start = time.monotonic()
     e0.record(stream)
     lat.step(args.steps)
     e1.record(stream)
     e1.synchronize()
-    clocks = sampler.stop()
+    t_end = time.monotonic()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     lat.sync()    # raises on a non-finite state
+    clocks = summarize_clocks(samples_in_window(sampler.samples, t_start, t_end),
+                              "NVML every 20 ms in the timed region" if nvml else
+                              "nvidia-smi every 100 ms in the timed region")
+    energy = measure_energy(lat.step, lat.sync, ms / args.steps, sites_of(LX, LY), nvml, sampler)
+    sampler.stop()
     ms = replicas.max_over_ranks(ms, dist, device="cuda")
     sites = LX * LY
     value = replicas.aggregate_mlups(sites, args.steps, ms, world)
@@ -418,24 +584,34 @@ def main():
     # ---- roofline of the step kernel ----
     hbm = (measured_peaks() or {}).get("hbm_gbs", 6800.0)
     if args.precision == "fp64":
-        inst_rate = FP64_INST_PER_SITE * sites / kernel_s / 1e12
-        peak = SM_COUNT * FP64_INST_PER_CLK_SM * SM_MAX_MHZ * 1e6 / 1e12
+        sm_count, sm_max_mhz, peak_src = device_peak_terms(torch, local, nvml, clocks)
+        peak = sm_count * FP64_INST_PER_CLK_SM * sm_max_mhz * 1e6 / 1e12
+        counts_valid = sources_match({"sources": FP64_INST_SOURCES})
+        if not counts_valid:
+            print("bench.py: step_fp64 sources changed since FP64_INST_PER_SITE was profiled; "
+                  "roofline achieved/frac reported as null", file=sys.stderr)
+        inst_rate = FP64_INST_PER_SITE * sites / kernel_s / 1e12 if counts_valid else None
         traffic = (round(TRAFFIC_FP64["bytes_per_site"] * sites) if sources_match(TRAFFIC_FP64)
                    and (LX, LY) == (2304, 8192) else None)
-        roofline = {"bound": "alu", "kernel": "step_fp64_kernel", "achieved": round(inst_rate, 4),
+        roofline = {"bound": "alu", "kernel": "step_fp64_kernel",
+                    "achieved": None if inst_rate is None else round(inst_rate, 4),
                     "peak": round(peak, 4), "unit": "T FP64-instructions/s",
-                    "frac": round(inst_rate / peak, 4), "traffic": traffic,
-                    "peak_note": "FP64 pipe: 152 SMs x 2 FP64 instructions (add, mul or FMA) per "
-                                 "clock per SM x 2070 MHz, the recipe's 1.25 TFLOP/s nominal with "
-                                 "FMA = 2 flops; measured by the library's FMA probe below",
+                    "frac": None if inst_rate is None else round(inst_rate / peak, 4), "traffic": traffic,
+                    "peak_note": f"FP64 pipe: {sm_count} SMs x 2 FP64 instructions (add, mul or FMA) "
+                                 f"per clock per SM x {sm_max_mhz:.0f} MHz ({peak_src}); the recipe's "
+                                 "1.25 TFLOP/s nominal with FMA = 2 flops; measured by the library's "
+                                 "FMA probe below",
+                    "sm_count": sm_count, "sm_max_mhz": sm_max_mhz, "peak_terms_source": peak_src,
                     "algorithmic_fp64_inst_per_site": FP64_INST_PER_SITE,
+                    "inst_count_matches_sources": counts_valid,
                     "achieved_tflops": round(FP64_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
                     "oracle_flop_per_site": ORACLE_FLOP_PER_SITE,
                     "achieved_tflops_oracle_formulation": round(ORACLE_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
                     "peak_tflops": round(2 * peak, 4),
                     "probe_fp64_tflops": round(probe_tf, 4),
                     "probe_fp64_varying_tflops": round(probe_var_tf, 4),
-                    "frac_of_varying_probe": round(inst_rate / (probe_var_tf / 2), 4),
+                    "frac_of_varying_probe": (None if inst_rate is None
+                                              else round(inst_rate / (probe_var_tf / 2), 4)),
                     "probe_note": "FMA chains that settle on a fixed point reach nearly the nominal "
                                   "rate; with operands that keep changing GB300's FP64 pipe sustains "
                                   "less (varying probe), the rate real data sees",
@@ -467,6 +643,9 @@ def main():
             net.close()
         if not args.no_ensemble:
             forms["ensemble"] = measure_ensemble(lb, torch, np, inputs, value / world)
+            forms["ensemble_persistent"] = measure_ensemble(lb, torch, np, inputs, value / world,
+                                                            persistent=True,
+                                                            tile=tuple(forms["ensemble"]["tile"]))
         forms["table1_1024x8192"] = measure_table1(lb, torch, np, inputs)
 
     line = {"metric": metric_name(args.precision),
@@ -477,7 +656,7 @@ def main():
             "data": "synthetic (seeded Rayleigh-Taylor fields)",
             "config": workload_config(world, args.precision),
             "roofline": roofline, "clocks": clocks, "gpu_launches": args.steps,
-            "energy": energy_of(clocks, ms / args.steps, world * sites),
+            "energy": energy,
             "e2e": e2e,
             "paper_context": {"KNL 7230 flat/quad Global MLUPS 1024x8192": 119,
                               "P100 Global MLUPS 1024x8192": 232}}
@@ -713,10 +892,13 @@ def measure_table1(lb, torch, np, inputs, reps=20):
                            "collide_GFs": 2253, "collide_MLUPS": 340, "global_MLUPS": 232}}
 
 
-def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300):
+def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300, persistent=False,
+                     tile=None):
     """Batched ensemble: n seed-drawn Rayleigh-Taylor lattices (Lx uniform over multiples of 32 in
     [128, 1024], Ly = 4 Lx, Atwood in [0.05, 0.5], tau in [tau_min(A), 1.2]), FP32 storage (exact-split
-    accumulation), autotuned tile shape, 100-step CUDA graphs; MLUPS = sum of sites x steps / s."""
+    accumulation), autotuned tile shape (or the given one), 100-step CUDA graphs; MLUPS = sum of
+    sites x steps / s. persistent: a grid of the co-resident blocks walking the work list instead
+    of one block per work item."""
     descs = inputs.ensemble_members(n, seed=seed)
     specs = []
     for d in descs:
@@ -725,9 +907,13 @@ def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300)
                       "T_top": st.T_top, "T_bottom": st.T_bottom, "rho": st.rho, "ux": st.ux,
                       "uy": st.uy, "T": st.T})
     stream = torch.cuda.Stream()
-    ens = lb.Ensemble(specs, precision="fp32split", graph_steps=100, stream=stream)
+    ens = lb.Ensemble(specs, precision="fp32split", graph_steps=100, stream=stream,
+                      persistent=persistent, tile=tile or (0, 0))
     specs = None
-    tx, ty, tune_mlups = ens.autotune(steps=3)
+    if tile is None:
+        tx, ty, tune_mlups = ens.autotune(steps=3)
+    else:
+        (tx, ty), tune_mlups = tile, None
     ens.step(100)
     ens.sync()
     sites = ens.info()["sites"]
@@ -746,8 +932,10 @@ def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300)
     return {"members": n, "sites": sites, "steps": steps, "mlups": round(mlups, 1),
             "speedup_vs_fp64": round(mlups / fp64_mlups, 3), "hbm_gbs": round(gbs, 1),
             "hbm_frac": round(gbs / hbm, 4), "tile": [tx, ty], "work_items": info["items"],
-            "autotune_best_mlups": round(tune_mlups, 1), "graph_steps": 100,
-            "precision": "fp32split"}
+            "autotune_best_mlups": None if tune_mlups is None else round(tune_mlups, 1),
+            "graph_steps": 100, "precision": "fp32split",
+            "launch": "persistent grid (co-resident blocks walk the work list)" if persistent
+                      else "one block per work item"}
 
 
 if __name__ == "__main__":
