@@ -47,8 +47,8 @@ FP64_FLOP_PER_SITE = 389
 # The kernel sources those counts were profiled on (code_digest, below): when the code differs the
 # counts are stale and the roofline's achieved and frac are reported as null
 # (tests/test_bench_host.py fails on a stale table, so a committed tree carries matching counts).
-FP64_INST_SOURCES = {"step_fp64.cu": "53caed22cf06649ae7f7b05bba55e6e1f7f769ee6d1f22ec792ca42ca8654936",
-                     "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437",
+FP64_INST_SOURCES = {"step_fp64.cu": "4547509feaf768fdab3e7d55bff7b208584aaa54f613781b7290a0b4e410950f",
+                     "d2q37_gpu.cuh": "0d01718b02a4a5a3855735e0210c120e052ae4a5e17a04021a2a833c966400e9",
                      "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}
 # The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
 # equilibrium written per population, BGK relaxation with the gravity shift): 2763 flops, counted
@@ -61,21 +61,21 @@ FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 FP64_INST_PER_CLK_SM = 2
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 698.450 MB + 646.185 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# 698.452 MB + 646.109 MB for 2359296 sites, scaled per site. Valid only for the kernel source
 # it was taken on (code_digest of the files below: sha256 of the code without comments);
 # otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (698.449664e6 + 646.185216e6) / 2359296,
-                "sources": {"step_fp64.cu": "53caed22cf06649ae7f7b05bba55e6e1f7f769ee6d1f22ec792ca42ca8654936",
-                            "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437",
+TRAFFIC_FP64 = {"bytes_per_site": (698.452480e6 + 646.109440e6) / 2359296,
+                "sources": {"step_fp64.cu": "4547509feaf768fdab3e7d55bff7b208584aaa54f613781b7290a0b4e410950f",
+                            "d2q37_gpu.cuh": "0d01718b02a4a5a3855735e0210c120e052ae4a5e17a04021a2a833c966400e9",
                             "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}}
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
-# (profiles/step_fp32split_1152x2048_full.md), 349.322 MB + 302.927 MB for 2359296 sites.
-TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.322496e6 + 302.927104e6) / 2359296,
-                     "sources": {"step_fp32dev.cu": "c3851df7f987638f59aa4678fecd1aae308352d8e3fe108c25bfb87cb46c501a",
-                                 "site_fp32dev.cuh": "fd45111f7e8b33d635222b860c17888a3e1857abc7898c0d1af8bd2ef0f12af3",
-                                 "d2q37_gpu.cuh": "370a76552951286d4c7fb342fc95cb33ebdb8f27efc349941b612e63092a5437"}}
+# (profiles/step_fp32split_1152x2048_full.md), 349.265 MB + 303.084 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.264640e6 + 303.084288e6) / 2359296,
+                     "sources": {"step_fp32dev.cu": "9bd8776f652ce5402527ff8a5eb09373b1db75d7a1be4418d81624f303f67877",
+                                 "site_fp32dev.cuh": "ed58b9d3cc6f5e6464749fb716c6985c34642f9abdd0ca704ee46d6a60204ae1",
+                                 "d2q37_gpu.cuh": "0d01718b02a4a5a3855735e0210c120e052ae4a5e17a04021a2a833c966400e9"}}
 
 
 def code_digest(path):

@@ -95,6 +95,8 @@ struct StepParams {
     int Lx, Ly;
     int y_periodic;
     int wall_mode;         // lb_wall_mode: 0 rest-equilibrium halo rows, 1 mirror closure
+    int cut;               // slab of a larger lattice: bit 0 = no wall below row 0, bit 1 = none
+                           // above row Ly - 1 (those halo rows are ghost rows another slab fills)
     long long plane;       // elements per population plane, (Ly + 2*HALO) * Lx
     // row of a site index n < 2^31 without a division: y = (n * row_m) >> row_s (row_of)
     unsigned row_m;
@@ -187,7 +189,8 @@ __device__ __forceinline__ void half_step_shift(const StepParams& P, double& ux,
 // fields. store(i, o, v) writes FP64 value v of population i at element offset o of a plane.
 // Rest closure: rho times the rest equilibrium per unit density at the wall temperature; mirror
 // closure: mirror_halo (a non-positive reflected temperature sets flag bit 1 and that halo site
-// gets the rest closure instead).
+// gets the rest closure instead). A side cut from a neighbouring slab (P.cut) has no wall: its halo
+// rows are ghost rows that the exchange between slabs writes.
 template <class Store>
 __device__ __forceinline__ void write_wall_rows(const StepParams& P, int x, int y, double rho, double ux,
                                                 double uy, double T, int* __restrict__ flag,
@@ -197,7 +200,7 @@ __device__ __forceinline__ void write_wall_rows(const StepParams& P, int x, int 
 #pragma unroll
     for (int side = 0; side < 2; ++side) {
         const bool bottom = side == 0;
-        if (bottom ? (y >= HALO) : (y < Ly - HALO)) continue;
+        if (bottom ? (y >= HALO || (P.cut & 1)) : (y < Ly - HALO || (P.cut & 2))) continue;
         const long long o = bottom ? (long long)(HALO - 1 - y) * Lx + x
                                    : (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
         if (P.wall_mode == 1) {

@@ -34,6 +34,9 @@ cudaError_t launch_step_fp64(const double* src, double* dst, const StepParams& P
 cudaError_t launch_propagate_fp64(const double* src, double* dst, const StepParams& P,
                                   cudaStream_t s);
 cudaError_t launch_collide_fp64(double* f, const StepParams& P, int* flag, cudaStream_t s);
+// the fused step on rows row0 .. row1 - 1 only (a slab's boundary bands or its interior)
+cudaError_t launch_step_fp64_rows(const double* src, double* dst, const StepParams& P, int* flag,
+                                  int row0, int row1, cudaStream_t s);
 cudaError_t launch_init_fp64(const double* rho, const double* ux, const double* uy,
                              const double* T, double* f, const StepParams& P, int* flag, cudaStream_t s);
 // half_step != 0: the half-step fields (u - g/2, T + |g|^2 / (4 D)) instead of the plain moments
@@ -47,6 +50,9 @@ cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& 
 // same storage, exact-split FP32 accumulation instead of FP64 (site_fp32dev.cuh)
 cudaError_t launch_step_fp32split(const float* src, float* dst, const StepParams& P, int* flag,
                                   cudaStream_t s);
+// either FP32 step (split = exact-split or FP64-sum form) on rows row0 .. row1 - 1 only
+cudaError_t launch_step_fp32_rows(bool split, const float* src, float* dst, const StepParams& P, int* flag,
+                                  int row0, int row1, cudaStream_t s);
 // the same step with TMA-staged pulls (step_fp32split_tma.cu); tmap is a CUtensorMap of src
 cudaError_t launch_step_fp32split_tma(const void* tmap, const float* src, float* dst,
                                       const StepParams& P, int* flag, int grid, cudaStream_t s);
@@ -80,5 +86,13 @@ cudaError_t launch_pairs(const float* src, const StepParams& P, const int* sites
 lb_status learned_tiles(LearnedState* ls, int ntiles, unsigned char* modes, cudaStream_t s);
 lb_status learned_stats(LearnedState* ls, long long* checked, long long* fallback, double* max_res,
                         cudaStream_t s);
+
+// ---- slabs of a lattice cut along y (slab.cu): 26 ghost population-rows per cut and direction ----
+int ghost_row_count();
+cudaError_t launch_slab_pack(size_t elem, const void* f, void* buf, const StepParams& P, int side, cudaStream_t s);
+cudaError_t launch_slab_unpack(size_t elem, const void* buf, void* f, const StepParams& P, int side,
+                               cudaStream_t s);
+cudaError_t launch_slab_exchange(size_t elem, void* f_lo, const StepParams& Plo, void* f_hi,
+                                 const StepParams& Phi, cudaStream_t s);
 
 }  // namespace lbg

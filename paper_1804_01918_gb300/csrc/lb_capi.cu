@@ -15,6 +15,7 @@
 
 #include "../../include/lb_d2q37.h"
 #include "../../include/lb_learned.h"
+#include "../../include/lb_slab.h"
 #include "d2q37_gpu.cuh"
 #include "kernels.cuh"
 
@@ -210,6 +211,8 @@ struct lb_ctx {
     alignas(64) unsigned char tmap[2][128];  // TMA descriptors of the two FP32 population copies
     bool tma_ready = false;                  // tensor maps built (FP32SPLIT, Lx % 4 == 0)
     bool use_tma = false;                    // step with the TMA-staged kernel
+    bool band_done = false;                  // slab: boundary bands of a split step written, swap pending
+    cudaEvent_t ev = nullptr;                // slab: orders an exchange after this context's queued work
 };
 
 namespace {
@@ -348,14 +351,19 @@ void lb_free(lb_ctx* c) {
         if (c->graph[k]) cudaGraphExecDestroy(c->graph[k]);
     learned_destroy(c->learned);
     lb_mlp_free(c->own_net);
+    if (c->ev) cudaEventDestroy(c->ev);
     if (c->own_ws && c->ws) cudaFree(c->ws);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }
 
-lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const double* uy,
-                  const double* T, lb_ctx** out) {
-    lbg::NvtxRange nvtx_("lb_init");
+}  // extern "C"
+
+namespace {
+// lb_init of a whole lattice (cuts = 0) or of one slab of a larger lattice (cuts: bit 0 = cut
+// below row 0, bit 1 = cut above row Ly - 1; those sides get no wall halo rows).
+lb_status init_ctx(const lb_params* p, int cuts, const double* rho, const double* ux, const double* uy,
+                   const double* T, lb_ctx** out) {
     if (!out) return LB_ERR_ARG;
     *out = nullptr;
     lb_status st = check_params(p);
@@ -370,6 +378,7 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
     c->p = *p;
     c->L = L;
     fill_step_params(*p, c->sp);
+    c->sp.cut = cuts;
     if (p->stream) {
         c->stream = (cudaStream_t)p->stream;
     } else {
@@ -433,10 +442,21 @@ lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const
     *out = c;
     return LB_OK;
 }
+}  // namespace
+
+extern "C" {
+
+lb_status lb_init(const lb_params* p, const double* rho, const double* ux, const double* uy,
+                  const double* T, lb_ctx** out) {
+    lbg::NvtxRange nvtx_("lb_init");
+    return init_ctx(p, 0, rho, ux, uy, T, out);
+}
 
 lb_status lb_step(lb_ctx* c, int n) {
     lbg::NvtxRange nvtx_("lb_step");
     if (!c || n < 0) return LB_ERR_ARG;
+    // a slab needs the ghost-row exchange between its steps
+    if ((c->sp.cut && n > 1) || c->band_done) return LB_ERR_STATE;
     // the learned step's check schedule varies from step to step: launch it directly
     while (n >= GRAPH_STEPS && !c->graph_failed && !c->learned) {
         const int par = c->cur;
@@ -471,7 +491,7 @@ lb_status lb_propagate(lb_ctx* c) {
 
 lb_status lb_set_staging(lb_ctx* c, int use_tma) {
     if (!c) return LB_ERR_ARG;
-    if (use_tma && !c->tma_ready) return LB_ERR_STATE;
+    if (use_tma && (!c->tma_ready || c->sp.cut)) return LB_ERR_STATE;
     LB_CUDA(cudaStreamSynchronize(c->stream));
     for (int k = 0; k < 2; ++k)
         if (c->graph[k]) {
@@ -591,7 +611,7 @@ lb_status lb_collect_pairs(lb_ctx* c, const int* sites, int n, float* pre, float
 
 lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int check_every) {
     if (!c || !net) return LB_ERR_ARG;
-    if (c->p.precision != LB_FP32SPLIT) return LB_ERR_STATE;
+    if (c->p.precision != LB_FP32SPLIT || c->sp.cut) return LB_ERR_STATE;
     LearnedState* ls = nullptr;
     lb_status st = learned_create(net, c->p.Lx, c->p.Ly, bound, check_every, &ls);
     if (st != LB_OK) return st;
@@ -697,6 +717,99 @@ lb_status lb_learned_tiles(lb_ctx* c, unsigned char* modes, int n) {
 lb_status lb_steps_done(const lb_ctx* c, long long* n) {
     if (!c || !n) return LB_ERR_ARG;
     *n = c->steps;
+    return LB_OK;
+}
+
+// ---- slabs of a lattice cut along y (include/lb_slab.h) ----
+
+lb_status lb_init_slab(const lb_params* p, int cuts, const double* rho, const double* ux, const double* uy,
+                       const double* T, lb_ctx** out) {
+    lbg::NvtxRange nvtx_("lb_init_slab");
+    if (!p || cuts < 0 || cuts > 3 || (cuts && p->y_periodic)) return LB_ERR_ARG;
+    if (cuts && p->Ly < 2 * HALO) return LB_ERR_ARG;
+    lb_status st = init_ctx(p, cuts, rho, ux, uy, T, out);
+    if (st != LB_OK) return st;
+    cudaError_t e = cudaEventCreateWithFlags(&(*out)->ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        lb_free(*out);
+        *out = nullptr;
+        return cuda_fail(e, "cudaEventCreateWithFlags");
+    }
+    return LB_OK;
+}
+
+lb_status lb_slab_step(lb_ctx* c, int part) {
+    lbg::NvtxRange nvtx_("lb_slab_step");
+    if (!c || part < 0 || part > 2) return LB_ERR_ARG;
+    if (c->learned || c->use_tma) return LB_ERR_STATE;
+    if (part == 0) {
+        if (c->band_done) return LB_ERR_STATE;
+        return launch_one_step(c);
+    }
+    if ((part == 1) == c->band_done) return LB_ERR_STATE;  // bands first, then the rest
+    const int Ly = c->p.Ly;
+    const int lo = (c->sp.cut & 1) ? HALO : 0, hi = (c->sp.cut & 2) ? Ly - HALO : Ly;
+    auto rows = [&](int r0, int r1) -> cudaError_t {
+        if (c->p.precision == LB_FP64)
+            return launch_step_fp64_rows((const double*)c->buf[c->cur], (double*)c->buf[c->cur ^ 1], c->sp,
+                                         c->flag, r0, r1, c->stream);
+        return launch_step_fp32_rows(c->p.precision == LB_FP32SPLIT, (const float*)c->buf[c->cur],
+                                     (float*)c->buf[c->cur ^ 1], c->sp, c->flag, r0, r1, c->stream);
+    };
+    cudaError_t e;
+    if (part == 1) {
+        e = rows(0, lo);
+        if (e == cudaSuccess) e = rows(hi, Ly);
+        if (e != cudaSuccess) return cuda_fail(e, "slab band launch");
+        c->band_done = true;
+        return LB_OK;
+    }
+    e = rows(lo, hi);
+    if (e != cudaSuccess) return cuda_fail(e, "slab interior launch");
+    c->band_done = false;
+    c->cur ^= 1;
+    c->steps += 1;
+    return LB_OK;
+}
+
+namespace {
+// The copy holding the newest state: the one being written while a split step is half done.
+void* newest(lb_ctx* c) { return c->buf[c->band_done ? c->cur ^ 1 : c->cur]; }
+size_t elem_bytes(const lb_ctx* c) { return c->p.precision == LB_FP64 ? 8 : 4; }
+}  // namespace
+
+lb_status lb_slab_pack(lb_ctx* c, int side, void* buf) {
+    if (!c || !buf || side < 0 || side > 1) return LB_ERR_ARG;
+    cudaError_t e = launch_slab_pack(elem_bytes(c), newest(c), buf, c->sp, side, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slab pack launch");
+    return LB_OK;
+}
+
+lb_status lb_slab_unpack(lb_ctx* c, int side, const void* buf) {
+    if (!c || !buf || side < 0 || side > 1) return LB_ERR_ARG;
+    if (!(c->sp.cut & (1 << side))) return LB_ERR_ARG;  // a wall side has no ghost rows
+    cudaError_t e = launch_slab_unpack(elem_bytes(c), buf, newest(c), c->sp, side, c->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slab unpack launch");
+    return LB_OK;
+}
+
+lb_status lb_slab_exchange(lb_ctx* lo, lb_ctx* hi) {
+    lbg::NvtxRange nvtx_("lb_slab_exchange");
+    if (!lo || !hi || lo == hi) return LB_ERR_ARG;
+    if (!(lo->sp.cut & 2) || !(hi->sp.cut & 1) || lo->p.Lx != hi->p.Lx || lo->p.precision != hi->p.precision)
+        return LB_ERR_ARG;
+    if (lo->band_done || hi->band_done || !lo->ev || !hi->ev) return LB_ERR_STATE;
+    if (hi->stream != lo->stream) {
+        LB_CUDA(cudaEventRecord(hi->ev, hi->stream));
+        LB_CUDA(cudaStreamWaitEvent(lo->stream, hi->ev, 0));
+    }
+    cudaError_t e = launch_slab_exchange(elem_bytes(lo), lo->buf[lo->cur], lo->sp, hi->buf[hi->cur], hi->sp,
+                                         lo->stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slab exchange launch");
+    if (hi->stream != lo->stream) {
+        LB_CUDA(cudaEventRecord(lo->ev, lo->stream));
+        LB_CUDA(cudaStreamWaitEvent(hi->stream, lo->ev, 0));
+    }
     return LB_OK;
 }
 

@@ -214,18 +214,18 @@ static __device__ __noinline__ void split_wall_rows(float* __restrict__ dst, con
 }
 
 // Rest-closure wall halo rows fed by site (x, y): rho times the rest equilibrium per unit density
-// at the wall temperature, stored as FP32 deviations.
+// at the wall temperature, stored as FP32 deviations (none on a side cut from a neighbouring slab).
 __device__ __forceinline__ void rest_wall_rows32(float* __restrict__ dst, const StepParams& P, int x, int y,
                                                  double rho) {
     const int Lx = P.Lx, Ly = P.Ly;
     const long long plane = P.plane;
-    if (y < HALO) {
+    if (y < HALO && !(P.cut & 1)) {
         const long long o = (long long)(HALO - 1 - y) * Lx + x;
 #pragma unroll
         for (int i = 0; i < NPOP; ++i)
             __stcs(dst + (long long)i * plane + o, (float)fma(rho, P.wall_bot[i], -shell_w(shell_of(i))));
     }
-    if (y >= Ly - HALO) {
+    if (y >= Ly - HALO && !(P.cut & 2)) {
         const long long o = (long long)(Ly + HALO + (Ly - 1 - y)) * Lx + x;
 #pragma unroll
         for (int i = 0; i < NPOP; ++i)

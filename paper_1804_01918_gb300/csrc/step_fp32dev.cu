@@ -27,20 +27,21 @@ namespace lbg {
 
 namespace {
 
+// Both step kernels cover sites site0 .. site1 - 1 (the whole lattice, or a band of rows of a slab).
 __global__ void __launch_bounds__(SITE_BLOCK)
 step_fp32dev_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P,
-                    int* __restrict__ flag) {
-    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
-    if (site >= P.Lx * P.Ly) return;
+                    int* __restrict__ flag, int site0, int site1) {
+    const int site = site0 + blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= site1) return;
     const int y = row_of(site, P);
     fp32dev_site(src, dst, P, site - y * P.Lx, y, flag);
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
 step_fp32split_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P,
-                      int* __restrict__ flag) {
-    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
-    if (site >= P.Lx * P.Ly) return;
+                      int* __restrict__ flag, int site0, int site1) {
+    const int site = site0 + blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= site1) return;
     const int y = row_of(site, P);
     fp32split_site(src, dst, P, P, site - y * P.Lx, y, flag);
 }
@@ -164,13 +165,24 @@ inline int site_blocks32(const StepParams& P) {
 
 cudaError_t launch_step_fp32dev(const float* src, float* dst, const StepParams& P, int* flag,
                                 cudaStream_t s) {
-    step_fp32dev_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
+    step_fp32dev_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag, 0, P.Lx * P.Ly);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_fp32split(const float* src, float* dst, const StepParams& P, int* flag,
                                   cudaStream_t s) {
-    step_fp32split_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
+    step_fp32split_kernel<<<site_blocks32(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag, 0, P.Lx * P.Ly);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_fp32_rows(bool split, const float* src, float* dst, const StepParams& P, int* flag,
+                                  int row0, int row1, cudaStream_t s) {
+    if (row1 <= row0) return cudaSuccess;
+    const int n = (row1 - row0) * P.Lx, blocks = (n + SITE_BLOCK - 1) / SITE_BLOCK;
+    if (split)
+        step_fp32split_kernel<<<blocks, SITE_BLOCK, 0, s>>>(src, dst, P, flag, row0 * P.Lx, row1 * P.Lx);
+    else
+        step_fp32dev_kernel<<<blocks, SITE_BLOCK, 0, s>>>(src, dst, P, flag, row0 * P.Lx, row1 * P.Lx);
     return cudaGetLastError();
 }
 

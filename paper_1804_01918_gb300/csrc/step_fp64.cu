@@ -334,12 +334,13 @@ __device__ __forceinline__ void shell_coefficients(const StepParams& P, double t
     }
 }
 
+// Sites site0 .. site1 - 1 (the whole lattice, or a band of rows of a slab).
 __global__ void __launch_bounds__(SITE_BLOCK)
 step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P,
-                 int* __restrict__ flag) {
+                 int* __restrict__ flag, int site0, int site1) {
     const int Lx = P.Lx, Ly = P.Ly;
-    const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;
-    if (site >= Lx * Ly) return;
+    const int site = site0 + blockIdx.x * SITE_BLOCK + threadIdx.x;
+    if (site >= site1) return;
     const int y = row_of(site, P);
     const int x = site - y * Lx;
     const long long plane = P.plane;
@@ -484,7 +485,16 @@ inline int site_blocks(const StepParams& P) {
 
 cudaError_t launch_step_fp64(const double* src, double* dst, const StepParams& P, int* flag,
                              cudaStream_t s) {
-    step_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag);
+    step_fp64_kernel<<<site_blocks(P), SITE_BLOCK, 0, s>>>(src, dst, P, flag, 0, P.Lx * P.Ly);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_fp64_rows(const double* src, double* dst, const StepParams& P, int* flag,
+                                  int row0, int row1, cudaStream_t s) {
+    if (row1 <= row0) return cudaSuccess;
+    const int n = (row1 - row0) * P.Lx;
+    step_fp64_kernel<<<(n + SITE_BLOCK - 1) / SITE_BLOCK, SITE_BLOCK, 0, s>>>(src, dst, P, flag, row0 * P.Lx,
+                                                                             row1 * P.Lx);
     return cudaGetLastError();
 }
 

@@ -123,6 +123,11 @@ def lib() -> C.CDLL:
         L.lb_learned_stats.argtypes = [vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                        C.POINTER(C.c_double)]
         L.lb_learned_tiles.argtypes = [vp, vp, C.c_int]
+        L.lb_init_slab.argtypes = [C.POINTER(lb_params), C.c_int, vp, vp, vp, vp, C.POINTER(vp)]
+        L.lb_slab_step.argtypes = [vp, C.c_int]
+        L.lb_slab_pack.argtypes = [vp, C.c_int, vp]
+        L.lb_slab_unpack.argtypes = [vp, C.c_int, vp]
+        L.lb_slab_exchange.argtypes = [vp, vp]
         _lib = L
     return _lib
 
@@ -251,6 +256,7 @@ class Lattice:
     wall_mode: object = "rest"
     rt_ratio: object = None  # set (with rt_seed) to initialise through lb_init_rt instead of fields
     rt_seed: int = 0
+    cuts: int = 0            # a slab of a larger lattice (include/lb_slab.h): bit 0 cut below, bit 1 above
 
     def __post_init__(self):
         import torch
@@ -272,7 +278,10 @@ class Lattice:
         self._params = make_params(self.Lx, self.Ly, self.tau, self.gx, self.gy, self.T_top,
                                    self.T_bottom, self.y_periodic, prec, sh, ws_ptr,
                                    nbytes if ws_ptr else 0, wall_mode=self.wall_mode)
-        if fields is None:
+        if self.cuts:
+            check(lib().lb_init_slab(C.byref(self._params), int(self.cuts), *[_ptr(f) for f in fields],
+                                     C.byref(self._ctx)), "lb_init_slab")
+        elif fields is None:
             check(lib().lb_init_rt(C.byref(self._params), float(self.rt_ratio),
                                    int(self.rt_seed) & ((1 << 64) - 1), C.byref(self._ctx)), "lb_init_rt")
             R = float(self.rt_ratio)
@@ -389,6 +398,18 @@ class Lattice:
         check(lib().lb_learned_stats(self._ctx, C.byref(a), C.byref(b), C.byref(r)), "lb_learned_stats")
         return {"tiles_checked": a.value, "tiles_fallback": b.value, "max_residual": r.value}
 
+    def slab_step(self, part: int = 0) -> None:
+        """One step of a slab (0 whole, 1 the rows next to its cuts, 2 the rest; lb_slab_step)."""
+        check(lib().lb_slab_step(self._ctx, int(part)), "lb_slab_step")
+
+    def slab_pack(self, side: int, buf) -> None:
+        """The rows sent across side (0 below, 1 above) into a CUDA tensor of 26 x Lx elements."""
+        check(lib().lb_slab_pack(self._ctx, int(side), buf.data_ptr()), "lb_slab_pack")
+
+    def slab_unpack(self, side: int, buf) -> None:
+        """The neighbour's packed rows into the ghost rows at side (0 below, 1 above)."""
+        check(lib().lb_slab_unpack(self._ctx, int(side), buf.data_ptr()), "lb_slab_unpack")
+
     def learned_tiles(self) -> np.ndarray:
         """Per-tile decisions [Ly/32, Lx/32] (1 = fell back to the plain collide at the last check)."""
         out = np.zeros((self.Ly // 32, self.Lx // 32), np.uint8)
@@ -483,6 +504,11 @@ def probe_fma(kind: str, blocks: int, threads: int, iters: int, out, stream=None
     k = {"fp64": 0, "fp32": 1, "fp64_varying": 2}[kind]
     sh = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else stream)
     check(lib().lb_probe_fma(k, sh, blocks, threads, iters, out.data_ptr()), "lb_probe_fma")
+
+
+def slab_exchange(lo: "Lattice", hi: "Lattice") -> None:
+    """Ghost rows across the cut between slab lo (below) and slab hi (above), device to device."""
+    check(lib().lb_slab_exchange(lo._ctx, hi._ctx), "lb_slab_exchange")
 
 
 def probe_wait(limit_ns: int, arrive: bool, stream=None):
