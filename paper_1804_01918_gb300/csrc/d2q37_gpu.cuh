@@ -23,6 +23,10 @@ constexpr int NPAIR = 18;
 constexpr int NSHELL = 8;
 constexpr int HALO = 3;
 constexpr double DIM = 2.0;
+// Domain of the FP64 step's fixed-point pair terms (step_fp64.cu): |u*_x|, |u*_y| <= 0.2, i.e.
+// |lambda r u*| components <= 0.25 r 0.2, and |h| = |T* - 1| / 2 <= 0.2 (T* in [0.6, 1.4]).
+constexpr double FX_UMAX = 0.2;
+constexpr double FX_HB = 0.2;
 
 // Tables are constexpr functions (usable in host code, device code and constant expressions).
 // Lattice vectors of populations 0..18; 19..36 are their negatives.
@@ -111,6 +115,9 @@ struct StepParams {
     // FP64 step (relax_site_terms, lambda = 1/4): lambda r^2, lambda r tau g, (dT_force - 1) / 2,
     // -1 / (4 lambda^2 r^2), 2^-48 / tau
     double lr2, lrtgx, lrtgy, hdT, mu4, om48;
+    // bit patterns of the fixed-point pair terms' domain bounds (step_fp64.cu, fxp): |lambda r u*|
+    // components <= FX_UB, |h| <= FX_HB
+    unsigned long long fx_ub, fx_hb;
     double T_bot, T_top;   // wall temperatures below row 0 and above row Ly - 1
     ShellCoef sh[NSHELL];
     double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population

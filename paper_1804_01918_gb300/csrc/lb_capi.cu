@@ -144,6 +144,11 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
     sp.hdT = 0.5 * (sp.dT_force - 1.0);
     sp.mu4 = -1.0 / (4.0 * lambda * lambda * sp.r2);
     sp.om48 = std::ldexp(sp.omega, -48);
+    {
+        const double ub = 0.25 * r * FX_UMAX, hb = FX_HB;
+        std::memcpy(&sp.fx_ub, &ub, 8);
+        std::memcpy(&sp.fx_hb, &hb, 8);
+    }
     sp.r_f = (float)sp.r;
     sp.r2_f = (float)sp.r2;
     sp.omega_f = (float)sp.omega;

@@ -146,6 +146,7 @@ struct Relax64 {
     double U1, V1, U1s, V1s;  // lambda r u*_x, lambda r u*_y and their squares
     double B11[2], S11[2];    // beta and beta^2 of the pairs (1, 1) and (1, -1)
     double rw, t, Rb, P1, P2, R0h;  // site terms of the shell coefficients
+    double h;                 // (T* - 1) / 2
     double X;                 // temperature_sum: T = r^2 X / (2 n0) before the forcing shift
 };
 
@@ -167,9 +168,10 @@ __device__ __forceinline__ double temperature_sum(const SiteSums& s, double a) {
     return fma(-a, fma(s.nx, s.nx, s.ny * s.ny), s.ne);
 }
 
-// The site terms (everything shared by the shells).
+// The site terms (everything shared by the shells); rw = rho / tau, or that factor times a power of
+// two (the fixed-point path below), which every term that carries it then carries too.
 __device__ __forceinline__ void relax_site_terms(const StepParams& P, const SiteSums& s, double a,
-                                                 Relax64& R) {
+                                                 double rw, Relax64& R) {
     const double k = P.lr2 * a;                        // lambda r^2 / N0
     R.U1 = fma(s.nx, k, P.lrtgx);                      // lambda r u*_x
     R.V1 = fma(s.ny, k, P.lrtgy);
@@ -177,7 +179,8 @@ __device__ __forceinline__ void relax_site_terms(const StepParams& P, const Site
     R.V1s = R.V1 * R.V1;
     const double h = fma(R.X, k, P.hdT);               // (T* - 1) / 2
     const double m = fma(R.U1s + R.V1s, P.mu4, 0.5);   // 1/2 - |u*|^2 / 4
-    R.rw = s.n0 * P.om48;                              // rho / tau
+    R.rw = rw;                                         // rho / tau (times 2^-E)
+    R.h = h;
     R.t = R.rw * h;
     const double bq = fma(h, -2.0, m);                 // m - 2h
     R.Rb = R.rw * bq;
@@ -288,6 +291,172 @@ __device__ __forceinline__ void relax_all(const double* f, const StepParams& P, 
     relax_shell<7>(f, P, R, store);
 }
 
+// ---- the pair terms in fixed point on the integer pipe --------------------------------------
+// GB300's FP64 pipe issues two instructions per clock per SM and binds this kernel; 64-bit integer
+// multiplies and adds run on the integer pipes at many times that rate. So, inside a domain of
+// moderate velocities and temperatures, each pair's equilibrium term G(+-c) = WA0 + b^2 e2 +- b q
+// (relax_pair) is formed in two's-complement fixed point from the shell's FP64 coefficients, and
+// only f' = (1 - 1/tau) f + G runs on the FP64 pipe: 2 FP64 instructions per pair instead of 7.
+//   - b = lambda xi.u* (beta on the rescaled shells) in Q.64 (value x 2^64; |b| < 1/2), b^2 the
+//     high word of b b (Q.64);
+//   - two units per shell S: the coarse 2^-C(S) for k WB1, DA, k^3 C and q = WB1 + hi(CO b^2),
+//     e2 = k q + DA (large numbers that only enter multiplied by b or b^2), and the fine 2^-F(S)
+//     for WA0 and G; the products b^2 e2 and b q are taken from the exact 128-bit product F(S) -
+//     C(S) bits below its high word, so G = WA0 + b^2 e2 +- b q keeps the fine unit;
+//   - rho / tau = mant 2^E with mant in [1, 2): the FP64 site terms carry mant, and 2^E is applied
+//     when G is rounded to FP64 (from_fixed; the rest population by an exponent shift).
+// C(S) and F(S) are the largest scales that keep every intermediate of shell S below 2^61 over the
+// domain |u*_x|, |u*_y| <= FX_UMAX and |T* - 1| / 2 <= FX_HB (bounds of the polynomials of
+// shell_relax and relax_pair over that box, density factor below 2). Evaluated exactly in integer
+// arithmetic against rational arithmetic, G then has the relative error of its final rounding
+// (<= 2.2e-16 in the Rayleigh-Taylor and strong-flow regimes; the FP64 evaluation: 4e-16 - 6e-16).
+// A site outside the domain takes the FP64 evaluation.
+namespace fxp {
+
+__host__ __device__ constexpr int coarse_of(int s) {
+    constexpr int t[NSHELL] = {0, 59, 60, 59, 64, 63, 63, 67};
+    return t[s];
+}
+__host__ __device__ constexpr int fine_of(int s) {
+    constexpr int t[NSHELL] = {0, 62, 63, 64, 65, 67, 69, 68};
+    return t[s];
+}
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
+}
+
+// The domain test on bit patterns (integer compares; NaN fails it). P.fx_ub / P.fx_hb hold the bit
+// patterns of lambda r FX_UMAX and FX_HB (set on the host).
+__device__ __forceinline__ bool in_domain(const StepParams& P, const Relax64& R) {
+    return abs_bits(R.U1) <= P.fx_ub && abs_bits(R.V1) <= P.fx_ub && abs_bits(R.h) <= P.fx_hb;
+}
+
+// v 2^S as a two's-complement integer, truncated toward zero (|v| 2^S < 2^62 in the domain).
+template <int S>
+__device__ __forceinline__ long long to_fixed(double v) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (e ? 0x0010000000000000ull : 0ull);
+    const int sh = e - 1075 + S;  // v 2^S = m 2^sh
+    const unsigned long long r = sh >= 0 ? (m << min(sh, 63)) : (m >> min(-sh, 63));
+    return (long long)b < 0 ? -(long long)r : (long long)r;
+}
+
+// g 2^-s rounded to FP64 (to nearest, ties to even), on the integer pipe.
+__device__ __forceinline__ double from_fixed(long long g, int s) {
+    const unsigned long long sign = (unsigned long long)g & 0x8000000000000000ull;
+    const unsigned long long u = g < 0 ? (unsigned long long)(-g) : (unsigned long long)g;
+    const int z = __clzll((long long)u);                    // 64 only for g = 0
+    const unsigned long long w = u << (z & 63);             // leading one at bit 63
+    const unsigned long long t = w >> 10;                   // 53 bits and the round bit
+    const unsigned long long x = ((w & 0x3FFull) != 0ull ? 1ull : 0ull) | ((t >> 1) & 1ull);
+    const unsigned long long sig = (t + x) >> 1;            // implicit one at bit 52 (or a carry)
+    const unsigned long long e1 = (unsigned long long)(1085 - z - s);  // biased exponent - 1
+    const unsigned long long bits = ((e1 << 52) + sig) | sign;
+    return z == 64 ? 0.0 : __longlong_as_double((long long)bits);
+}
+
+// floor(a b 2^-64): the high word of the 128-bit product.
+__device__ __forceinline__ long long hi(long long a, long long b) { return __mul64hi(a, b); }
+
+// floor(a b 2^(D - 64)): the 128-bit product D bits below its high word (fits by the bounds).
+template <int D>
+__device__ __forceinline__ long long prod_at(long long a, long long b) {
+    if constexpr (D == 0) {
+        return __mul64hi(a, b);
+    } else {
+        const unsigned long long h = (unsigned long long)__mul64hi(a, b);
+        const unsigned long long l = (unsigned long long)a * (unsigned long long)b;
+        return (long long)((h << D) | (l >> (64 - D)));
+    }
+}
+
+// Q.64 pair variables of the site: U = lambda r u*_x, V = lambda r u*_y, U +- V.
+struct Base {
+    long long U, V, P, M;
+};
+
+template <int I>
+__device__ __forceinline__ long long pair_b(const Base& B) {
+    constexpr int cx = cxh(I), cy = cyh(I);
+    if constexpr (cy == 0) return B.U;
+    else if constexpr (cx == 0) return B.V;
+    else if constexpr (cx == cy) return B.P;
+    else if constexpr (cx == -cy) return B.M;
+    else if constexpr (cx == 1) return B.U + (long long)cy * B.V;
+    else return (long long)cx * B.U + (cy > 0 ? B.V : -B.V);
+}
+
+}  // namespace fxp
+
+// Shell S's coefficients: WA0 in the fine unit, the others in the coarse unit.
+struct ShellFx {
+    long long WA0, WB1, DA, CO;
+};
+
+template <int I, class Store>
+__device__ __forceinline__ void relax_pair_fx(const double* f, const fxp::Base& B, const ShellFx& c,
+                                              double omc, int s, Store& store) {
+    using namespace fxp;
+    constexpr int S = shellh(I);
+    constexpr int D = fine_of(S) - coarse_of(S);
+    constexpr long long k = shell_kappa(S);
+    const long long b = pair_b<I>(B);
+    const long long b2 = hi(b, b);
+    const long long q = c.WB1 + hi(c.CO, b2);
+    const long long e2 = k * q + c.DA;
+    const long long we = c.WA0 + prod_at<D>(b2, e2);
+    const long long bq = prod_at<D>(b, q);
+    store(I, fma(omc, f[I], from_fixed(we + bq, s)));
+    store(I + NPAIR, fma(omc, f[I + NPAIR], from_fixed(we - bq, s)));
+}
+
+template <int S, int N>
+struct ShellPairsFx {
+    template <class Store>
+    __device__ __forceinline__ static void run(const double* f, const fxp::Base& B, const ShellFx& c, double omc,
+                                               int s, Store& store) {
+        ShellPairsFx<S, N - 1>::run(f, B, c, omc, s, store);
+        if constexpr (shellh(N) == S) relax_pair_fx<N>(f, B, c, omc, s, store);
+    }
+};
+template <int S>
+struct ShellPairsFx<S, 0> {
+    template <class Store>
+    __device__ __forceinline__ static void run(const double*, const fxp::Base&, const ShellFx&, double, int,
+                                               Store&) {}
+};
+
+template <int S, class Store>
+__device__ __forceinline__ void relax_shell_fx(const double* f, const StepParams& P, const Relax64& R,
+                                               const fxp::Base& B, int E, Store& store) {
+    using namespace fxp;
+    const ShellRelax c = shell_relax<S>(P, R);
+    const ShellFx x{to_fixed<fine_of(S)>(c.WA0), to_fixed<coarse_of(S)>(c.WB1), to_fixed<coarse_of(S)>(c.DA),
+                    to_fixed<coarse_of(S)>(c.CO)};
+    ShellPairsFx<S, NPAIR>::run(f, B, x, P.omc, fine_of(S) - E, store);
+}
+
+// All 37 populations with the pair terms in fixed point (site terms carrying 2^-E, see above).
+template <class Store>
+__device__ __forceinline__ void relax_all_fx(const double* f, const StepParams& P, const Relax64& R, int E,
+                                             Store& store) {
+    using namespace fxp;
+    // rest population: the shell-0 term (a positive normal number) scaled back by 2^E in its exponent
+    const double g0 = P.sh[0].q_a0 * R.R0h;
+    store(0, fma(P.omc, f[0], __longlong_as_double(__double_as_longlong(g0) + ((long long)E << 52))));
+    const long long U = to_fixed<64>(R.U1), V = to_fixed<64>(R.V1);
+    const Base B{U, V, U + V, U - V};
+    relax_shell_fx<1>(f, P, R, B, E, store);
+    relax_shell_fx<3>(f, P, R, B, E, store);
+    relax_shell_fx<6>(f, P, R, B, E, store);
+    relax_shell_fx<2>(f, P, R, B, E, store);
+    relax_shell_fx<5>(f, P, R, B, E, store);
+    relax_shell_fx<4>(f, P, R, B, E, store);
+    relax_shell_fx<7>(f, P, R, B, E, store);
+}
+
 // Collide site (x, y) with populations f (Sec. 3: moments, shifted equilibrium, BGK relaxation):
 // store(i, o, v) writes population i at element offset o of its plane (the site's own offset,
 // then the wall halo rows the site feeds). Shared by the fused step and the collide kernel, so the
@@ -301,11 +470,22 @@ __device__ __forceinline__ void collide_site(const double* f, const StepParams& 
     Relax64 R;
     R.X = temperature_sum(s, a);
     if (bad_positive(s.n0) || bad_positive(R.X) || bad) atomicOr(flag, bad ? bad : 1);
-    relax_site_terms(P, s, a, R);
+    // rho / tau = mant 2^E, mant in [1, 2): the site terms carry mant, the pair terms' conversion
+    // back to FP64 adds E to the exponent
+    const double rw = s.n0 * P.om48;
+    const unsigned long long rb = (unsigned long long)__double_as_longlong(rw);
+    const int E = (int)((rb >> 52) & 0x7FFu) - 1023;
+    relax_site_terms(P, s, a, __longlong_as_double((long long)((rb & 0x000FFFFFFFFFFFFFull) | 0x3FF0000000000000ull)),
+                     R);
 
     const long long o = (long long)(y + HALO) * P.Lx + x;
     auto own = [&](int i, double v) { store(i, o, v); };
-    relax_all(f, P, R, own);
+    if (fxp::in_domain(P, R)) {
+        relax_all_fx(f, P, R, E, own);
+    } else {  // outside the fixed-point formats: the FP64 evaluation with rho / tau itself
+        relax_site_terms(P, s, a, rw, R);
+        relax_all(f, P, R, own);
+    }
 
     // wall halo rows from this site's post-collision fields (rho, u + g, T)
     if (!P.y_periodic && (y < HALO || y >= P.Ly - HALO)) {
@@ -334,8 +514,10 @@ __device__ __forceinline__ void shell_coefficients(const StepParams& P, double t
     }
 }
 
-// Sites site0 .. site1 - 1 (the whole lattice, or a band of rows of a slab).
-__global__ void __launch_bounds__(SITE_BLOCK)
+// Sites site0 .. site1 - 1 (the whole lattice, or a band of rows of a slab). Three blocks (12 warps)
+// per SM: the register cap that keeps the occupancy of the FP64-only version.
+constexpr int STEP_BLOCKS_PER_SM = 3;
+__global__ void __launch_bounds__(SITE_BLOCK, STEP_BLOCKS_PER_SM)
 step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P,
                  int* __restrict__ flag, int site0, int site1) {
     const int Lx = P.Lx, Ly = P.Ly;
@@ -355,7 +537,7 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
 // reads the 37 populations of its own site, relaxes them exactly as the fused step does, writes
 // them back, and on rows 0..2 and Ly-3..Ly-1 writes the wall halo rows. After propagate this gives
 // the same populations, bit for bit, as one fused step.
-__global__ void __launch_bounds__(SITE_BLOCK)
+__global__ void __launch_bounds__(SITE_BLOCK, STEP_BLOCKS_PER_SM)
 collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict__ flag) {
     const int Lx = P.Lx, Ly = P.Ly;
     const int site = blockIdx.x * SITE_BLOCK + threadIdx.x;

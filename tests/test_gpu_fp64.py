@@ -310,6 +310,29 @@ def test_strong_flow_matches_oracle(L, orc, tau):
     assert np.max(np.abs(got - want) / w) <= TOL
 
 
+@pytest.mark.parametrize("tau", [0.6, 1.7])
+def test_fixed_point_domain_edge_and_fallback_match_oracle(L, orc, tau):
+    """Sites on both sides of the fixed-point pair terms' domain (|u*| components <= 0.2, T* in
+    [0.6, 1.4]; outside it the FP64 evaluation runs) mixed within every warp: uncorrelated
+    velocities up to 0.3 per component and temperatures 0.45-1.55. After 5 steps every population
+    agrees with the oracle within 1e-12 of its weight."""
+    Lx, Ly = 64, 24
+    st = inputs.random_state(Lx, Ly, seed=11, du=0.3, dT=0.55, drho=0.2)
+    lat = L.Lattice(Lx, Ly, tau, st.rho, st.ux, st.uy, st.T, gx=1e-3, gy=-2e-3, T_top=0.8,
+                    T_bottom=1.2)
+    lat.step(5)
+    lat.sync()
+    got = gpu_to_oracle(L, orc, lat.get_populations())
+    lat.close()
+    want = orc.run(orc.init_fields(st), tau=tau, nsteps=5, gx=1e-3, gy=-2e-3, T_top=0.8, T_bottom=1.2)
+    _, _, w, _ = orc.velocity_set()
+    inside = (np.abs(st.ux) <= 0.2) & (np.abs(st.uy) <= 0.2) & (np.abs(st.T - 1.0) <= 0.4)
+    assert 0.2 < inside.mean() < 0.8            # both paths, within warps
+    err = float(np.max(np.abs(got - want) / w))
+    print(f"fixed-point domain edge, tau {tau}: max |f - f_oracle| / w = {err:.2e}")
+    assert err <= TOL
+
+
 @pytest.mark.parametrize("wall_mode", ["rest", "mirror"])
 def test_fused_step_matches_oracle_over_1000_steps(L, orc, wall_mode):
     """Ten times the bar's horizon: the rounding differences between the kernel (exact integer
