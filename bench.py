@@ -36,44 +36,44 @@ if ROOT not in sys.path:
 
 LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
 NPOP = 37
-# FP64 work of the fused step per site in this kernel's formulation: 116.2 FP64-pipe instructions
-# (80.0 fused + 36.1 non-fused; ncu on step_fp64_kernel, per site), i.e. 196 flops with FMA = 2.
+# FP64 work of the fused step per site in this kernel's formulation: 121.2 FP64-pipe instructions
+# (79.0 fused + 42.1 non-fused; ncu on step_fp64_kernel, per site), i.e. 200 flops with FMA = 2.
 # The moment sums run as exact 96-bit integer sums on the integer pipe, rounded to FP64 there too,
 # and each pair's equilibrium term is formed in 64-bit fixed point there (one FP64 FMA per
 # population remains). The FP64 pipe issues one such instruction per lane-slot whatever its kind, so the
 # ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per SM x f_max (the 1.25 TFLOP/s
 # nominal FP64 rate counts an FMA as 2 flops).
-FP64_INST_PER_SITE = 116.2
-FP64_FLOP_PER_SITE = 196
+FP64_INST_PER_SITE = 121.2
+FP64_FLOP_PER_SITE = 200
 # The kernel sources those counts were profiled on (code_digest, below): when the code differs the
 # counts are stale and the roofline's achieved and frac are reported as null
 # (tests/test_bench_host.py fails on a stale table, so a committed tree carries matching counts).
-FP64_INST_SOURCES = {"step_fp64.cu": "9750f88e4bc46a30b605abd8b470cbbf8c8ee20e75d6119df7a6a3030fa920f9",
+FP64_INST_SOURCES = {"step_fp64.cu": "52ba4f0b1ceb5de2353b8c8fdd7e5ce41a47cb7b8b1d7de6a1c08c7a1de0c27e",
                      "d2q37_gpu.cuh": "018be3fc24d2d1e111a0b0f60ca97bbfb4f70db6005580ca2c81518bc54328ce",
                      "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}
 # The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
 # equilibrium written per population, BGK relaxation with the gravity shift): 2763 flops, counted
 # by compiling the oracle's collide with an operation-counting scalar type
 # (oracle/count_collide_flops.cpp; tests/test_oracle_flops.py re-derives the number). The
-# kernel's factored formulation needs 196 of them in FP64 (the rest runs on the integer pipe).
+# kernel's factored formulation needs 200 of them in FP64 (the rest runs on the integer pipe).
 ORACLE_FLOP_PER_SITE = 2763
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 FP64_INST_PER_CLK_SM = 2
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 698.488 MB + 645.861 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# 698.478 MB + 691.452 MB for 2359296 sites, scaled per site. Valid only for the kernel source
 # it was taken on (code_digest of the files below: sha256 of the code without comments);
 # otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (698.488064e6 + 645.860864e6) / 2359296,
-                "sources": {"step_fp64.cu": "9750f88e4bc46a30b605abd8b470cbbf8c8ee20e75d6119df7a6a3030fa920f9",
+TRAFFIC_FP64 = {"bytes_per_site": (698.478336e6 + 691.451904e6) / 2359296,
+                "sources": {"step_fp64.cu": "52ba4f0b1ceb5de2353b8c8fdd7e5ce41a47cb7b8b1d7de6a1c08c7a1de0c27e",
                             "d2q37_gpu.cuh": "018be3fc24d2d1e111a0b0f60ca97bbfb4f70db6005580ca2c81518bc54328ce",
                             "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}}
 
 
 # The same for step_fp32split_kernel: ncu DRAM bytes of one launch on a 1152x2048 capture
-# (profiles/step_fp32split_1152x2048_full.md), 349.265 MB + 303.084 MB for 2359296 sites.
-TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.264640e6 + 303.084288e6) / 2359296,
+# (profiles/step_fp32split_1152x2048_full.md), 349.264 MB + 303.117 MB for 2359296 sites.
+TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.264128e6 + 303.117056e6) / 2359296,
                      "sources": {"step_fp32dev.cu": "9bd8776f652ce5402527ff8a5eb09373b1db75d7a1be4418d81624f303f67877",
                                  "site_fp32dev.cuh": "ed58b9d3cc6f5e6464749fb716c6985c34642f9abdd0ca704ee46d6a60204ae1",
                                  "d2q37_gpu.cuh": "018be3fc24d2d1e111a0b0f60ca97bbfb4f70db6005580ca2c81518bc54328ce"}}

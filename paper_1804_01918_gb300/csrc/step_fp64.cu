@@ -80,29 +80,55 @@ struct SiteSums {
     double n0, nx, ny, ne;
 };
 
-__device__ __forceinline__ SiteSums site_sums(const double* f, int* bad) {
-    using namespace fx;
-    I96 bx[7], by[7];
+// The moment sums as an accumulator over populations given one at a time (add<I>), so that a caller
+// can take the populations in batches.
+struct SumBins {
+    fx::I96 bx[7], by[7];
+    unsigned emax;
+    __device__ __forceinline__ void init() {
 #pragma unroll
-    for (int k = 0; k < 7; ++k) bx[k] = by[k] = zero96();
-    unsigned emax = 0u;
-#pragma unroll
-    for (int i = 0; i < NPOP; ++i) {
-        const I96 n = to96(f[i], emax);
-        add96(bx[cx_of(i) + 3], n);
-        add96(by[cy_of(i) + 3], n);
+        for (int k = 0; k < 7; ++k) bx[k] = by[k] = fx::zero96();
+        emax = 0u;
     }
-    *bad = emax == 0x7FFu ? 1 : (emax > EXP_LIMIT ? 2 : 0);
-    const I96 px1 = plus96(bx[4], bx[2]), px2 = plus96(bx[5], bx[1]), px3 = plus96(bx[6], bx[0]);
-    const I96 py1 = plus96(by[4], by[2]), py2 = plus96(by[5], by[1]), py3 = plus96(by[6], by[0]);
-    const I96 n0 = plus96(plus96(bx[3], px1), plus96(px2, px3));
-    const I96 nx = plus96(plus96(times3(minus96(bx[6], bx[0])), times2(minus96(bx[5], bx[1]))),
-                          minus96(bx[4], bx[2]));
-    const I96 ny = plus96(plus96(times3(minus96(by[6], by[0])), times2(minus96(by[5], by[1]))),
-                          minus96(by[4], by[2]));
-    const I96 ne = plus96(plus96(plus96(times9(px3), times4(px2)), px1),
-                          plus96(plus96(times9(py3), times4(py2)), py1));
-    return SiteSums{to_double48(n0), to_double48(nx), to_double48(ny), to_double48(ne)};
+    template <int I>
+    __device__ __forceinline__ void add(double v) {
+        const fx::I96 n = fx::to96(v, emax);
+        fx::add96(bx[cx_of(I) + 3], n);
+        fx::add96(by[cy_of(I) + 3], n);
+    }
+    __device__ __forceinline__ SiteSums finish(int* bad) const {
+        using namespace fx;
+        *bad = emax == 0x7FFu ? 1 : (emax > EXP_LIMIT ? 2 : 0);
+        const I96 px1 = plus96(bx[4], bx[2]), px2 = plus96(bx[5], bx[1]), px3 = plus96(bx[6], bx[0]);
+        const I96 py1 = plus96(by[4], by[2]), py2 = plus96(by[5], by[1]), py3 = plus96(by[6], by[0]);
+        const I96 n0 = plus96(plus96(bx[3], px1), plus96(px2, px3));
+        const I96 nx = plus96(plus96(times3(minus96(bx[6], bx[0])), times2(minus96(bx[5], bx[1]))),
+                              minus96(bx[4], bx[2]));
+        const I96 ny = plus96(plus96(times3(minus96(by[6], by[0])), times2(minus96(by[5], by[1]))),
+                              minus96(by[4], by[2]));
+        const I96 ne = plus96(plus96(plus96(times9(px3), times4(px2)), px1),
+                              plus96(plus96(times9(py3), times4(py2)), py1));
+        return SiteSums{to_double48(n0), to_double48(nx), to_double48(ny), to_double48(ne)};
+    }
+};
+
+template <int I>
+struct AddAll {
+    __device__ __forceinline__ static void run(SumBins& b, const double* f) {
+        AddAll<I - 1>::run(b, f);
+        b.add<I>(f[I]);
+    }
+};
+template <>
+struct AddAll<-1> {
+    __device__ __forceinline__ static void run(SumBins&, const double*) {}
+};
+
+__device__ __forceinline__ SiteSums site_sums(const double* f, int* bad) {
+    SumBins b;
+    b.init();
+    AddAll<NPOP - 1>::run(b, f);
+    return b.finish(bad);
 }
 
 struct SiteMoments {
@@ -122,6 +148,50 @@ __device__ __forceinline__ SiteMoments site_moments(const double* f, double r, d
     const double u2 = m.ux * m.ux + m.uy * m.uy;
     m.T = 0.5 * fma(r2 * inv, s.ne, -u2);
     return m;
+}
+
+// Populations A .. B of the pull for (x, y), loaded together, then each added to the sums and
+// written to the thread's shared-memory column fs[i * SITE_BLOCK] (population 0 kept in *f0).
+template <int A, int I, int B>
+__device__ __forceinline__ void batch_load(const double* __restrict__ src, double* g, int x, int y, int Lx, int Ly,
+                                           int yp, long long plane) {
+    if constexpr (I <= B) {
+        g[I - A] = __ldg(src + plane_off(I, plane) + pull_index<I>(x, y, Lx, Ly, yp));
+        batch_load<A, I + 1, B>(src, g, x, y, Lx, Ly, yp, plane);
+    }
+}
+template <int A, int I, int B>
+__device__ __forceinline__ void batch_add(SumBins& acc, const double* g, double* fs, double* f0) {
+    if constexpr (I <= B) {
+        acc.add<I>(g[I - A]);
+        if constexpr (I == 0)
+            *f0 = g[0];
+        else
+            fs[I * SITE_BLOCK] = g[I - A];
+        batch_add<A, I + 1, B>(acc, g, fs, f0);
+    }
+}
+// The same for a site's own populations (the in-place collide): population i at site + i plane.
+template <int A, int I, int B>
+__device__ __forceinline__ void own_load(const double* site, double* g, long long plane) {
+    if constexpr (I <= B) {
+        g[I - A] = site[plane_off(I, plane)];
+        own_load<A, I + 1, B>(site, g, plane);
+    }
+}
+template <int A, int B>
+__device__ __forceinline__ void own_batch(const double* site, long long plane, SumBins& acc, double* fs, double* f0) {
+    double g[B - A + 1];
+    own_load<A, A, B>(site, g, plane);
+    batch_add<A, A, B>(acc, g, fs, f0);
+}
+
+template <int A, int B>
+__device__ __forceinline__ void pull_batch(const double* __restrict__ src, int x, int y, int Lx, int Ly, int yp,
+                                           long long plane, SumBins& acc, double* fs, double* f0) {
+    double g[B - A + 1];
+    batch_load<A, A, B>(src, g, x, y, Lx, Ly, yp, plane);
+    batch_add<A, A, B>(acc, g, fs, f0);
 }
 
 // The relaxation of one site toward the shifted equilibrium f_eq(rho, u*, T*), u* = u + tau g,
@@ -332,17 +402,6 @@ __device__ __forceinline__ bool in_domain(const StepParams& P, const Relax64& R)
     return abs_bits(R.U1) <= P.fx_ub && abs_bits(R.V1) <= P.fx_ub && abs_bits(R.h) <= P.fx_hb;
 }
 
-// v 2^S as a two's-complement integer, truncated toward zero (|v| 2^S < 2^62 in the domain).
-template <int S>
-__device__ __forceinline__ long long to_fixed(double v) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
-    const int e = (int)((b >> 52) & 0x7FFu);
-    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (e ? 0x0010000000000000ull : 0ull);
-    const int sh = e - 1075 + S;  // v 2^S = m 2^sh
-    const unsigned long long r = sh >= 0 ? (m << min(sh, 63)) : (m >> min(-sh, 63));
-    return (long long)b < 0 ? -(long long)r : (long long)r;
-}
-
 // g 2^-s rounded to FP64 (to nearest, ties to even), on the integer pipe.
 __device__ __forceinline__ double from_fixed(long long g, int s) {
     const unsigned long long sign = (unsigned long long)g & 0x8000000000000000ull;
@@ -357,104 +416,125 @@ __device__ __forceinline__ double from_fixed(long long g, int s) {
     return z == 64 ? 0.0 : __longlong_as_double((long long)bits);
 }
 
+// v 2^S as a two's-complement integer, truncated toward zero (|v| 2^S < 2^62 in the domain).
+__device__ __forceinline__ long long to_fixed_rt(double v, int S) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    const int e = (int)((b >> 52) & 0x7FFu);
+    const unsigned long long m = (b & 0x000FFFFFFFFFFFFFull) | (e ? 0x0010000000000000ull : 0ull);
+    const int sh = e - 1075 + S;  // v 2^S = m 2^sh
+    const unsigned long long r = sh >= 0 ? (m << min(sh, 63)) : (m >> min(-sh, 63));
+    return (long long)b < 0 ? -(long long)r : (long long)r;
+}
+
 // floor(a b 2^-64): the high word of the 128-bit product.
 __device__ __forceinline__ long long hi(long long a, long long b) { return __mul64hi(a, b); }
 
-// floor(a b 2^(D - 64)): the 128-bit product D bits below its high word (fits by the bounds).
-template <int D>
-__device__ __forceinline__ long long prod_at(long long a, long long b) {
-    if constexpr (D == 0) {
-        return __mul64hi(a, b);
-    } else {
-        const unsigned long long h = (unsigned long long)__mul64hi(a, b);
-        const unsigned long long l = (unsigned long long)a * (unsigned long long)b;
-        return (long long)((h << D) | (l >> (64 - D)));
-    }
-}
-
-// Q.64 pair variables of the site: U = lambda r u*_x, V = lambda r u*_y, U +- V.
-struct Base {
-    long long U, V, P, M;
-};
-
-template <int I>
-__device__ __forceinline__ long long pair_b(const Base& B) {
-    constexpr int cx = cxh(I), cy = cyh(I);
-    if constexpr (cy == 0) return B.U;
-    else if constexpr (cx == 0) return B.V;
-    else if constexpr (cx == cy) return B.P;
-    else if constexpr (cx == -cy) return B.M;
-    else if constexpr (cx == 1) return B.U + (long long)cy * B.V;
-    else return (long long)cx * B.U + (cy > 0 ? B.V : -B.V);
+// floor(a b 2^(D - 64)) for 1 <= D <= 63 given at run time.
+__device__ __forceinline__ long long prod_at_rt(long long a, long long b, int D) {
+    const unsigned long long h = (unsigned long long)__mul64hi(a, b);
+    const unsigned long long l = (unsigned long long)a * (unsigned long long)b;
+    return (long long)((h << D) | (l >> (64 - D)));
 }
 
 }  // namespace fxp
 
-// Shell S's coefficients: WA0 in the fine unit, the others in the coarse unit.
-struct ShellFx {
-    long long WA0, WB1, DA, CO;
+// The pairs in shell order with the coefficients of their pair variable (cx, cy) / kappa, and per
+// shell its first pair, kappa and fixed-point units: the tables of the rolled pair loop below.
+struct PairTable {
+    int pop[NPAIR], bx[NPAIR], by[NPAIR];
+    int first[NSHELL + 1], kappa[NSHELL], coarse[NSHELL], fine[NSHELL];
 };
-
-template <int I, class Store>
-__device__ __forceinline__ void relax_pair_fx(const double* f, const fxp::Base& B, const ShellFx& c,
-                                              double omc, int s, Store& store) {
-    using namespace fxp;
-    constexpr int S = shellh(I);
-    constexpr int D = fine_of(S) - coarse_of(S);
-    constexpr long long k = shell_kappa(S);
-    const long long b = pair_b<I>(B);
-    const long long b2 = hi(b, b);
-    const long long q = c.WB1 + hi(c.CO, b2);
-    const long long e2 = k * q + c.DA;
-    const long long we = c.WA0 + prod_at<D>(b2, e2);
-    const long long bq = prod_at<D>(b, q);
-    store(I, fma(omc, f[I], from_fixed(we + bq, s)));
-    store(I + NPAIR, fma(omc, f[I + NPAIR], from_fixed(we - bq, s)));
-}
-
-template <int S, int N>
-struct ShellPairsFx {
-    template <class Store>
-    __device__ __forceinline__ static void run(const double* f, const fxp::Base& B, const ShellFx& c, double omc,
-                                               int s, Store& store) {
-        ShellPairsFx<S, N - 1>::run(f, B, c, omc, s, store);
-        if constexpr (shellh(N) == S) relax_pair_fx<N>(f, B, c, omc, s, store);
+__host__ __device__ constexpr PairTable make_pair_table() {
+    // (the rolled loop takes the pairs of a shell two at a time: every shell has 2 or 4)
+    PairTable t{};
+    int n = 0;
+    for (int S = 0; S < NSHELL; ++S) {
+        t.first[S] = n;
+        t.kappa[S] = shell_kappa(S);
+        t.coarse[S] = fxp::coarse_of(S);
+        t.fine[S] = fxp::fine_of(S);
+        for (int I = 1; I <= NPAIR; ++I)
+            if (shellh(I) == S) {
+                t.pop[n] = I;
+                t.bx[n] = cxh(I) / shell_kappa(S);
+                t.by[n] = cyh(I) / shell_kappa(S);
+                ++n;
+            }
     }
-};
-template <int S>
-struct ShellPairsFx<S, 0> {
-    template <class Store>
-    __device__ __forceinline__ static void run(const double*, const fxp::Base&, const ShellFx&, double, int,
-                                               Store&) {}
-};
-
-template <int S, class Store>
-__device__ __forceinline__ void relax_shell_fx(const double* f, const StepParams& P, const Relax64& R,
-                                               const fxp::Base& B, int E, Store& store) {
-    using namespace fxp;
-    const ShellRelax c = shell_relax<S>(P, R);
-    const ShellFx x{to_fixed<fine_of(S)>(c.WA0), to_fixed<coarse_of(S)>(c.WB1), to_fixed<coarse_of(S)>(c.DA),
-                    to_fixed<coarse_of(S)>(c.CO)};
-    ShellPairsFx<S, NPAIR>::run(f, B, x, P.omc, fine_of(S) - E, store);
+    t.first[NSHELL] = n;
+    return t;
 }
+__constant__ PairTable c_pairs = make_pair_table();
 
-// All 37 populations with the pair terms in fixed point (site terms carrying 2^-E, see above).
+// All 37 populations with the pair terms in fixed point (site terms carrying 2^-E, see above), as
+// one compact loop over shells and their pairs: the populations are read from the thread's column
+// fs[i * SITE_BLOCK] of the block's shared-memory copy, so one loop body serves every pair (the
+// fully unrolled form overflowed the instruction cache). f0 is the rest population.
 template <class Store>
-__device__ __forceinline__ void relax_all_fx(const double* f, const StepParams& P, const Relax64& R, int E,
-                                             Store& store) {
+__device__ __forceinline__ void relax_all_fx(const double* fs, double f0, const StepParams& P, const Relax64& R,
+                                             int E, Store& store) {
     using namespace fxp;
     // rest population: the shell-0 term (a positive normal number) scaled back by 2^E in its exponent
     const double g0 = P.sh[0].q_a0 * R.R0h;
-    store(0, fma(P.omc, f[0], __longlong_as_double(__double_as_longlong(g0) + ((long long)E << 52))));
-    const long long U = to_fixed<64>(R.U1), V = to_fixed<64>(R.V1);
-    const Base B{U, V, U + V, U - V};
-    relax_shell_fx<1>(f, P, R, B, E, store);
-    relax_shell_fx<3>(f, P, R, B, E, store);
-    relax_shell_fx<6>(f, P, R, B, E, store);
-    relax_shell_fx<2>(f, P, R, B, E, store);
-    relax_shell_fx<5>(f, P, R, B, E, store);
-    relax_shell_fx<4>(f, P, R, B, E, store);
-    relax_shell_fx<7>(f, P, R, B, E, store);
+    store(0, fma(P.omc, f0, __longlong_as_double(__double_as_longlong(g0) + ((long long)E << 52))));
+    const long long U = to_fixed_rt(R.U1, 64), V = to_fixed_rt(R.V1, 64);
+#pragma unroll 1
+    for (int S = 1; S < NSHELL; ++S) {
+        const ShellCoef& c = P.sh[S];
+        const long long k = c_pairs.kappa[S];
+        const double WA0 = fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h));
+        const double WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);          // k WB1
+        const double DA = fma(-c.q_e0, R.t, (double)k * WB1);        // k^2 (WA2 - WB1)
+        const double CO = c.q_co * R.rw;                              // k^3 C
+        const int sc = c_pairs.coarse[S], sf = c_pairs.fine[S], D = sf - sc;
+        const long long xA0 = to_fixed_rt(WA0, sf), xB1 = to_fixed_rt(WB1, sc), xDA = to_fixed_rt(DA, sc),
+                        xCO = to_fixed_rt(CO, sc);
+        const int se = sf - E;
+        // two pairs per iteration (every shell has an even number of pairs): two independent chains
+#pragma unroll 1
+        for (int j = c_pairs.first[S]; j < c_pairs.first[S + 1]; j += 2) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int I = c_pairs.pop[j + h];
+                const long long b = (long long)c_pairs.bx[j + h] * U + (long long)c_pairs.by[j + h] * V;
+                const long long b2 = hi(b, b);
+                const long long q = xB1 + hi(xCO, b2);
+                const long long e2 = k * q + xDA;
+                const long long we = xA0 + prod_at_rt(b2, e2, D);
+                const long long bq = prod_at_rt(b, q, D);
+                store(I, fma(P.omc, fs[I * SITE_BLOCK], from_fixed(we + bq, se)));
+                store(I + NPAIR, fma(P.omc, fs[(I + NPAIR) * SITE_BLOCK], from_fixed(we - bq, se)));
+            }
+        }
+    }
+}
+
+// The same relaxation in FP64 throughout (sites outside the fixed-point domain), as the same compact
+// loop over the shared-memory copy: per pair b from the table's (cx, cy) / kappa, then relax_pair's
+// arithmetic.
+template <class Store>
+__device__ __noinline__ void relax_all_fp64_rolled(const double* fs, double f0, const StepParams& P,
+                                                   const Relax64& R, Store& store) {
+    store(0, fma(P.omc, f0, P.sh[0].q_a0 * R.R0h));
+#pragma unroll 1
+    for (int S = 1; S < NSHELL; ++S) {
+        const ShellCoef& c = P.sh[S];
+        const double k = (double)c_pairs.kappa[S];
+        const double WA0 = fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h));
+        const double WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);
+        const double DA = fma(-c.q_e0, R.t, k * WB1);
+        const double CO = c.q_co * R.rw;
+#pragma unroll 1
+        for (int j = c_pairs.first[S]; j < c_pairs.first[S + 1]; ++j) {
+            const int I = c_pairs.pop[j];
+            const double b = fma((double)c_pairs.bx[j], R.U1, (double)c_pairs.by[j] * R.V1);
+            const double b2 = b * b;
+            const double q = fma(b2, CO, WB1);
+            const double we = fma(b2, fma(k, q, DA), WA0);
+            store(I, fma(P.omc, fs[I * SITE_BLOCK], fma(b, q, we)));
+            store(I + NPAIR, fma(P.omc, fs[(I + NPAIR) * SITE_BLOCK], fma(-b, q, we)));
+        }
+    }
 }
 
 // Collide site (x, y) with populations f (Sec. 3: moments, shifted equilibrium, BGK relaxation):
@@ -462,10 +542,27 @@ __device__ __forceinline__ void relax_all_fx(const double* f, const StepParams& 
 // then the wall halo rows the site feeds). Shared by the fused step and the collide kernel, so the
 // two give the same bits.
 template <class Store>
-__device__ __forceinline__ void collide_site(const double* f, const StepParams& P, int x, int y,
+__device__ __forceinline__ void collide_from_sums(const SiteSums& s, int bad, double f0, const double* fs,
+                                                  const StepParams& P, int x, int y, int* __restrict__ flag,
+                                                  Store&& store);
+
+// Collide with the populations f in registers (copied to the thread's shared-memory column first).
+template <class Store>
+__device__ __forceinline__ void collide_site(const double* f, double* fs, const StepParams& P, int x, int y,
                                              int* __restrict__ flag, Store&& store) {
     int bad;
     const SiteSums s = site_sums(f, &bad);
+#pragma unroll
+    for (int i = 1; i < NPOP; ++i) fs[i * SITE_BLOCK] = f[i];  // this thread's column of the block's copy
+    collide_from_sums(s, bad, f[0], fs, P, x, y, flag, store);
+}
+
+// The collide of a site whose moment sums are s (status bits bad), rest population f0 and other
+// populations in the thread's shared-memory column fs.
+template <class Store>
+__device__ __forceinline__ void collide_from_sums(const SiteSums& s, int bad, double f0, const double* fs,
+                                                  const StepParams& P, int x, int y, int* __restrict__ flag,
+                                                  Store&& store) {
     const double a = recip_nr(s.n0);
     Relax64 R;
     R.X = temperature_sum(s, a);
@@ -481,10 +578,10 @@ __device__ __forceinline__ void collide_site(const double* f, const StepParams& 
     const long long o = (long long)(y + HALO) * P.Lx + x;
     auto own = [&](int i, double v) { store(i, o, v); };
     if (fxp::in_domain(P, R)) {
-        relax_all_fx(f, P, R, E, own);
+        relax_all_fx(fs, f0, P, R, E, own);
     } else {  // outside the fixed-point formats: the FP64 evaluation with rho / tau itself
         relax_site_terms(P, s, a, rw, R);
-        relax_all(f, P, R, own);
+        relax_all_fp64_rolled(fs, f0, P, R, own);
     }
 
     // wall halo rows from this site's post-collision fields (rho, u + g, T)
@@ -516,7 +613,7 @@ __device__ __forceinline__ void shell_coefficients(const StepParams& P, double t
 
 // Sites site0 .. site1 - 1 (the whole lattice, or a band of rows of a slab). Three blocks (12 warps)
 // per SM: the register cap that keeps the occupancy of the FP64-only version.
-constexpr int STEP_BLOCKS_PER_SM = 3;
+constexpr int STEP_BLOCKS_PER_SM = 5;
 __global__ void __launch_bounds__(SITE_BLOCK, STEP_BLOCKS_PER_SM)
 step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const StepParams P,
                  int* __restrict__ flag, int site0, int site1) {
@@ -527,10 +624,21 @@ step_fp64_kernel(const double* __restrict__ src, double* __restrict__ dst, const
     const int x = site - y * Lx;
     const long long plane = P.plane;
 
-    double f[NPOP];
-    PullAll<NPOP - 1>::run(src, f, x, y, Lx, Ly, P.y_periodic, plane);
-    collide_site(f, P, x, y, flag,
-                 [&](int i, long long o, double v) { __stcs(dst + plane_off(i, plane) + o, v); });
+    // the pull in two batches of loads (the compiler barrier keeps the second batch after the first's
+    // consumers), each population added to the moment sums and staged in shared memory as it is
+    // used: about half the population registers of loading all 37 at once
+    __shared__ double fs[NPOP * SITE_BLOCK];
+    double* col = fs + threadIdx.x;
+    SumBins acc;
+    acc.init();
+    double f0;
+    pull_batch<0, 18>(src, x, y, Lx, Ly, P.y_periodic, plane, acc, col, &f0);
+    asm volatile("" ::: "memory");
+    pull_batch<19, NPOP - 1>(src, x, y, Lx, Ly, P.y_periodic, plane, acc, col, &f0);
+    int bad;
+    const SiteSums s = acc.finish(&bad);
+    collide_from_sums(s, bad, f0, col, P, x, y, flag,
+                      [&](int i, long long o, double v) { __stcs(dst + plane_off(i, plane) + o, v); });
 }
 
 // Collide only, in place (the paper's separate collide kernel, Sec. 3-5 and Table 1): each thread
@@ -546,11 +654,18 @@ collide_fp64_kernel(double* __restrict__ f, const StepParams P, int* __restrict_
     const int x = site - y * Lx;
     const long long plane = P.plane;
     const long long o = (long long)(y + HALO) * Lx + x;
-    double v[NPOP];
-#pragma unroll
-    for (int i = 0; i < NPOP; ++i) v[i] = f[plane_off(i, plane) + o];
-    collide_site(v, P, x, y, flag,
-                 [&](int i, long long oh, double val) { __stcs(f + plane_off(i, plane) + oh, val); });
+    __shared__ double fs[NPOP * SITE_BLOCK];
+    double* col = fs + threadIdx.x;
+    SumBins acc;
+    acc.init();
+    double f0;
+    own_batch<0, 18>(f + o, plane, acc, col, &f0);
+    asm volatile("" ::: "memory");
+    own_batch<19, NPOP - 1>(f + o, plane, acc, col, &f0);
+    int bad;
+    const SiteSums s = acc.finish(&bad);
+    collide_from_sums(s, bad, f0, col, P, x, y, flag,
+                      [&](int i, long long oh, double val) { __stcs(f + plane_off(i, plane) + oh, val); });
 }
 
 __global__ void __launch_bounds__(SITE_BLOCK)
