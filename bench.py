@@ -45,6 +45,9 @@ NPOP = 37
 # nominal FP64 rate counts an FMA as 2 flops).
 FP64_INST_PER_SITE = 121.2
 FP64_FLOP_PER_SITE = 200
+# Pipe shares of the same capture (ncu, % of peak, active): the FP64 pipe and the integer ALU pipe
+# are both near saturation since the pair terms moved to fixed point.
+FP64_PIPE_SHARES = {"fp64": 0.795, "alu": 0.714, "fma": 0.205, "issue": 0.617}
 # The kernel sources those counts were profiled on (code_digest, below): when the code differs the
 # counts are stale and the roofline's achieved and frac are reported as null
 # (tests/test_bench_host.py fails on a stale table, so a committed tree carries matching counts).
@@ -604,6 +607,10 @@ def main():
                                  "FMA probe below",
                     "sm_count": sm_count, "sm_max_mhz": sm_max_mhz, "peak_terms_source": peak_src,
                     "algorithmic_fp64_inst_per_site": FP64_INST_PER_SITE,
+                    "pipe_shares_ncu": FP64_PIPE_SHARES if counts_valid else None,
+                    "bound_note": "frac is the FP64 pipe's share at the measured step time; the "
+                                  "integer ALU pipe (exact moment sums, fixed-point pair terms) is "
+                                  "nearly as busy (pipe_shares_ncu, 1152x2048 capture)",
                     "inst_count_matches_sources": counts_valid,
                     "achieved_tflops": round(FP64_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
                     "oracle_flop_per_site": ORACLE_FLOP_PER_SITE,
