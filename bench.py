@@ -36,41 +36,48 @@ if ROOT not in sys.path:
 
 LX, LY, TAU, RATIO = 2304, 8192, 0.9, 2.0
 NPOP = 37
-# FP64 work of the fused step per site in this kernel's formulation: 121.2 FP64-pipe instructions
-# (79.0 fused + 42.1 non-fused; ncu on step_fp64_kernel, per site), i.e. 200 flops with FMA = 2.
+# FP64 work of the fused step per site in this kernel's formulation: 86.2 FP64-pipe instructions
+# (65.0 fused + 21.1 non-fused; ncu on step_fp64_kernel, per site), i.e. 151 flops with FMA = 2.
 # The moment sums run as exact 96-bit integer sums on the integer pipe, rounded to FP64 there too,
 # and each pair's equilibrium term is formed in 64-bit fixed point there (one FP64 FMA per
 # population remains). The FP64 pipe issues one such instruction per lane-slot whatever its kind, so the
 # ALU roofline is the FP64 instruction rate: 152 SMs x 2 per clock per SM x f_max (the 1.25 TFLOP/s
 # nominal FP64 rate counts an FMA as 2 flops).
-FP64_INST_PER_SITE = 121.2
-FP64_FLOP_PER_SITE = 200
-# Pipe shares of the same capture (ncu, % of peak, active): the FP64 pipe and the integer ALU pipe
-# are both near saturation since the pair terms moved to fixed point.
-FP64_PIPE_SHARES = {"fp64": 0.795, "alu": 0.714, "fma": 0.205, "issue": 0.617}
+FP64_INST_PER_SITE = 86.2
+FP64_FLOP_PER_SITE = 151
+# The binding unit of this kernel is the integer ALU pipe (16 lanes per SM sub-partition, i.e. 64
+# thread-instructions per clock per SM). Its instructions per site follow from the same capture:
+# ALU share of peak 75.67 % (elapsed) x 1.1847 M cycles x 64 lanes x 152 SMs / 2359296 sites = 3696
+# (the FMA pipe's 18.9 % at 128 lanes gives 1848, the FP64 pipe 86, and loads, stores and control
+# the rest of the 6370 instructions per site).
+ALU_INST_PER_SITE = 3696
+ALU_LANES_PER_CLK_SM = 64
+# Pipe shares of the same capture (ncu, % of peak, active): since the pair terms and most shell
+# coefficients moved to fixed point, the integer ALU pipe is the busiest.
+FP64_PIPE_SHARES = {"fp64": 0.573, "alu": 0.769, "fma": 0.251, "issue": 0.663}
 # The kernel sources those counts were profiled on (code_digest, below): when the code differs the
 # counts are stale and the roofline's achieved and frac are reported as null
 # (tests/test_bench_host.py fails on a stale table, so a committed tree carries matching counts).
-FP64_INST_SOURCES = {"step_fp64.cu": "52ba4f0b1ceb5de2353b8c8fdd7e5ce41a47cb7b8b1d7de6a1c08c7a1de0c27e",
-                     "d2q37_gpu.cuh": "018be3fc24d2d1e111a0b0f60ca97bbfb4f70db6005580ca2c81518bc54328ce",
+FP64_INST_SOURCES = {"step_fp64.cu": "58d1f96e4a03974f4f8281c49f293b8d80de66a563c02a5c232ff9bf53941afd",
+                     "d2q37_gpu.cuh": "d3baaae19fce2cc02e2e1c94f075d125d5d01659018f115a632612b46c4fc86c",
                      "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}
 # The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
 # equilibrium written per population, BGK relaxation with the gravity shift): 2763 flops, counted
 # by compiling the oracle's collide with an operation-counting scalar type
 # (oracle/count_collide_flops.cpp; tests/test_oracle_flops.py re-derives the number). The
-# kernel's factored formulation needs 200 of them in FP64 (the rest runs on the integer pipe).
+# kernel's factored formulation needs 151 of them in FP64 (the rest runs on the integer pipes).
 ORACLE_FLOP_PER_SITE = 2763
 FP64_BYTES_PER_SITE = 2 * NPOP * 8       # 37 reads + 37 writes (Table 1's propagate accounting)
 FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 FP64_INST_PER_CLK_SM = 2
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 698.478 MB + 691.452 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# 698.547 MB + 692.220 MB for 2359296 sites, scaled per site. Valid only for the kernel source
 # it was taken on (code_digest of the files below: sha256 of the code without comments);
 # otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (698.478336e6 + 691.451904e6) / 2359296,
-                "sources": {"step_fp64.cu": "52ba4f0b1ceb5de2353b8c8fdd7e5ce41a47cb7b8b1d7de6a1c08c7a1de0c27e",
-                            "d2q37_gpu.cuh": "018be3fc24d2d1e111a0b0f60ca97bbfb4f70db6005580ca2c81518bc54328ce",
+TRAFFIC_FP64 = {"bytes_per_site": (698.546944e6 + 692.219648e6) / 2359296,
+                "sources": {"step_fp64.cu": "58d1f96e4a03974f4f8281c49f293b8d80de66a563c02a5c232ff9bf53941afd",
+                            "d2q37_gpu.cuh": "d3baaae19fce2cc02e2e1c94f075d125d5d01659018f115a632612b46c4fc86c",
                             "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}}
 
 
@@ -79,7 +86,7 @@ TRAFFIC_FP64 = {"bytes_per_site": (698.478336e6 + 691.451904e6) / 2359296,
 TRAFFIC_FP32SPLIT = {"bytes_per_site": (349.264128e6 + 303.117056e6) / 2359296,
                      "sources": {"step_fp32dev.cu": "9bd8776f652ce5402527ff8a5eb09373b1db75d7a1be4418d81624f303f67877",
                                  "site_fp32dev.cuh": "ed58b9d3cc6f5e6464749fb716c6985c34642f9abdd0ca704ee46d6a60204ae1",
-                                 "d2q37_gpu.cuh": "018be3fc24d2d1e111a0b0f60ca97bbfb4f70db6005580ca2c81518bc54328ce"}}
+                                 "d2q37_gpu.cuh": "d3baaae19fce2cc02e2e1c94f075d125d5d01659018f115a632612b46c4fc86c"}}
 
 
 def code_digest(path):
@@ -597,20 +604,26 @@ def main():
         inst_rate = FP64_INST_PER_SITE * sites / kernel_s / 1e12 if counts_valid else None
         traffic = (round(TRAFFIC_FP64["bytes_per_site"] * sites) if sources_match(TRAFFIC_FP64)
                    and (LX, LY) == (2304, 8192) else None)
+        alu_rate = ALU_INST_PER_SITE * sites / kernel_s / 1e12 if counts_valid else None
+        alu_peak = sm_count * ALU_LANES_PER_CLK_SM * sm_max_mhz * 1e6 / 1e12
         roofline = {"bound": "alu", "kernel": "step_fp64_kernel",
-                    "achieved": None if inst_rate is None else round(inst_rate, 4),
-                    "peak": round(peak, 4), "unit": "T FP64-instructions/s",
-                    "frac": None if inst_rate is None else round(inst_rate / peak, 4), "traffic": traffic,
-                    "peak_note": f"FP64 pipe: {sm_count} SMs x 2 FP64 instructions (add, mul or FMA) "
-                                 f"per clock per SM x {sm_max_mhz:.0f} MHz ({peak_src}); the recipe's "
-                                 "1.25 TFLOP/s nominal with FMA = 2 flops; measured by the library's "
-                                 "FMA probe below",
+                    "achieved": None if alu_rate is None else round(alu_rate, 3),
+                    "peak": round(alu_peak, 3), "unit": "T integer-ALU instructions/s",
+                    "frac": None if alu_rate is None else round(alu_rate / alu_peak, 4), "traffic": traffic,
+                    "peak_note": f"integer ALU pipe: {sm_count} SMs x 64 instructions per clock per SM x "
+                                 f"{sm_max_mhz:.0f} MHz ({peak_src}); the step's binding unit since its pair "
+                                 "terms and most shell coefficients run in fixed point; ALU instructions per "
+                                 "site from ncu's ALU-pipe share of the 1152x2048 capture",
+                    "alu_inst_per_site": ALU_INST_PER_SITE,
+                    "fp64_pipe": {"achieved": None if inst_rate is None else round(inst_rate, 4),
+                                  "peak": round(peak, 4), "unit": "T FP64-instructions/s",
+                                  "frac": None if inst_rate is None else round(inst_rate / peak, 4),
+                                  "peak_note": f"FP64 pipe: {sm_count} SMs x 2 FP64 instructions per clock per "
+                                               f"SM x {sm_max_mhz:.0f} MHz, the recipe's 1.25 TFLOP/s nominal "
+                                               "with FMA = 2 flops"},
                     "sm_count": sm_count, "sm_max_mhz": sm_max_mhz, "peak_terms_source": peak_src,
                     "algorithmic_fp64_inst_per_site": FP64_INST_PER_SITE,
                     "pipe_shares_ncu": FP64_PIPE_SHARES if counts_valid else None,
-                    "bound_note": "frac is the FP64 pipe's share at the measured step time; the "
-                                  "integer ALU pipe (exact moment sums, fixed-point pair terms) is "
-                                  "nearly as busy (pipe_shares_ncu, 1152x2048 capture)",
                     "inst_count_matches_sources": counts_valid,
                     "achieved_tflops": round(FP64_FLOP_PER_SITE * sites / kernel_s / 1e12, 4),
                     "oracle_flop_per_site": ORACLE_FLOP_PER_SITE,

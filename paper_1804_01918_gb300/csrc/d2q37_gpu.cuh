@@ -27,6 +27,16 @@ constexpr double DIM = 2.0;
 // |lambda r u*| components <= 0.25 r 0.2, and |h| = |T* - 1| / 2 <= 0.2 (T* in [0.6, 1.4]).
 constexpr double FX_UMAX = 0.2;
 constexpr double FX_HB = 0.2;
+// Its per-shell units: values in units of 2^-coarse (k WB1, DA, k^3 C, q, e2) and 2^-fine (WA0 and
+// the pair term G); the largest scales that keep every intermediate below 2^61 over the domain.
+__host__ __device__ constexpr int fx_coarse_unit(int s) {
+    constexpr int t[NSHELL] = {0, 59, 60, 59, 64, 63, 63, 67};
+    return t[s];
+}
+__host__ __device__ constexpr int fx_fine_unit(int s) {
+    constexpr int t[NSHELL] = {0, 62, 63, 64, 65, 67, 69, 68};
+    return t[s];
+}
 
 // Tables are constexpr functions (usable in host code, device code and constant expressions).
 // Lattice vectors of populations 0..18; 19..36 are their negatives.
@@ -94,6 +104,16 @@ struct ShellCoef32 {
     float q_a0, q_a1, q_a2, q_e0, q_e1, q_b0, q_b1, q_c;
 };
 
+// A shell's constants for the fixed-point pair terms of the FP64 step (step_fp64.cu), rounded to
+// integers on the host: each is the high word's factor for a site term in the stated format, so
+//   k WB1 = hi(b1, t Q.64) + hi(b0, Rb Q.62),  DA = k (k WB1) - hi(e0, t Q.64),
+//   k^3 C = hi(co, mantissa of rho/tau Q.62)                      in 2^-coarse:
+// b1 = q_b1 2^coarse, b0 = q_b0 2^(coarse + 2), e0 = q_e0 2^coarse, co = q_co 2^(coarse + 2)
+// (all below 2^62).
+struct ShellFx {
+    long long b1, b0, e0, co;
+};
+
 // Everything a step kernel needs, passed by value as a kernel parameter.
 struct StepParams {
     int Lx, Ly;
@@ -118,6 +138,8 @@ struct StepParams {
     // bit patterns of the fixed-point pair terms' domain bounds (step_fp64.cu, fxp): |lambda r u*|
     // components <= FX_UB, |h| <= FX_HB
     unsigned long long fx_ub, fx_hb;
+    // per shell the constants of shell_relax in fixed point (ShellFx)
+    ShellFx shfx[NSHELL];
     double T_bot, T_top;   // wall temperatures below row 0 and above row Ly - 1
     ShellCoef sh[NSHELL];
     double wall_bot[NPOP]; // rest equilibrium per unit density at T_bottom, per population

@@ -148,6 +148,15 @@ void fill_step_params(const lb_params& p, StepParams& sp) {
         const double ub = 0.25 * r * FX_UMAX, hb = FX_HB;
         std::memcpy(&sp.fx_ub, &ub, 8);
         std::memcpy(&sp.fx_hb, &hb, 8);
+        for (int s = 1; s < NSHELL; ++s) {
+            const ShellCoef& c = sp.sh[s];
+            const int co = fx_coarse_unit(s);
+            ShellFx& q = sp.shfx[s];
+            q.b1 = std::llround(std::ldexp(c.q_b1, co));
+            q.b0 = std::llround(std::ldexp(c.q_b0, co + 2));
+            q.e0 = std::llround(std::ldexp(c.q_e0, co));
+            q.co = std::llround(std::ldexp(c.q_co, co + 2));
+        }
     }
     sp.r_f = (float)sp.r;
     sp.r2_f = (float)sp.r2;

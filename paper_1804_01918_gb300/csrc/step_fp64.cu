@@ -383,14 +383,8 @@ __device__ __forceinline__ void relax_all(const double* f, const StepParams& P, 
 // A site outside the domain takes the FP64 evaluation.
 namespace fxp {
 
-__host__ __device__ constexpr int coarse_of(int s) {
-    constexpr int t[NSHELL] = {0, 59, 60, 59, 64, 63, 63, 67};
-    return t[s];
-}
-__host__ __device__ constexpr int fine_of(int s) {
-    constexpr int t[NSHELL] = {0, 62, 63, 64, 65, 67, 69, 68};
-    return t[s];
-}
+__host__ __device__ constexpr int coarse_of(int s) { return fx_coarse_unit(s); }
+__host__ __device__ constexpr int fine_of(int s) { return fx_fine_unit(s); }
 
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(v) & 0x7FFFFFFFFFFFFFFFull;
@@ -478,17 +472,23 @@ __device__ __forceinline__ void relax_all_fx(const double* fs, double f0, const 
     const double g0 = P.sh[0].q_a0 * R.R0h;
     store(0, fma(P.omc, f0, __longlong_as_double(__double_as_longlong(g0) + ((long long)E << 52))));
     const long long U = to_fixed_rt(R.U1, 64), V = to_fixed_rt(R.V1, 64);
+    // the site terms of the integer products in fixed point (bounds over the domain: |t| < 1/2,
+    // |Rb| and the density factor's mantissa < 2)
+    const long long mq = to_fixed_rt(R.rw, 62), T = to_fixed_rt(R.t, 64), Rb = to_fixed_rt(R.Rb, 62);
 #pragma unroll 1
     for (int S = 1; S < NSHELL; ++S) {
-        const ShellCoef& c = P.sh[S];
         const long long k = c_pairs.kappa[S];
-        const double WA0 = fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h));
-        const double WB1 = fma(c.q_b1, R.t, c.q_b0 * R.Rb);          // k WB1
-        const double DA = fma(-c.q_e0, R.t, (double)k * WB1);        // k^2 (WA2 - WB1)
-        const double CO = c.q_co * R.rw;                              // k^3 C
-        const int sc = c_pairs.coarse[S], sf = c_pairs.fine[S], D = sf - sc;
-        const long long xA0 = to_fixed_rt(WA0, sf), xB1 = to_fixed_rt(WB1, sc), xDA = to_fixed_rt(DA, sc),
-                        xCO = to_fixed_rt(CO, sc);
+        const int sf = c_pairs.fine[S], D = sf - c_pairs.coarse[S];
+        // shell_relax's coefficients: WA0 in FP64 (3 FP64 instructions), rounded to the fine unit;
+        // k WB1, DA and k^3 C as integer products of the host's fixed-point constants (ShellFx) and
+        // the site terms, in the coarse unit (measured fastest: all four as integer products, or
+        // all but k^3 C in FP64, were 5 % and 3 % slower)
+        const ShellFx& q = P.shfx[S];
+        const ShellCoef& c = P.sh[S];
+        const long long xA0 = to_fixed_rt(fma(c.q_a2, R.P2, fma(c.q_a1, R.P1, c.q_a0 * R.R0h)), sf);
+        const long long xB1 = hi(q.b1, T) + hi(q.b0, Rb);
+        const long long xDA = k * xB1 - hi(q.e0, T);
+        const long long xCO = hi(q.co, mq);
         const int se = sf - E;
         // two pairs per iteration (every shell has an even number of pairs): two independent chains
 #pragma unroll 1

@@ -3,11 +3,12 @@ checked on the host by evaluating the kernel's integer arithmetic exactly with P
 
 * over the whole domain (|u*| components <= FX_UMAX, |T* - 1| / 2 <= FX_HB, density factor in
   [1, 2)) no intermediate leaves the 2^62 range the formats promise;
-* in the Rayleigh-Taylor and strong-flow regimes the fixed-point G = WA0 + b^2 e2 +- b q, against
-  exact rational arithmetic on the same FP64 inputs, is as accurate as the FP64 evaluation of the
-  same expression (the formats were chosen so).
+* in the Rayleigh-Taylor and strong-flow regimes the fixed-point G = WA0 + b^2 e2 +- b q (the
+  shell coefficients themselves integer products of the host's rounded constants and the site
+  terms), against exact rational arithmetic on the same FP64 constants and site terms, is as
+  accurate as the FP64 evaluation of the same expression (the formats were chosen so).
 
-The per-shell scales are read from the kernel source; weights and the thermal scale come from the
+The per-shell scales are read from the kernel header; weights and the thermal scale come from the
 oracle's velocity set. Relaxation terms follow step_fp64.cu (relax_site_terms, shell_relax,
 pair_base, relax_pair_fx).
 """
@@ -31,14 +32,13 @@ PAIRS = [(1, 0, 1), (0, 1, 1), (1, 1, 2), (1, -1, 2), (2, 0, 3), (0, 2, 3), (2, 
 
 
 def kernel_tables():
-    src = open(os.path.join(CSRC, "step_fp64.cu")).read()
-    def table(name):
-        m = re.search(name + r"\(int s\) \{\s*constexpr int t\[NSHELL\] = \{([^}]*)\}", src)
-        return [int(v) for v in m.group(1).split(",")]
     hdr = open(os.path.join(CSRC, "d2q37_gpu.cuh")).read()
+    def table(name):
+        m = re.search(name + r"\(int s\) \{\s*constexpr int t\[NSHELL\] = \{([^}]*)\}", hdr)
+        return [int(v) for v in m.group(1).split(",")]
     umax = float(re.search(r"FX_UMAX = ([0-9.]+);", hdr).group(1))
     hb = float(re.search(r"FX_HB = ([0-9.]+);", hdr).group(1))
-    return table("coarse_of"), table("fine_of"), umax, hb
+    return table("fx_coarse_unit"), table("fx_fine_unit"), umax, hb
 
 
 @pytest.fixture(scope="module")
@@ -111,16 +111,37 @@ def pair_b(cx, cy, U, V):
     return cx * U + (V if cy > 0 else -V)
 
 
-def fixed_G(coarse, fine, S, coef, U, V, cx, cy):
-    """The kernel's integer arithmetic of one pair: (G(+c), G(-c)) as integers in the fine unit."""
-    WA0, WB1, DA, CO = coef
+def shell_constants(S, w, r):
+    """shell_relax's FP64 constants q_a2, q_a1, q_a0, q_b1, q_b0, q_e0, q_co of shell S."""
+    k, X, ww = KAPPA[S], r * r * C2[S], w[S]
+    return (0.5 * ww * X * X, 2 * ww * X, 2 * ww, 4 * k * ww * X, 8 * k * ww, 16 * k * k * ww,
+            32 * k ** 3 * ww / 3)
+
+
+def fixed_G(coarse, fine, S, site_terms, w, r, U, V, cx, cy, rwm):
+    """The kernel's integer arithmetic of one pair: (G(+c), G(-c)) as integers in the fine unit.
+    WA0 is the FP64 evaluation rounded to the fine unit; k WB1, DA and k^3 C are high words of
+    products of the host's rounded constants (d2q37_gpu.cuh, ShellFx) with the site terms."""
+    t, Rb, P1, P2, R0h = site_terms
     sc, sf = coarse[S], fine[S]
     d, k = sf - sc, KAPPA[S]
+    qa2, qa1, qa0, qb1, qb0, qe0, qco = shell_constants(S, w, r)
+    c = [None, None, None, round(qb1 * 2.0 ** sc), round(qb0 * 2.0 ** (sc + 2)), round(qe0 * 2.0 ** sc),
+         round(qco * 2.0 ** (sc + 2))]
+    for v in c[3:]:
+        fits(v)
+    T, RB = to_fixed(t, 64), to_fixed(Rb, 62)
+    mq = to_fixed(rwm, 62)
+    WA0 = qa2 * P2 + (qa1 * P1 + qa0 * R0h)     # the kernel's FP64 WA0 (fma order; rounding aside)
+    xa0 = fits(to_fixed(WA0, sf))
+    xb1 = fits(((c[3] * T) >> 64) + ((c[4] * RB) >> 64))
+    xda = fits(k * xb1 - ((c[5] * T) >> 64))
+    xco = fits((c[6] * mq) >> 64)
     b = fits(pair_b(cx, cy, U, V))
     b2 = fits((b * b) >> 64)
-    q = fits(to_fixed(WB1, sc) + ((to_fixed(CO, sc) * b2) >> 64))
-    e2 = fits(k * q + to_fixed(DA, sc))
-    we = fits(to_fixed(WA0, sf) + fits((b2 * e2) >> (64 - d)))
+    q = fits(xb1 + ((xco * b2) >> 64))
+    e2 = fits(k * q + xda)
+    we = fits(xa0 + fits((b2 * e2) >> (64 - d)))
     bq = fits((b * q) >> (64 - d))
     return fits(we + bq), fits(we - bq)
 
@@ -136,7 +157,7 @@ def test_no_intermediate_leaves_the_formats_over_the_domain(model):
                     U1, V1, t, Rb, P1, P2, R0h = site(ux, uy, h, rwm, r)
                     U, V = fits(to_fixed(U1, 64)), fits(to_fixed(V1, 64))
                     for cx, cy, S in PAIRS:
-                        fixed_G(coarse, fine, S, shell(S, w, r, rwm, t, Rb, P1, P2, R0h), U, V, cx, cy)
+                        fixed_G(coarse, fine, S, (t, Rb, P1, P2, R0h), w, r, U, V, cx, cy, rwm)
 
 
 @pytest.mark.parametrize("urange,Trange", [(0.05, (0.67, 1.33)), (0.16, (0.8, 1.2))])
@@ -151,16 +172,22 @@ def test_fixed_point_G_as_accurate_as_fp64(model, urange, Trange):
         U1, V1, t, Rb, P1, P2, R0h = site(ux, uy, h, rwm, r)
         U, V = to_fixed(U1, 64), to_fixed(V1, 64)
         for cx, cy, S in PAIRS:
-            coef = shell(S, w, r, rwm, t, Rb, P1, P2, R0h)
-            WA0, WB1, DA, CO = coef
+            WA0, WB1, DA, CO = shell(S, w, r, rwm, t, Rb, P1, P2, R0h)     # the FP64 evaluation
             k = KAPPA[S]
+            qa2, qa1, qa0, qb1, qb0, qe0, qco = (Fr(v) for v in shell_constants(S, w, r))
+            # exact: the same constants and FP64 site terms in rational arithmetic
+            ta, Rba, P1a, P2a, R0a = Fr(t), Fr(Rb), Fr(P1), Fr(P2), Fr(R0h)
+            WB1x = qb1 * ta + qb0 * Rba
+            WA0x = Fr(qa2 * P2 + (qa1 * P1 + qa0 * R0h))      # the FP64 WA0 that both paths use
+            DAx = k * WB1x - qe0 * ta
+            COx = qco * Fr(rwm)
             bx = Fr(pair_b(cx, cy, Fr(U1), Fr(V1)))
-            qx = Fr(WB1) + Fr(CO) * bx * bx
-            wex = Fr(WA0) + bx * bx * (k * qx + Fr(DA))
+            qx = WB1x + COx * bx * bx
+            wex = WA0x + bx * bx * (k * qx + DAx)
             bf = pair_b(cx, cy, U1, V1)
             qf = WB1 + CO * bf * bf
             wef = WA0 + bf * bf * (k * qf + DA)
-            Gp, Gm = fixed_G(coarse, fine, S, coef, U, V, cx, cy)
+            Gp, Gm = fixed_G(coarse, fine, S, (t, Rb, P1, P2, R0h), w, r, U, V, cx, cy, rwm)
             for sgn, gfx in ((1, Gp), (-1, Gm)):
                 exact = wex + sgn * bx * qx
                 worst_fx = max(worst_fx, abs(from_fixed(gfx, fine[S]) - float(exact)) / abs(float(exact)))
