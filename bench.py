@@ -47,18 +47,17 @@ FP64_INST_PER_SITE = 86.2
 FP64_FLOP_PER_SITE = 151
 # The binding unit of this kernel is the integer ALU pipe (16 lanes per SM sub-partition, i.e. 64
 # thread-instructions per clock per SM). Its instructions per site follow from the same capture:
-# ALU share of peak 75.67 % (elapsed) x 1.1847 M cycles x 64 lanes x 152 SMs / 2359296 sites = 3696
-# (the FMA pipe's 18.9 % at 128 lanes gives 1848, the FP64 pipe 86, and loads, stores and control
-# the rest of the 6370 instructions per site).
-ALU_INST_PER_SITE = 3696
+# ALU share of peak 70.53 % (elapsed) x 1.0822 M cycles x 64 lanes x 152 SMs / 2359296 sites = 3147
+# (of 5694 instructions per site; the FMA pipe takes the 64-bit multiplies, the FP64 pipe 86).
+ALU_INST_PER_SITE = 3147
 ALU_LANES_PER_CLK_SM = 64
 # Pipe shares of the same capture (ncu, % of peak, active): since the pair terms and most shell
 # coefficients moved to fixed point, the integer ALU pipe is the busiest.
-FP64_PIPE_SHARES = {"fp64": 0.573, "alu": 0.769, "fma": 0.251, "issue": 0.663}
+FP64_PIPE_SHARES = {"fp64": 0.627, "alu": 0.716, "fma": 0.215, "issue": 0.648}
 # The kernel sources those counts were profiled on (code_digest, below): when the code differs the
 # counts are stale and the roofline's achieved and frac are reported as null
 # (tests/test_bench_host.py fails on a stale table, so a committed tree carries matching counts).
-FP64_INST_SOURCES = {"step_fp64.cu": "58d1f96e4a03974f4f8281c49f293b8d80de66a563c02a5c232ff9bf53941afd",
+FP64_INST_SOURCES = {"step_fp64.cu": "85ffbf362e557f7acf45bbbfdab6c7fd84155e6352c689134d8472c27fe87275",
                      "d2q37_gpu.cuh": "d3baaae19fce2cc02e2e1c94f075d125d5d01659018f115a632612b46c4fc86c",
                      "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}
 # The algorithmic work of one site update in the oracle's plain formulation (moments, the Hermite
@@ -72,11 +71,11 @@ FP32DEV_BYTES_PER_SITE = 2 * NPOP * 4
 FP64_INST_PER_CLK_SM = 2
 # DRAM bytes of one step_fp64_kernel launch measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum) on the 1152x2048 capture (profiles/step_fp64_1152x2048_full.md):
-# 698.547 MB + 692.220 MB for 2359296 sites, scaled per site. Valid only for the kernel source
+# 698.482 MB + 692.198 MB for 2359296 sites, scaled per site. Valid only for the kernel source
 # it was taken on (code_digest of the files below: sha256 of the code without comments);
 # otherwise reported as null.
-TRAFFIC_FP64 = {"bytes_per_site": (698.546944e6 + 692.219648e6) / 2359296,
-                "sources": {"step_fp64.cu": "58d1f96e4a03974f4f8281c49f293b8d80de66a563c02a5c232ff9bf53941afd",
+TRAFFIC_FP64 = {"bytes_per_site": (698.482176e6 + 692.197888e6) / 2359296,
+                "sources": {"step_fp64.cu": "85ffbf362e557f7acf45bbbfdab6c7fd84155e6352c689134d8472c27fe87275",
                             "d2q37_gpu.cuh": "d3baaae19fce2cc02e2e1c94f075d125d5d01659018f115a632612b46c4fc86c",
                             "fixed96.cuh": "223c1f873d175ecc44292e1d48cb1cfb717e8884e9503cfe3f056c32c7b33788"}}
 

@@ -96,6 +96,18 @@ struct SumBins {
         fx::add96(bx[cx_of(I) + 3], n);
         fx::add96(by[cy_of(I) + 3], n);
     }
+    // The same for a positive v with 2^-28 <= v < 16 (biased exponent 995 .. 1026): no sign, no
+    // right shift, no clamping, and nothing to report through emax.
+    template <int I>
+    __device__ __forceinline__ void add_in_range(double v) {
+        const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+        const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+        const unsigned k = (hi >> 20) - 995u;
+        const unsigned mh = (hi & 0xFFFFFu) | 0x100000u;
+        const fx::I96 n{lo << k, __funnelshift_l(lo, mh, k), __funnelshift_l(mh, 0u, k)};
+        fx::add96(bx[cx_of(I) + 3], n);
+        fx::add96(by[cy_of(I) + 3], n);
+    }
     __device__ __forceinline__ SiteSums finish(int* bad) const {
         using namespace fx;
         *bad = emax == 0x7FFu ? 1 : (emax > EXP_LIMIT ? 2 : 0);
@@ -160,16 +172,36 @@ __device__ __forceinline__ void batch_load(const double* __restrict__ src, doubl
         batch_load<A, I + 1, B>(src, g, x, y, Lx, Ly, yp, plane);
     }
 }
-template <int A, int I, int B>
-__device__ __forceinline__ void batch_add(SumBins& acc, const double* g, double* fs, double* f0) {
+template <int A, int I, int B, bool kInRange>
+__device__ __forceinline__ void batch_add_as(SumBins& acc, const double* g, double* fs, double* f0) {
     if constexpr (I <= B) {
-        acc.add<I>(g[I - A]);
+        if constexpr (kInRange)
+            acc.add_in_range<I>(g[I - A]);
+        else
+            acc.add<I>(g[I - A]);
         if constexpr (I == 0)
             *f0 = g[0];
         else
             fs[I * SITE_BLOCK] = g[I - A];
-        batch_add<A, I + 1, B>(acc, g, fs, f0);
+        batch_add_as<A, I + 1, B, kInRange>(acc, g, fs, f0);
     }
+}
+// Whether every value of the batch is positive with 2^-28 <= v < 16 (the range of add_in_range).
+template <int A, int I, int B>
+__device__ __forceinline__ bool batch_in_range(const double* g) {
+    if constexpr (I <= B) {
+        const unsigned hi = (unsigned)((unsigned long long)__double_as_longlong(g[I - A]) >> 32);
+        return (hi - (995u << 20)) < (32u << 20) && batch_in_range<A, I + 1, B>(g);
+    } else {
+        return true;
+    }
+}
+template <int A, int I, int B>
+__device__ __forceinline__ void batch_add(SumBins& acc, const double* g, double* fs, double* f0) {
+    if (batch_in_range<A, A, B>(g))
+        batch_add_as<A, A, B, true>(acc, g, fs, f0);
+    else
+        batch_add_as<A, A, B, false>(acc, g, fs, f0);
 }
 // The same for a site's own populations (the in-place collide): population i at site + i plane.
 template <int A, int I, int B>
@@ -396,18 +428,17 @@ __device__ __forceinline__ bool in_domain(const StepParams& P, const Relax64& R)
     return abs_bits(R.U1) <= P.fx_ub && abs_bits(R.V1) <= P.fx_ub && abs_bits(R.h) <= P.fx_hb;
 }
 
-// g 2^-s rounded to FP64 (to nearest, ties to even), on the integer pipe.
+// g 2^-s rounded to FP64 on the integer pipe: to nearest, a tie rounded away from zero (within half
+// an ulp like ties-to-even, and fewer instructions).
 __device__ __forceinline__ double from_fixed(long long g, int s) {
-    const unsigned long long sign = (unsigned long long)g & 0x8000000000000000ull;
-    const unsigned long long u = g < 0 ? (unsigned long long)(-g) : (unsigned long long)g;
-    const int z = __clzll((long long)u);                    // 64 only for g = 0
-    const unsigned long long w = u << (z & 63);             // leading one at bit 63
-    const unsigned long long t = w >> 10;                   // 53 bits and the round bit
-    const unsigned long long x = ((w & 0x3FFull) != 0ull ? 1ull : 0ull) | ((t >> 1) & 1ull);
-    const unsigned long long sig = (t + x) >> 1;            // implicit one at bit 52 (or a carry)
-    const unsigned long long e1 = (unsigned long long)(1085 - z - s);  // biased exponent - 1
-    const unsigned long long bits = ((e1 << 52) + sig) | sign;
-    return z == 64 ? 0.0 : __longlong_as_double((long long)bits);
+    const unsigned long long sm = (unsigned long long)(g >> 63);      // 0 or all ones
+    const unsigned long long u = ((unsigned long long)g ^ sm) - sm;   // |g|
+    const int z = __clzll((long long)u);                              // 64 only for g = 0
+    const unsigned long long w = u << (z & 63);                       // leading one at bit 63
+    const unsigned long long sig = ((w >> 10) + 1ull) >> 1;           // 53 bits, or 2^53 on a carry
+    const unsigned long long e1 = (unsigned long long)(1085 - z - s); // biased exponent - 1
+    const unsigned long long bits = ((e1 << 52) + sig) | (sm & 0x8000000000000000ull);
+    return u ? __longlong_as_double((long long)bits) : 0.0;
 }
 
 // v 2^S as a two's-complement integer, truncated toward zero (|v| 2^S < 2^62 in the domain).

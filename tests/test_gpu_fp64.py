@@ -333,6 +333,34 @@ def test_fixed_point_domain_edge_and_fallback_match_oracle(L, orc, tau):
     assert err <= TOL
 
 
+def test_exact_sums_outside_their_fast_range_match_oracle(L, orc):
+    """The step's exact moment sums take a shorter path when every population of a batch is positive
+    and in [2^-28, 16); planted negative, tiny (< 2^-28, truncated at the 2^-80 quantum) and large
+    populations at scattered sites send those sites' batches through the general conversion. One
+    step agrees with the oracle within 1e-12 of each population's weight everywhere."""
+    Lx, Ly = 48, 20
+    st = inputs.random_state(Lx, Ly, seed=13, du=0.05, dT=0.1, drho=0.1)
+    f0 = orc.equilibrium(st.rho, st.ux, st.uy, st.T)
+    rng = np.random.default_rng(14)
+    f0 = f0 * (1.0 + 0.02 * rng.uniform(-1, 1, f0.shape))
+    _, _, w, _ = orc.velocity_set()
+    for k, (y, x) in enumerate([(2, 3), (5, 40), (9, 17), (13, 30), (17, 8), (11, 44)]):
+        i = (7 * k + 3) % 37
+        f0[y, x, i] = (-0.01, 1e-12, 3e-10, 2.5, -1e-9, 0.9)[k] * (w[i] if k != 3 else 1.0)
+    cx, cy, _, _ = L.velocity_set()
+    lat = L.Lattice(Lx, Ly, 0.8, st.rho, st.ux, st.uy, st.T, T_top=st.T_top, T_bottom=st.T_bottom,
+                    y_periodic=True)
+    lat.set_populations(orc.to_planes(f0, cx, cy))
+    lat.step(1)
+    lat.sync()
+    got = orc.from_planes(lat.get_populations(), cx, cy)
+    lat.close()
+    want = orc.run(f0, tau=0.8, nsteps=1, y_periodic=True)
+    err = float(np.max(np.abs(got - want) / w))
+    print(f"planted populations outside the fast range: max |f - f_oracle| / w = {err:.2e}")
+    assert err <= TOL
+
+
 @pytest.mark.parametrize("wall_mode", ["rest", "mirror"])
 def test_fused_step_matches_oracle_over_1000_steps(L, orc, wall_mode):
     """Ten times the bar's horizon: the rounding differences between the kernel (exact integer
