@@ -252,7 +252,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         for (int c = 0; c < HID; c += 32) {
             tc::tmem_ld32(tmem_lane_addr(tm, warp, c), v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b1[c + j]);
+            for (int j = 0; j < 32; j += 2) gelu_bias2(v[j], v[j + 1], b1[c + j], b1[c + j + 1]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
         }
@@ -262,7 +262,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         for (int c = 0; c < HID; c += 32) {
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), v);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + b2[c + j]);
+            for (int j = 0; j < 32; j += 2) gelu_bias2(v[j], v[j + 1], b2[c + j], b2[c + j + 1]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
         }
@@ -308,7 +308,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), z);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(z[j] + b2[c + j]);
+            for (int j = 0; j < 32; j += 2) gelu_grad_bias2(v[j], v[j + 1], z[j], z[j + 1], b2[c + j], b2[c + j + 1]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
             gbw[HID + c + (tid & 31)] = warp_column_sums(v);
@@ -330,7 +330,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
             tc::tmem_ld32(tmem_lane_addr(tm, warp, c), z);
 #pragma unroll
-            for (int j = 0; j < 32; ++j) v[j] *= gelu_grad(z[j] + b1[c + j]);
+            for (int j = 0; j < 32; j += 2) gelu_grad_bias2(v[j], v[j + 1], z[j], z[j + 1], b1[c + j], b1[c + j + 1]);
 #pragma unroll
             for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
             gbw[c + (tid & 31)] = warp_column_sums(v);
@@ -468,7 +468,7 @@ __device__ __forceinline__ bool mlp_forward_tile(FwdCtx& f, const NetDev& net, f
             for (int c = 0; c < HID; c += 32) {
                 tc::tmem_ld32(tmem_lane_addr(f.tm, f.warp, (layer == 0 ? 0 : 128) + c), v);
 #pragma unroll
-                for (int j = 0; j < 32; ++j) v[j] = gelu(v[j] + bias[c + j]);
+                for (int j = 0; j < 32; j += 2) gelu_bias2(v[j], v[j + 1], bias[c + j], bias[c + j + 1]);
 #pragma unroll
                 for (int j = 0; j < 32; j += 8) store_row8(f.sm + FW_H, f.tid, c + j, HID, v + j);
             }

@@ -103,6 +103,80 @@ __device__ __forceinline__ float gelu_grad(float z) {
     return fmaf(e, fmaf(z, 0.39894228040143268f, -copysignf(hp, z)), step);
 }
 
+// ---- pairs of FP32 values in one 64-bit register and the paired FP32 instructions of sm_100+
+// (fma/mul/add .rn.f32x2): each rounds both halves exactly as its scalar counterpart does, in one
+// instruction. The epilogues evaluate GELU and its derivative two columns at a time with them.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void x2_split(f32x2 v, float& a, float& b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_splat(float c) { return x2(c, c); }
+
+// P(t) / 2 and E of gelu_parts for a pair |z| = (a0, a1), and the pair itself as A.
+__device__ __forceinline__ void gelu_parts2(f32x2 A, float a0, float a1, f32x2& HP, f32x2& E) {
+    constexpr float kP = (float)(0.3275911 * 0.70710678118654752);
+    constexpr float c1 = 0.5f * 0.254829592f, c2 = 0.5f * -0.284496736f, c3 = 0.5f * 1.421413741f,
+                    c4 = 0.5f * -1.453152027f, c5 = 0.5f * 1.061405429f;
+    constexpr float kE = (float)(-0.5 * 1.4426950408889634);
+    float d0, d1;
+    x2_split(x2_fma(x2_splat(kP), A, x2_splat(1.0f)), d0, d1);
+    const f32x2 T = x2(rcp_approx(d0), rcp_approx(d1));
+    f32x2 P = x2_fma(T, x2_splat(c5), x2_splat(c4));
+    P = x2_fma(T, P, x2_splat(c3));
+    P = x2_fma(T, P, x2_splat(c2));
+    HP = x2_mul(T, x2_fma(T, P, x2_splat(c1)));
+    float q0, q1;
+    x2_split(x2_mul(x2_mul(A, A), x2_splat(kE)), q0, q1);
+    E = x2(ex2_approx(q0), ex2_approx(q1));
+}
+
+// GELU of z0 + b0 and z1 + b1 (in place): gelu() two at a time.
+__device__ __forceinline__ void gelu_bias2(float& z0, float& z1, float b0, float b1) {
+    float y0, y1;
+    x2_split(x2_add(x2(z0, z1), x2(b0, b1)), y0, y1);
+    const float a0 = fabsf(y0), a1 = fabsf(y1);
+    f32x2 HP, E;
+    gelu_parts2(x2(a0, a1), a0, a1, HP, E);
+    // max(y, 0) - |y| P E / 2
+    const f32x2 R = x2_fma(x2_mul(x2(-a0, -a1), HP), E, x2(fmaxf(y0, 0.0f), fmaxf(y1, 0.0f)));
+    x2_split(R, z0, z1);
+}
+
+// v0 * GELU'(z0 + b0) and v1 * GELU'(z1 + b1) (into v0, v1): gelu_grad() two at a time.
+__device__ __forceinline__ void gelu_grad_bias2(float& v0, float& v1, float z0, float z1, float b0, float b1) {
+    float y0, y1;
+    x2_split(x2_add(x2(z0, z1), x2(b0, b1)), y0, y1);
+    const float a0 = fabsf(y0), a1 = fabsf(y1);
+    f32x2 HP, E;
+    gelu_parts2(x2(a0, a1), a0, a1, HP, E);
+    float h0, h1;
+    x2_split(HP, h0, h1);
+    // [y >= 0] + E (y / sqrt(2 pi) - sign(y) P / 2)
+    const f32x2 inner = x2_fma(x2(y0, y1), x2_splat(0.39894228040143268f), x2(-copysignf(h0, y0), -copysignf(h1, y1)));
+    const f32x2 G = x2_fma(E, inner, x2(y0 >= 0.0f ? 1.0f : 0.0f, y1 >= 0.0f ? 1.0f : 0.0f));
+    x2_split(x2_mul(x2(v0, v1), G), v0, v1);
+}
+
 __device__ __forceinline__ uint32_t pack_bf16x2(float a, float b) {
     const __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
     return *reinterpret_cast<const uint32_t*>(&v);
