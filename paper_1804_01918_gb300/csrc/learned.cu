@@ -558,92 +558,273 @@ mlp_eval_kernel(NetDev net, const float* __restrict__ x, float* __restrict__ y, 
     fwd_teardown(f, ok);
 }
 
-// The learned LB step (see the file header). Lx and Ly are multiples of 32.
-__global__ void __launch_bounds__(128)
-step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P, NetDev net,
-                    unsigned char* __restrict__ tile_mode, int check, float bound,
-                    LearnedStats* __restrict__ stats, int* __restrict__ flag) {
-    extern __shared__ __align__(1024) char sm[];
-    FwdCtx f;
-    fwd_setup(f, net, sm);
-    float* red = reinterpret_cast<float*>(sm + FW_RED);
-    const int ntx = P.Lx / 32, ntiles = ntx * (P.Ly / 32);
-    const float* mu_x = f.cst + FC_MUX;
-    const float* isd_x = f.cst + FC_ISDX;
-    const float* mu_t = f.cst + FC_MUT;
-    const float* sd_t = f.cst + FC_SDT;
-    bool alive = true;
-    for (int t = blockIdx.x; t < ntiles && alive; t += gridDim.x) {
-        const int x0 = (t % ntx) * 32, y0 = (t / ntx) * 32;
-        const int mode = tile_mode[t];
-        const int x = x0 + (f.tid & 31);
-        if (!check && mode) {
-            for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
-            continue;
+// ---- the learned LB step ----------------------------------------------------------------------
+// One CTA per SM with three independent groups of four warps (a warpgroup each), persistent over
+// 32 x 32-site tiles: a group takes a whole tile and steps it in eight sub-tiles of 128 sites (four
+// rows of 32, one site per thread): pull, exact-split sums, the network (three tcgen05 products
+// issued by one thread of the group, bias + GELU epilogues from the group's 128 TMEM columns into
+// its H image), the change added and projected onto the exact moments, stored; on check steps the
+// plain collide of the same sites as well, for the tile residual and, in the group's scratch tile,
+// for a fallback, which copies it over the stored tile. While one group waits for the tensor cores
+// the other two keep the SM busy. Per group in shared memory: the H image (whose first 12 KB hold
+// the X image until the first product has read it) and the pulled deviations (staged there during
+// the network, so that a thread holds few registers); the BF16 weights are shared by the groups.
+// TMEM: layer 1's accumulator at the group's columns 0..127, layer 2's at the same columns once
+// the first epilogue has read them, the output at 0..47. Waits on the tensor cores are bounded in
+// time; only named barriers of the group synchronise it.
+namespace ws {
+constexpr int GROUPS = 3;
+constexpr int THREADS = GROUPS * TILE;
+constexpr int SLOT_D = NPOP * TILE * 4;     // [37][128] floats
+constexpr int SCRATCH_TILE = NPOP * 1024;   // floats: a tile's plain result, [37][32 rows][32]
+constexpr int COPY_V4 = NPOP * 32 * 8;      // 16-byte pieces of a tile
+constexpr int OFF_W1 = 0;
+constexpr int OFF_W2 = OFF_W1 + BYTES_W1;
+constexpr int OFF_W3 = OFF_W2 + BYTES_W2;
+constexpr int OFF_H = OFF_W3 + BYTES_W3;    // per group
+constexpr int OFF_D = OFF_H + GROUPS * BYTES_H;
+constexpr int OFF_C = OFF_D + GROUPS * SLOT_D;
+constexpr int OFF_RED = OFF_C + FC_FLOATS * 4;  // 8 floats per group
+constexpr int OFF_BAR = OFF_RED + GROUPS * 32;
+constexpr int OFF_TSLOT = OFF_BAR + GROUPS * 8;
+constexpr int BYTES = OFF_TSLOT + 16;
+static_assert(BYTES <= 232448, "the learned step needs one SM's shared memory");
+static_assert(BYTES_X <= BYTES_H, "the X image lives in the H image");
+static_assert(OFF_H % 128 == 0 && BYTES_H % 128 == 0 && OFF_D % 16 == 0 && OFF_BAR % 8 == 0, "alignment");
+
+struct Group {
+    char* sm;
+    const float* cst;
+    char* H;
+    float* D;
+    float* red;
+    uint64_t* bar;
+    uint32_t tm;  // the group's TMEM columns
+    uint32_t ph;  // phase of the group's barrier
+    int q, wq, id;
+};
+
+// An empty asm the compiler must assume changes the fields of s (no instruction is emitted).
+__device__ __forceinline__ void opaque(SplitPre& s) {
+    asm volatile("" : "+r"(s.p.n0), "+r"(s.p.nx), "+r"(s.p.ny), "+r"(s.p.ne), "+f"(s.p.r0), "+f"(s.p.rx),
+                 "+f"(s.p.ry), "+f"(s.p.re), "+f"(s.s0), "+f"(s.rho), "+f"(s.ux), "+f"(s.uy), "+f"(s.T));
+}
+
+// The three products and epilogues of one sub-tile, whose inputs the group has written as the X
+// image; the network's output (without b3) for this thread's site in y. False if a wait gave up
+// (the whole group then returns false).
+__device__ __forceinline__ bool mlp_subtile(Group& g, float* y) {
+    const float* b1 = g.cst + FC_B1;
+    const float* b2 = g.cst + FC_B2;
+    float v[32];
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    tc::wg_sync(g.id);
+    for (int layer = 0; layer < 3; ++layer) {
+        if (g.q == 0) {
+            tc::fence_after_sync();
+            if (layer == 0) mma_kmajor(g.tm, g.H, g.sm + OFF_W1, KIN, HID);
+            if (layer == 1) mma_kmajor(g.tm, g.H, g.sm + OFF_W2, HID, HID);
+            if (layer == 2) mma_kmajor(g.tm, g.H, g.sm + OFF_W3, HID, NOUTP);
+            tc::mma_commit(g.bar);
         }
-        float rmax = 0.0f, fmax = 0.0f;
-        for (int sub = 0; sub < 8; ++sub) {
-            const int y = y0 + 4 * sub + (f.tid >> 5);
-            float d[NPOP];
-            Pull32<NPOP - 1>::run(src, d, x, y, P.Lx, P.Ly, P.y_periodic, P.plane);
-            SplitPre s;
-            split_pre(d, P, s, flag);
-            float xn[KIN];
+        const bool ok = tc::mbar_wait_bounded(g.bar, g.ph, WAIT_LIMIT);
+        g.ph ^= 1u;
+        if (tc::wg_any(g.id, !ok)) return false;
+        tc::fence_after_sync();
+        if (layer < 2) {
+            const float* bias = layer == 0 ? b1 : b2;
+            for (int cc = 0; cc < HID; cc += 32) {
+                tc::tmem_ld32(tmem_lane_addr(g.tm, g.wq, cc), v);
 #pragma unroll
-            for (int i = 0; i < NIN; ++i) xn[i] = (d[i] - mu_x[i]) * isd_x[i];
+                for (int j = 0; j < 32; j += 2) gelu_bias2(v[j], v[j + 1], bias[cc + j], bias[cc + j + 1]);
 #pragma unroll
-            for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
-#pragma unroll
-            for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(sm + FW_X, f.tid, k0, KIN, xn + k0);
-            float yv[NOUT];
-            if (!mlp_forward_tile(f, net, yv)) {
-                alive = false;
-                break;
+                for (int j = 0; j < 32; j += 8) store_row8(g.H, g.q, cc + j, HID, v + j);
             }
-            float dl[NPOP];
-#pragma unroll
-            for (int i = 0; i < NPOP; ++i) dl[i] = d[i] + fmaf(yv[i], sd_t[i], mu_t[i]);
-            split_project(dl, P, P, s);
-            if (check) {
-                split_collide(d, P, P, s);  // d becomes the plain collide's candidate
-                split_project(d, P, P, s);
-#pragma unroll
-                for (int i = 0; i < NPOP; ++i) {
-                    rmax = fmaxf(rmax, fabsf(dl[i] - d[i]));
-                    fmax = fmaxf(fmax, fabsf((float)shell_w(shell_of(i)) + d[i]));
-                }
-            }
-            split_store(dst, P, x, y, dl, s, flag);
+            tc::fence_async_smem();
+        } else {
+            tc::tmem_ld32(tmem_lane_addr(g.tm, g.wq, 0), y);
+            tc::tmem_ld16(tmem_lane_addr(g.tm, g.wq, 32), y + 32);
         }
-        if (!alive) break;
-        if (check) {
-            // block maxima of the residual and of |f_plain|
-            for (int o = 16; o > 0; o >>= 1) {
-                rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
-                fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+        // the group's TMEM columns (and H, for the next sub-tile's X) are free for the next product
+        tc::fence_before_sync();
+        tc::wg_sync(g.id);
+    }
+    return true;
+}
+
+// The plain result of a tile that falls back, from the group's scratch tile over the stored one.
+__device__ __forceinline__ void copy_tile(const float* scr, float* __restrict__ dst, const StepParams& P, int x0,
+                                          int y0, int q) {
+    constexpr int BATCH = 4;
+    for (int u0 = 0; u0 < COPY_V4; u0 += TILE * BATCH) {
+        float4 v4[BATCH];
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+            const int u = u0 + b * TILE + q;
+            if (u < COPY_V4) v4[b] = reinterpret_cast<const float4*>(scr)[u];
+        }
+#pragma unroll
+        for (int b = 0; b < BATCH; ++b) {
+            const int u = u0 + b * TILE + q;
+            if (u < COPY_V4) {
+                // piece u: population u / 256, row (u / 8) mod 32, 16-byte column u mod 8
+                const int j = u >> 8, row = (u >> 3) & 31, c4 = u & 7;
+                char* base = reinterpret_cast<char*>(dst + (long long)(y0 + row + HALO) * P.Lx + x0);
+                reinterpret_cast<float4*>(base + P.plane_b32[j])[c4] = v4[b];
             }
-            if ((f.tid & 31) == 0) {
-                red[f.warp] = rmax;
-                red[4 + f.warp] = fmax;
-            }
-            __syncthreads();
-            const float R = fmaxf(fmaxf(red[0], red[1]), fmaxf(red[2], red[3]));
-            const float F = fmaxf(fmaxf(red[4], red[5]), fmaxf(red[6], red[7]));
-            __syncthreads();
-            const float res = F > 0.0f ? R / F : R;
-            const int fall = !(res <= bound);
-            if (f.tid == 0) {
-                tile_mode[t] = (unsigned char)fall;
-                atomicAdd(&stats->checked, 1ull);
-                if (fall) atomicAdd(&stats->fallback, 1ull);
-                atomicMax(&stats->max_res_bits, __float_as_uint(res));
-            }
-            if (fall)
-                for (int sub = 0; sub < 8; ++sub) fp32split_site(src, dst, P, P, x, y0 + 4 * sub + (f.tid >> 5), flag);
         }
     }
-    if (!alive && f.tid == 0) atomicOr(flag, ERR_TIMEOUT);
-    fwd_teardown(f, alive);
+}
+
+// One learned tile stepped by group g. False if a wait gave up.
+__device__ __forceinline__ bool learned_tile(Group& g, const float* __restrict__ src, float* __restrict__ dst,
+                                             const StepParams& P, int t, int x0, int y0, int check, float bound,
+                                             float* scr, unsigned char* __restrict__ tile_mode,
+                                             LearnedStats* __restrict__ stats, int* flag) {
+    const int q = g.q;
+    const float* mu_x = g.cst + FC_MUX;
+    const float* isd_x = g.cst + FC_ISDX;
+    const float* b3 = g.cst + FC_B3;
+    const float* mu_t = g.cst + FC_MUT;
+    const float* sd_t = g.cst + FC_SDT;
+    float rmax = 0.0f, fmax = 0.0f;
+    for (int sub = 0; sub < 8; ++sub) {
+        const int x = x0 + (q & 31), yy = 4 * sub + (q >> 5);
+        SplitPre sp;
+        {
+            float d[NPOP];
+            pull32(src, d, P, x, y0 + yy);
+            split_pre(d, P, sp, flag);
+            float xn[KIN];
+#pragma unroll
+            for (int j = 0; j < NIN; ++j) {
+                g.D[j * TILE + q] = d[j];
+                xn[j] = (d[j] - mu_x[j]) * isd_x[j];
+            }
+#pragma unroll
+            for (int j = NIN; j < KIN; ++j) xn[j] = 0.0f;
+#pragma unroll
+            for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(g.H, q, k0, KIN, xn + k0);
+        }
+        float yv[NOUTP];
+        if (!mlp_subtile(g, yv)) return false;
+        float dl[NPOP];
+#pragma unroll
+        for (int j = 0; j < NPOP; ++j) dl[j] = g.D[j * TILE + q] + fmaf(yv[j] + b3[j], sd_t[j], mu_t[j]);
+        split_project(dl, P, P, sp);
+        if (check) {
+            // the plain result of the same sites, for the residual and (in the scratch tile) for
+            // a fallback; bit for bit the plain step's: the site fields pass an empty asm that
+            // the compiler must treat as changing them, so that no product of the projection
+            // above is shared with this one (a shared product is not fused into an FMA, a
+            // private one may be, as in the plain step)
+            opaque(sp);
+            float d[NPOP];
+#pragma unroll
+            for (int j = 0; j < NPOP; ++j) d[j] = g.D[j * TILE + q];
+            split_collide(d, P, P, sp);
+            split_project(d, P, P, sp);
+            const int o = yy * 32 + (q & 31);
+#pragma unroll
+            for (int j = 0; j < NPOP; ++j) {
+                scr[j * 1024 + o] = d[j];
+                rmax = fmaxf(rmax, fabsf(dl[j] - d[j]));
+                fmax = fmaxf(fmax, fabsf((float)shell_w(shell_of(j)) + d[j]));
+            }
+        }
+        split_store(dst, P, x, y0 + yy, dl, sp, flag);
+    }
+    if (!check) return true;
+    for (int o = 16; o > 0; o >>= 1) {
+        rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o));
+        fmax = fmaxf(fmax, __shfl_xor_sync(0xffffffffu, fmax, o));
+    }
+    if ((q & 31) == 0) {
+        g.red[g.wq] = rmax;
+        g.red[4 + g.wq] = fmax;
+    }
+    tc::wg_sync(g.id);  // also orders the group's stores above before the fallback copy below
+    const float R = fmaxf(fmaxf(g.red[0], g.red[1]), fmaxf(g.red[2], g.red[3]));
+    const float F = fmaxf(fmaxf(g.red[4], g.red[5]), fmaxf(g.red[6], g.red[7]));
+    tc::wg_sync(g.id);  // red is reused by the next tile
+    const float res = F > 0.0f ? R / F : R;
+    const int fall = !(res <= bound);
+    if (q == 0) {
+        tile_mode[t] = (unsigned char)fall;
+        atomicAdd(&stats->checked, 1ull);
+        if (fall) atomicAdd(&stats->fallback, 1ull);
+        atomicMax(&stats->max_res_bits, __float_as_uint(res));
+    }
+    if (fall) {
+        copy_tile(scr, dst, P, x0, y0, q);
+        tc::wg_sync(g.id);  // the scratch tile is rewritten by the group's next tile
+    }
+    return true;
+}
+
+}  // namespace ws
+
+// The learned LB step (see the file header and above). Lx and Ly are multiples of 32; scratch
+// holds one tile per group.
+__global__ void __launch_bounds__(ws::THREADS, 1)
+step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, const StepParams P, NetDev net,
+                    unsigned char* __restrict__ tile_mode, int check, float bound,
+                    LearnedStats* __restrict__ stats, float* scratch, int* __restrict__ flag) {
+    using namespace ws;
+    extern __shared__ __align__(1024) char sm[];
+    const int tid = threadIdx.x, gi = tid >> 7;
+    copy_to_smem(sm + OFF_W1, net.w1img, BYTES_W1);
+    copy_to_smem(sm + OFF_W2, net.w2img, BYTES_W2);
+    copy_to_smem(sm + OFF_W3, net.w3img, BYTES_W3);
+    float* cst = reinterpret_cast<float*>(sm + OFF_C);
+    for (int k = tid; k < HID; k += THREADS) {
+        cst[FC_B1 + k] = net.params[OFF_B1 + k];
+        cst[FC_B2 + k] = net.params[OFF_B2 + k];
+    }
+    for (int k = tid; k < NOUT; k += THREADS) {
+        cst[FC_B3 + k] = net.params[OFF_B3 + k];
+        cst[FC_MUX + k] = net.norm[k];
+        cst[FC_ISDX + k] = 1.0f / net.norm[NIN + k];
+        cst[FC_MUT + k] = net.norm[2 * NIN + k];
+        cst[FC_SDT + k] = net.norm[3 * NIN + k];
+    }
+    uint64_t* bars = reinterpret_cast<uint64_t*>(sm + OFF_BAR);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + OFF_TSLOT);
+    if (tid < GROUPS) tc::mbar_init(bars + tid, 1);
+    if (tid < 32) tc::tmem_alloc(tslot, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    Group g;
+    g.sm = sm;
+    g.cst = cst;
+    g.H = sm + OFF_H + gi * BYTES_H;
+    g.D = reinterpret_cast<float*>(sm + OFF_D + gi * SLOT_D);
+    g.red = reinterpret_cast<float*>(sm + OFF_RED) + 8 * gi;
+    g.bar = bars + gi;
+    g.tm = *tslot + 128u * (uint32_t)gi;
+    g.ph = 0;
+    g.q = tid & 127;
+    g.wq = (tid >> 5) & 3;
+    g.id = 1 + gi;
+    float* scr = scratch + ((size_t)blockIdx.x * GROUPS + gi) * SCRATCH_TILE;
+    const int ntx = P.Lx / 32, ntiles = ntx * (P.Ly / 32);
+    bool alive = true;
+    for (int t = blockIdx.x * GROUPS + gi; t < ntiles && alive; t += gridDim.x * GROUPS) {
+        const int x0 = (t % ntx) * 32, y0 = (t / ntx) * 32;
+        if (!check && tile_mode[t]) {
+            for (int sub = 0; sub < 8; ++sub)
+                fp32split_site(src, dst, P, P, x0 + (g.q & 31), y0 + 4 * sub + (g.q >> 5), flag);
+            continue;
+        }
+        alive = learned_tile(g, src, dst, P, t, x0, y0, check, bound, scr, tile_mode, stats, flag);
+    }
+    if (!alive && g.q == 0) atomicOr(flag, ERR_TIMEOUT);
+    tc::fence_before_sync();
+    const bool gave_up = __syncthreads_or(!alive);
+    if (tid < 32) tc::tmem_dealloc(*tslot, 512);
+    if (tid < GROUPS && !gave_up) tc::mbar_inval(bars + tid);
 }
 
 // ---- FP32 debug mode of the loss and gradient ------------------------------------------------
@@ -824,7 +1005,7 @@ lb_status set_smem_limits() {
     if (dev >= 0 && dev < MAXDEV && done[dev].load()) return LB_OK;
     L_CUDA(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES));
     L_CUDA(cudaFuncSetAttribute(mlp_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
-    L_CUDA(cudaFuncSetAttribute(step_learned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
+    L_CUDA(cudaFuncSetAttribute(step_learned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ws::BYTES));
     if (dev >= 0 && dev < MAXDEV) done[dev].store(true);
     return LB_OK;
 }
@@ -1122,6 +1303,8 @@ struct LearnedState {
     const lb_mlp* net = nullptr;
     unsigned char* tile_mode = nullptr;
     LearnedStats* stats = nullptr;
+    float* scratch = nullptr;  // plain results of the tiles in flight: one tile per group
+    int ctas = 1;
     char* mem = nullptr;
     float bound = 1e-4f;
     int check_every = 1;
@@ -1135,7 +1318,10 @@ lb_status learned_create(const lb_mlp* net, int Lx, int Ly, double bound, int ch
     LearnedState* ls = new (std::nothrow) LearnedState();
     if (!ls) return LB_ERR_ALLOC;
     const size_t ntiles = (size_t)(Lx / 32) * (Ly / 32);
-    cudaError_t e = cudaMalloc((void**)&ls->mem, 256 + (ntiles + 255) / 256 * 256);
+    ls->ctas = sm_count();  // one CTA per SM, a scratch tile per group
+    const size_t modes = (ntiles + 255) / 256 * 256;
+    cudaError_t e = cudaMalloc((void**)&ls->mem,
+                               256 + modes + (size_t)ls->ctas * ws::GROUPS * ws::SCRATCH_TILE * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
         delete ls;
@@ -1144,6 +1330,7 @@ lb_status learned_create(const lb_mlp* net, int Lx, int Ly, double bound, int ch
     }
     ls->stats = (LearnedStats*)ls->mem;
     ls->tile_mode = (unsigned char*)(ls->mem + 256);
+    ls->scratch = (float*)(ls->mem + 256 + modes);
     e = cudaMemset(ls->mem, 0, 256 + ntiles);
     if (e != cudaSuccess) {
         cudaFree(ls->mem);
@@ -1178,9 +1365,9 @@ cudaError_t launch_step_learned(const float* src, float* dst, const StepParams& 
     const int check = (ls->steps % ls->check_every) == 0;
     ls->steps += 1;
     const int ntiles = (P.Lx / 32) * (P.Ly / 32);
-    const int grid = std::min(ntiles, 2 * sm_count());
-    step_learned_kernel<<<grid, TILE, FW_BYTES, s>>>(src, dst, P, ls->net->dev(), ls->tile_mode, check, ls->bound,
-                                                     ls->stats, flag);
+    const int grid = std::min((ntiles + ws::GROUPS - 1) / ws::GROUPS, ls->ctas);
+    step_learned_kernel<<<grid, ws::THREADS, ws::BYTES, s>>>(src, dst, P, ls->net->dev(), ls->tile_mode, check,
+                                                             ls->bound, ls->stats, ls->scratch, flag);
     return cudaGetLastError();
 }
 

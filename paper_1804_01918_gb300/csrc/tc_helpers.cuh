@@ -133,6 +133,28 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* mbar, uint32_t parity) {
         : "memory");
     return ok != 0;
 }
+// Arrive on *mbar (release at CTA scope: this thread's earlier writes are visible to a thread
+// that has waited for the phase).
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(mbar)) : "memory");
+}
+
+// ---- named barriers of one warpgroup (128 threads; ids 1..15, id 0 is __syncthreads) ----
+__device__ __forceinline__ void wg_sync(int id) {
+    asm volatile("bar.sync %0, 128;" ::"r"(id) : "memory");
+}
+// Barrier of the warpgroup that also returns whether p held in any of its threads.
+__device__ __forceinline__ bool wg_any(int id, bool p) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred a, b;\n\tsetp.ne.u32 a, %1, 0;\n\tbar.red.or.pred b, %2, 128, a;\n\t"
+        "selp.u32 %0, 1, 0, b;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(id)
+        : "memory");
+    return r != 0;
+}
+
 // The GPU's global nanosecond timer.
 __device__ __forceinline__ uint64_t globaltimer_ns() {
     uint64_t t;

@@ -153,3 +153,21 @@ def test_learned_step_matches_oracle_random_state_periodic(L, orc):
     got, modes, stats, want, tl, tp = run_case(L, orc, st, 0.8, np.inf, params, norm, y_periodic=True,
                                                gx=1e-3)
     check_case(got, modes, stats, want, tl, tp)
+
+
+@pytest.mark.parametrize("bound", [np.inf, "gap"])
+def test_learned_step_with_constant_network_output_is_fp32_exact(L, orc, bound):
+    """With the last weight matrix zero the network's output is its last bias b3 exactly (the
+    third product adds zeros in FP32), so the kept tiles hold the projection of d + sd_t b3 + mu_t
+    at the FP32 bar of the plain forms, with nothing left to the BF16 network: a dropped or
+    mis-indexed b3, mu_t or sd_t, or an error in the addition or the projection fails here."""
+    _, _, wg, _ = L.velocity_set()
+    st = inputs.rayleigh_taylor(128, 96, R=2.0, seed=4)
+    params = inputs.mlp_params(7)
+    w3 = slice(128 * 37 + 128 + 128 * 128 + 128, 128 * 37 + 128 + 128 * 128 + 128 + 37 * 128)
+    params[w3] = 0.0
+    norm = inputs.mlp_norm(wg, seed=2, sd_t=1e-4, mu_t=2e-4)
+    got, modes, stats, want, _, tp = run_case(L, orc, st, 0.9, bound, params, norm)
+    _, _, w, _ = orc.velocity_set()
+    assert np.max(np.abs(want["y"])) > 0.01          # the bias is there to be dropped
+    check_case(got, modes, stats, want, FP32_BAR * w, tp)
