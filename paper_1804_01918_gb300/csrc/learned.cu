@@ -563,21 +563,25 @@ mlp_eval_kernel(NetDev net, const float* __restrict__ x, float* __restrict__ y, 
 // 32 x 32-site tiles: a group takes a whole tile and steps it in eight sub-tiles of 128 sites (four
 // rows of 32, one site per thread): pull, exact-split sums, the network (three tcgen05 products
 // issued by one thread of the group, bias + GELU epilogues from the group's 128 TMEM columns into
-// its H image), the change added and projected onto the exact moments, stored; on check steps the
-// plain collide of the same sites as well, for the tile residual and, in the group's scratch tile,
-// for a fallback, which copies it over the stored tile. While one group waits for the tensor cores
-// the other two keep the SM busy. Per group in shared memory: the H image (whose first 12 KB hold
-// the X image until the first product has read it) and the pulled deviations (staged there during
-// the network, so that a thread holds few registers); the BF16 weights are shared by the groups.
-// TMEM: layer 1's accumulator at the group's columns 0..127, layer 2's at the same columns once
-// the first epilogue has read them, the output at 0..47. Waits on the tensor cores are bounded in
-// time; only named barriers of the group synchronise it.
+// its H image), the change added and projected onto the exact moments, stored. On check steps the
+// group evaluates the plain collide of the same sites while its first product runs, for the tile
+// residual and, in the group's scratch tile, for a fallback, which copies it over the stored tile.
+// While one group waits for the tensor cores the other two keep the SM busy. Per group in shared
+// memory: the H image (whose first 12 KB hold the X image until the first product has read it) and
+// the pulled deviations (staged there during the network, so that a thread holds few registers);
+// the BF16 weights are shared by the groups. TMEM: layer 1's accumulator at the group's columns
+// 0..127, layer 2's at the same columns once the first epilogue has read them, the output at
+// 0..47; the plain result waits for the residual in 37 of the spare columns 384..511. Waits on the
+// tensor cores are bounded in time; only named barriers of the group synchronise it.
 namespace ws {
 constexpr int GROUPS = 3;
 constexpr int THREADS = GROUPS * TILE;
 constexpr int SLOT_D = NPOP * TILE * 4;     // [37][128] floats
 constexpr int SCRATCH_TILE = NPOP * 1024;   // floats: a tile's plain result, [37][32 rows][32]
 constexpr int COPY_V4 = NPOP * 32 * 8;      // 16-byte pieces of a tile
+// TMEM: the groups' networks at columns 0..383, their plain results (37 columns) from 384 on
+constexpr int PLAIN_COL = GROUPS * 128, PLAIN_STRIDE = 40;
+static_assert(PLAIN_COL + (GROUPS - 1) * PLAIN_STRIDE + NPOP <= 512, "TMEM columns");
 constexpr int OFF_W1 = 0;
 constexpr int OFF_W2 = OFF_W1 + BYTES_W1;
 constexpr int OFF_W3 = OFF_W2 + BYTES_W2;
@@ -599,7 +603,8 @@ struct Group {
     float* D;
     float* red;
     uint64_t* bar;
-    uint32_t tm;  // the group's TMEM columns
+    uint32_t tm;  // the group's TMEM columns (lane 0)
+    uint32_t tp;  // this warp's lanes at the group's plain-result columns
     uint32_t ph;  // phase of the group's barrier
     int q, wq, id;
 };
@@ -610,24 +615,27 @@ __device__ __forceinline__ void opaque(SplitPre& s) {
                  "+f"(s.p.ry), "+f"(s.p.re), "+f"(s.s0), "+f"(s.rho), "+f"(s.ux), "+f"(s.uy), "+f"(s.T));
 }
 
-// The three products and epilogues of one sub-tile, whose inputs the group has written as the X
-// image; the network's output (without b3) for this thread's site in y. False if a wait gave up
-// (the whole group then returns false).
-__device__ __forceinline__ bool mlp_subtile(Group& g, float* y) {
-    const float* b1 = g.cst + FC_B1;
-    const float* b2 = g.cst + FC_B2;
-    float v[32];
+// The first product of a sub-tile whose inputs the group has written as the X image: the group
+// synchronises and one thread issues it (the threads may work on before mlp_finish).
+__device__ __forceinline__ void mlp_begin(Group& g) {
     tc::fence_async_smem();
     tc::fence_before_sync();
     tc::wg_sync(g.id);
+    if (g.q == 0) {
+        tc::fence_after_sync();
+        mma_kmajor(g.tm, g.H, g.sm + OFF_W1, KIN, HID);
+        tc::mma_commit(g.bar);
+    }
+}
+
+// The rest of the network for the sub-tile: the two epilogues and products that follow, and the
+// network's output (without b3) for this thread's site in y. False if a wait gave up (the whole
+// group then returns false).
+__device__ __forceinline__ bool mlp_finish(Group& g, float* y) {
+    const float* b1 = g.cst + FC_B1;
+    const float* b2 = g.cst + FC_B2;
+    float v[32];
     for (int layer = 0; layer < 3; ++layer) {
-        if (g.q == 0) {
-            tc::fence_after_sync();
-            if (layer == 0) mma_kmajor(g.tm, g.H, g.sm + OFF_W1, KIN, HID);
-            if (layer == 1) mma_kmajor(g.tm, g.H, g.sm + OFF_W2, HID, HID);
-            if (layer == 2) mma_kmajor(g.tm, g.H, g.sm + OFF_W3, HID, NOUTP);
-            tc::mma_commit(g.bar);
-        }
         const bool ok = tc::mbar_wait_bounded(g.bar, g.ph, WAIT_LIMIT);
         g.ph ^= 1u;
         if (tc::wg_any(g.id, !ok)) return false;
@@ -649,6 +657,11 @@ __device__ __forceinline__ bool mlp_subtile(Group& g, float* y) {
         // the group's TMEM columns (and H, for the next sub-tile's X) are free for the next product
         tc::fence_before_sync();
         tc::wg_sync(g.id);
+        if (layer < 2 && g.q == 0) {
+            tc::fence_after_sync();
+            mma_kmajor(g.tm, g.H, g.sm + (layer == 0 ? OFF_W2 : OFF_W3), HID, layer == 0 ? HID : NOUTP);
+            tc::mma_commit(g.bar);
+        }
     }
     return true;
 }
@@ -706,32 +719,42 @@ __device__ __forceinline__ bool learned_tile(Group& g, const float* __restrict__
             for (int j = NIN; j < KIN; ++j) xn[j] = 0.0f;
 #pragma unroll
             for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(g.H, q, k0, KIN, xn + k0);
+            mlp_begin(g);
+            if (check) {
+                // while the first product runs: the plain result of the same sites (the plain
+                // step's arithmetic in the plain step's order), for the residual (parked in the
+                // group's spare TMEM columns) and, in the scratch tile, for a fallback
+                split_collide(d, P, P, sp);
+                split_project(d, P, P, sp);
+                const int o = yy * 32 + (q & 31);
+#pragma unroll
+                for (int j = 0; j < NPOP; ++j) {
+                    scr[j * 1024 + o] = d[j];
+                    fmax = fmaxf(fmax, fabsf((float)shell_w(shell_of(j)) + d[j]));
+                }
+                tc::tmem_st32(g.tp, d);
+                tc::tmem_st4(g.tp + 32u, d + 32);
+                tc::tmem_st1(g.tp + 36u, d[36]);
+            }
         }
+        // no product of the plain projection above may be shared with the projection below (a
+        // shared product is not fused into an FMA, a private one may be, as in the plain step):
+        // the site fields pass an empty asm that the compiler must treat as changing them
+        opaque(sp);
         float yv[NOUTP];
-        if (!mlp_subtile(g, yv)) return false;
+        if (!mlp_finish(g, yv)) return false;
         float dl[NPOP];
 #pragma unroll
         for (int j = 0; j < NPOP; ++j) dl[j] = g.D[j * TILE + q] + fmaf(yv[j] + b3[j], sd_t[j], mu_t[j]);
         split_project(dl, P, P, sp);
         if (check) {
-            // the plain result of the same sites, for the residual and (in the scratch tile) for
-            // a fallback; bit for bit the plain step's: the site fields pass an empty asm that
-            // the compiler must treat as changing them, so that no product of the projection
-            // above is shared with this one (a shared product is not fused into an FMA, a
-            // private one may be, as in the plain step)
-            opaque(sp);
-            float d[NPOP];
+            float pl[NPOP];
+            tc::tmem_wait_st();
+            tc::tmem_ld32(g.tp, pl);
+            tc::tmem_ld4(g.tp + 32u, pl + 32);
+            pl[36] = tc::tmem_ld1(g.tp + 36u);
 #pragma unroll
-            for (int j = 0; j < NPOP; ++j) d[j] = g.D[j * TILE + q];
-            split_collide(d, P, P, sp);
-            split_project(d, P, P, sp);
-            const int o = yy * 32 + (q & 31);
-#pragma unroll
-            for (int j = 0; j < NPOP; ++j) {
-                scr[j * 1024 + o] = d[j];
-                rmax = fmaxf(rmax, fabsf(dl[j] - d[j]));
-                fmax = fmaxf(fmax, fabsf((float)shell_w(shell_of(j)) + d[j]));
-            }
+            for (int j = 0; j < NPOP; ++j) rmax = fmaxf(rmax, fabsf(dl[j] - pl[j]));
         }
         split_store(dst, P, x, y0 + yy, dl, sp, flag);
     }
@@ -804,6 +827,7 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
     g.red = reinterpret_cast<float*>(sm + OFF_RED) + 8 * gi;
     g.bar = bars + gi;
     g.tm = *tslot + 128u * (uint32_t)gi;
+    g.tp = tmem_lane_addr(*tslot, (tid >> 5) & 3, PLAIN_COL + PLAIN_STRIDE * gi);
     g.ph = 0;
     g.q = tid & 127;
     g.wq = (tid >> 5) & 3;
