@@ -164,11 +164,19 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     int* abort_flag = reinterpret_cast<int*>(sm + TR_MISC + 12);
     float* loss_sm = reinterpret_cast<float*>(sm + TR_MISC + 16);
 
-    copy_to_smem(sm + TR_W1, net.w1img, BYTES_W1);
-    copy_to_smem(sm + TR_W2, net.w2img, BYTES_W2);
-    copy_to_smem(sm + TR_W3, net.w3img, BYTES_W3);
-    copy_to_smem(sm + TR_W3T, net.w3timg, BYTES_W3T);
-    copy_to_smem(sm + TR_W2T, net.w2timg, BYTES_W2T);
+    uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + TR_MISC + 24);
+    if (tid == 0) {
+        // the five weight images (100 KB) by bulk copies, arriving on wbar while the threads
+        // gather and normalise their samples (one copy loop of 16-byte loads per thread waited for
+        // the L2 round trip ~50 times)
+        tc::mbar_init(wbar, 1);
+        tc::mbar_expect_tx(wbar, BYTES_W1 + BYTES_W2 + BYTES_W3 + BYTES_W3T + BYTES_W2T);
+        tc::bulk_g2s(sm + TR_W1, net.w1img, BYTES_W1, wbar);
+        tc::bulk_g2s(sm + TR_W2, net.w2img, BYTES_W2, wbar);
+        tc::bulk_g2s(sm + TR_W3, net.w3img, BYTES_W3, wbar);
+        tc::bulk_g2s(sm + TR_W3T, net.w3timg, BYTES_W3T, wbar);
+        tc::bulk_g2s(sm + TR_W2T, net.w2timg, BYTES_W2T, wbar);
+    }
     for (int k = tid; k < 4 * TR_GBN; k += blockDim.x) gb[k] = 0.0f;
     float* gbw = gb + warp * TR_GBN;  // this warp's slots: each written once per tile, no atomics
     if (tid == 0) {
@@ -206,7 +214,9 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     tc::fence_after_sync();
     const uint32_t tm = *tslot;
     uint32_t ph = 0;
-    bool ok = true;
+    // the weights have arrived (the products read them)
+    bool ok = !__syncthreads_or(!tc::mbar_wait_bounded(wbar, 0, WAIT_LIMIT));
+    const bool weights_ok = ok;
 
     auto issue_and_wait = [&](int which) {
         if (tid == 0) {
@@ -246,6 +256,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     const float* b3 = net.params + OFF_B3;
     float v[32];
     do {
+        if (!ok) break;
         // ---- forward ----
         issue_and_wait(0);
         if (!ok) break;
@@ -378,6 +389,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     // product can still be pending on it (a wait that gave up leaves it alone)
     if (warp == 0) tc::tmem_dealloc(tm, 512);
     if (tid == 0 && ok) tc::mbar_inval(bar);
+    if (tid == 0 && weights_ok) tc::mbar_inval(wbar);
 }
 
 // Sum the per-tile gradient partials, take an Adam step on the FP32 master parameters and
@@ -1098,6 +1110,40 @@ lb_status check_flag(int* dflag, cudaStream_t s) {
 
 }  // namespace
 
+// Host and device permutation buffers of a training run (two of each) and its per-epoch loss sums.
+struct TrainBuffers {
+    int* hperm[2] = {nullptr, nullptr};
+    int* dperm[2] = {nullptr, nullptr};
+    cudaEvent_t copied[2] = {nullptr, nullptr};
+    double* loss = nullptr;
+    ~TrainBuffers() {
+        for (int b = 0; b < 2; ++b) {
+            if (hperm[b]) cudaFreeHost(hperm[b]);
+            if (dperm[b]) cudaFree(dperm[b]);
+            if (copied[b]) cudaEventDestroy(copied[b]);
+        }
+        if (loss) cudaFree(loss);
+    }
+    lb_status alloc(long long n, int epochs) {
+        for (int b = 0; b < 2; ++b) {
+            cudaError_t e = cudaMallocHost((void**)&hperm[b], (size_t)n * sizeof(int));
+            if (e == cudaSuccess) e = cudaMalloc((void**)&dperm[b], (size_t)n * sizeof(int));
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&copied[b], cudaEventDisableTiming);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                set_last_error("MLP training buffers allocation failed");
+                return LB_ERR_ALLOC;
+            }
+        }
+        if (cudaMalloc((void**)&loss, (size_t)epochs * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_last_error("MLP training buffers allocation failed");
+            return LB_ERR_ALLOC;
+        }
+        return LB_OK;
+    }
+};
+
 extern "C" {
 
 lb_status lb_mlp_create(uint64_t seed, lb_mlp** out) {
@@ -1279,40 +1325,54 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
         }
         L_CUDA(cudaMemcpyAsync(net->norm, norm.data(), 4 * NIN * sizeof(float), cudaMemcpyHostToDevice, s));
     }
-    int* dperm = nullptr;
-    L_CUDA(cudaMalloc((void**)&dperm, (size_t)n * sizeof(int)));
-    std::vector<int> perm((size_t)n);
+    // Each epoch's permutation is drawn on the host while the GPU trains on the previous one (two
+    // pinned host buffers, two device buffers); the epochs' losses are summed into their own slots
+    // and read at the end, so the host waits for the GPU only before reusing a host buffer.
+    TrainBuffers tb;
+    st = tb.alloc(n, epochs);
+    if (st != LB_OK) return st;
     const long long nb = n / batch;
     uint64_t rs = seed;
-    for (int ep = 0; ep < epochs && st == LB_OK; ++ep) {
+    auto shuffle = [&](int* perm) {
         for (long long k = 0; k < n; ++k) perm[k] = (int)k;
         for (long long k = n - 1; k > 0; --k) {  // Fisher-Yates
             const long long j = (long long)(splitmix64(rs) % (uint64_t)(k + 1));
             std::swap(perm[k], perm[j]);
         }
-        cudaError_t e = cudaMemcpyAsync(dperm, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(sc.loss, 0, sizeof(double), s);
-        if (e == cudaSuccess) e = cudaMemsetAsync(sc.flag, 0, sizeof(int), s);
+    };
+    shuffle(tb.hperm[0]);
+    L_CUDA(cudaMemsetAsync(sc.flag, 0, sizeof(int), s));
+    L_CUDA(cudaMemsetAsync(tb.loss, 0, (size_t)epochs * sizeof(double), s));
+    for (int ep = 0; ep < epochs && st == LB_OK; ++ep) {
+        const int b = ep & 1;
+        cudaError_t e = cudaMemcpyAsync(tb.dperm[b], tb.hperm[b], (size_t)n * sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaEventRecord(tb.copied[b], s);
         if (e != cudaSuccess) {
             st = fail_l(e, "epoch setup");
             break;
         }
         for (long long bi = 0; bi < nb && st == LB_OK; ++bi)
-            st = train_batch(net, pre, post, dperm, bi * batch, ntiles, 1, lr, 1, sc.partial, sc.loss, sc.flag,
-                             nullptr, s);
-        if (st != LB_OK) break;
-        st = check_flag(sc.flag, s);
-        if (st != LB_OK) break;
-        double l = 0.0;
-        e = cudaMemcpy(&l, sc.loss, sizeof(double), cudaMemcpyDeviceToHost);
+            st = train_batch(net, pre, post, tb.dperm[b], bi * batch, ntiles, 1, lr, 1, sc.partial, tb.loss + ep,
+                             sc.flag, nullptr, s);
+        if (st != LB_OK || ep + 1 == epochs) break;
+        // the next epoch's permutation, into the host buffer whose copy (two epochs back) is done
+        e = cudaEventSynchronize(tb.copied[b ^ 1]);
         if (e != cudaSuccess) {
-            st = fail_l(e, "epoch loss");
+            st = fail_l(e, "epoch setup");
             break;
         }
-        if (epoch_loss) epoch_loss[ep] = (float)(l / ((double)nb * batch * NOUT));
+        shuffle(tb.hperm[b ^ 1]);
+    }
+    if (st == LB_OK) st = check_flag(sc.flag, s);
+    if (st == LB_OK) {
+        std::vector<double> l((size_t)epochs);
+        cudaError_t e = cudaMemcpyAsync(l.data(), tb.loss, (size_t)epochs * sizeof(double), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = fail_l(e, "epoch losses");
+        else if (epoch_loss)
+            for (int ep = 0; ep < epochs; ++ep) epoch_loss[ep] = (float)(l[ep] / ((double)nb * batch * NOUT));
     }
     cudaStreamSynchronize(s);
-    cudaFree(dperm);
     return st;
 }
 
