@@ -144,20 +144,23 @@ constexpr int TR_W3 = TR_W2 + BYTES_W2;
 constexpr int TR_W3T = TR_W3 + BYTES_W3;
 constexpr int TR_W2T = TR_W3T + BYTES_W3T;
 constexpr int TR_GBN = HID + HID + NOUTP;  // bias-gradient columns db1[128] db2[128] db3[48]
-constexpr int TR_GB = TR_W2T + BYTES_W2T;  // per-warp column sums [4][TR_GBN], added in warp order
-constexpr int TR_MISC = TR_GB + 4 * TR_GBN * 4;
+constexpr int TR_WARPS = 8;                 // two warpgroups: each epilogue's columns split in halves
+constexpr int TR_GB = TR_W2T + BYTES_W2T;  // per-warp column sums [8][TR_GBN], added in warp order
+constexpr int TR_MISC = TR_GB + TR_WARPS * TR_GBN * 4;
 constexpr int TR_BYTES = TR_MISC + 64;
 
 // One 128-sample tile: forward, loss, backward; writes this CTA's parameter-gradient partial
-// (packed like the parameters) and adds its loss sum to *loss_acc.
+// (packed like the parameters) and adds its loss sum to *loss_acc. Two warpgroups: thread q of
+// either owns sample q (TMEM lane q); each epilogue's 128 columns are split between them (columns
+// 64 wg .. 64 wg + 63), and the per-sample work (inputs, loss) is warpgroup 0's.
 //   raw = 1: a = pre deviations, b = post deviations (normalised inside);
 //   raw = 0: a = normalised inputs, b = normalised targets.
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(2 * TILE, 1)
 mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restrict__ b,
                  const int* __restrict__ perm, long long base, float inv_count, int raw,
                  float* __restrict__ partial, double* __restrict__ loss_acc, int* __restrict__ flag) {
     extern __shared__ __align__(1024) char sm[];
-    const int tid = threadIdx.x, warp = tid >> 5;
+    const int tid = threadIdx.x, warp = tid >> 5, q = tid & (TILE - 1), wg = tid >> 7, c0 = 64 * wg;
     float* gb = reinterpret_cast<float*>(sm + TR_GB);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TR_MISC);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + TR_MISC + 8);
@@ -177,7 +180,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         tc::bulk_g2s(sm + TR_W3T, net.w3timg, BYTES_W3T, wbar);
         tc::bulk_g2s(sm + TR_W2T, net.w2timg, BYTES_W2T, wbar);
     }
-    for (int k = tid; k < 4 * TR_GBN; k += blockDim.x) gb[k] = 0.0f;
+    for (int k = tid; k < TR_WARPS * TR_GBN; k += blockDim.x) gb[k] = 0.0f;
     float* gbw = gb + warp * TR_GBN;  // this warp's slots: each written once per tile, no atomics
     if (tid == 0) {
         tc::mbar_init(bar, 1);
@@ -187,10 +190,10 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     if (warp == 0) tc::tmem_alloc(tslot, 512);
 
     // ---- this thread's sample ----
-    const long long row = perm ? (long long)perm[base + (long long)blockIdx.x * TILE + tid]
-                               : base + (long long)blockIdx.x * TILE + tid;
+    const long long row = perm ? (long long)perm[base + (long long)blockIdx.x * TILE + q]
+                               : base + (long long)blockIdx.x * TILE + q;
     float xn[KIN], tn[NIN];
-    {
+    if (wg == 0) {
         const float* norm = net.norm;
 #pragma unroll
         for (int i = 0; i < NIN; ++i) {
@@ -206,7 +209,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
 #pragma unroll
         for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
 #pragma unroll
-        for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(sm + TR_X, tid, k0, KIN, xn + k0);
+        for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(sm + TR_X, q, k0, KIN, xn + k0);
     }
     tc::fence_async_smem();
     tc::fence_before_sync();
@@ -260,28 +263,28 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         // ---- forward ----
         issue_and_wait(0);
         if (!ok) break;
-        for (int c = 0; c < HID; c += 32) {
+        for (int c = c0; c < c0 + 64; c += 32) {
             tc::tmem_ld32(tmem_lane_addr(tm, warp, c), v);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) gelu_bias2(v[j], v[j + 1], b1[c + j], b1[c + j + 1]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, q, c + j, HID, v + j);
         }
         sync_for_mma();
         issue_and_wait(1);
         if (!ok) break;
-        for (int c = 0; c < HID; c += 32) {
+        for (int c = c0; c < c0 + 64; c += 32) {
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), v);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) gelu_bias2(v[j], v[j + 1], b2[c + j], b2[c + j + 1]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, q, c + j, HID, v + j);
         }
         sync_for_mma();
         issue_and_wait(2);
         if (!ok) break;
         // ---- output, loss and its gradient ----
-        {
+        if (wg == 0) {
             float yv[NOUTP];
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 256), yv);
             tc::tmem_ld16(tmem_lane_addr(tm, warp, 288), yv + 32);
@@ -297,7 +300,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
                 }
             }
 #pragma unroll
-            for (int j = 0; j < NOUTP; j += 8) store_row8(sm + TR_DY, tid, j, NOUTP, dy + j);
+            for (int j = 0; j < NOUTP; j += 8) store_row8(sm + TR_DY, q, j, NOUTP, dy + j);
             // db3: warp column sums, then one shared atomic per column and warp
             float cs[32];
 #pragma unroll
@@ -314,41 +317,41 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         issue_and_wait(3);
         if (!ok) break;
         // ---- dZ2 = dH2 * gelu'(z2) into the H2 buffer; dW3^T partial ----
-        for (int c = 0; c < HID; c += 32) {
+        for (int c = c0; c < c0 + 64; c += 32) {
             float z[32];
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 128 + c), z);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) gelu_grad_bias2(v[j], v[j + 1], z[j], z[j + 1], b2[c + j], b2[c + j + 1]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, tid, c + j, HID, v + j);
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H2, q, c + j, HID, v + j);
             gbw[HID + c + (tid & 31)] = warp_column_sums(v);
         }
-        {
+        if (wg == 1) {
             float g[NOUTP];
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 304), g);
             tc::tmem_ld16(tmem_lane_addr(tm, warp, 336), g + 32);
             float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W3;
 #pragma unroll
-            for (int j = 0; j < NOUT; ++j) out[j * HID + tid] = g[j];  // dW3[j][h], h = this lane
+            for (int j = 0; j < NOUT; ++j) out[j * HID + q] = g[j];  // dW3[j][h], h = this lane
         }
         sync_for_mma();
         issue_and_wait(4);
         if (!ok) break;
         // ---- dZ1 = dH1 * gelu'(z1) into the H1 buffer; dW2 partial ----
-        for (int c = 0; c < HID; c += 32) {
+        for (int c = c0; c < c0 + 64; c += 32) {
             float z[32];
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 384 + c), v);
             tc::tmem_ld32(tmem_lane_addr(tm, warp, c), z);
 #pragma unroll
             for (int j = 0; j < 32; j += 2) gelu_grad_bias2(v[j], v[j + 1], z[j], z[j + 1], b1[c + j], b1[c + j + 1]);
 #pragma unroll
-            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, tid, c + j, HID, v + j);
+            for (int j = 0; j < 32; j += 8) store_row8(sm + TR_H1, q, c + j, HID, v + j);
             gbw[c + (tid & 31)] = warp_column_sums(v);
         }
         {
-            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W2 + (size_t)tid * HID;  // row o
-            for (int c = 0; c < HID; c += 32) {
+            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W2 + (size_t)q * HID;  // row o
+            for (int c = c0; c < c0 + 64; c += 32) {
                 tc::tmem_ld32(tmem_lane_addr(tm, warp, 256 + c), v);
 #pragma unroll
                 for (int j = 0; j < 32; j += 4)
@@ -358,11 +361,11 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         sync_for_mma();
         issue_and_wait(5);
         if (!ok) break;
-        {
+        if (wg == 0) {
             float g[NOUTP];
             tc::tmem_ld32(tmem_lane_addr(tm, warp, 128), g);
             tc::tmem_ld16(tmem_lane_addr(tm, warp, 160), g + 32);
-            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W1 + (size_t)tid * NIN;  // row o
+            float* out = partial + (size_t)blockIdx.x * PART_STRIDE + OFF_W1 + (size_t)q * NIN;  // row o
 #pragma unroll
             for (int i = 0; i < NIN; ++i) out[i] = g[i];
         }
@@ -371,8 +374,11 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     __syncthreads();
     if (ok) {
         float* out = partial + (size_t)blockIdx.x * PART_STRIDE;
-        auto col = [&](int k) {  // the four warps' column sums, added in warp order
-            return ((gb[k] + gb[TR_GBN + k]) + gb[2 * TR_GBN + k]) + gb[3 * TR_GBN + k];
+        auto col = [&](int k) {  // the warps' column sums (zero where a warp has none), in warp order
+            float a = gb[k];
+#pragma unroll
+            for (int w = 1; w < TR_WARPS; ++w) a += gb[w * TR_GBN + k];
+            return a;
         };
         for (int k = tid; k < HID; k += blockDim.x) {
             out[OFF_B1 + k] = col(k);
@@ -1052,8 +1058,8 @@ lb_status train_batch(lb_mlp* net, const float* a, const float* b, const int* pe
                       int ntiles, int raw, float lr, int apply, float* partial, double* loss_acc,
                       int* flag, float* grad_out, cudaStream_t s) {
     const float inv_count = 1.0f / ((float)ntiles * TILE * NOUT);
-    mlp_train_kernel<<<ntiles, TILE, TR_BYTES, s>>>(net->dev(), a, b, perm, base, inv_count, raw, partial,
-                                                    loss_acc, flag);
+    mlp_train_kernel<<<ntiles, 2 * TILE, TR_BYTES, s>>>(net->dev(), a, b, perm, base, inv_count, raw, partial,
+                                                        loss_acc, flag);
     L_CUDA(cudaGetLastError());
     float bc1 = 1.0f, bc2 = 1.0f;
     if (apply) {
