@@ -146,52 +146,157 @@ constexpr int TR_W2T = TR_W3T + BYTES_W3T;
 constexpr int TR_GBN = HID + HID + NOUTP;  // bias-gradient columns db1[128] db2[128] db3[48]
 constexpr int TR_WARPS = 8;                 // two warpgroups: each epilogue's columns split in halves
 constexpr int TR_GB = TR_W2T + BYTES_W2T;  // per-warp column sums [8][TR_GBN], added in warp order
-constexpr int TR_MISC = TR_GB + TR_WARPS * TR_GBN * 4;
+constexpr int TR_BIAS = TR_GB + TR_WARPS * TR_GBN * 4;  // b1[128] b2[128] b3[48] of this batch
+constexpr int TR_MISC = TR_BIAS + TR_GBN * 4;
 constexpr int TR_BYTES = TR_MISC + 64;
 
-// One 128-sample tile: forward, loss, backward; writes this CTA's parameter-gradient partial
-// (packed like the parameters) and adds its loss sum to *loss_acc. Two warpgroups: thread q of
-// either owns sample q (TMEM lane q); each epilogue's 128 columns are split between them (columns
-// 64 wg .. 64 wg + 63), and the per-sample work (inputs, loss) is warpgroup 0's.
+// Parameter p: the sum of the per-tile gradient partials, then (apply) an Adam step on the FP32
+// master parameter and its BF16 entries in the operand images. The arithmetic is written with
+// explicit roundings, so that it is the same wherever it is inlined.
+__device__ __forceinline__ void adam_param(int p, float* __restrict__ params, float* __restrict__ m,
+                                           float* __restrict__ vv, const float* partial, int nparts, float lr,
+                                           float bc1, float bc2, int apply, float* __restrict__ grad_out,
+                                           char* __restrict__ w1img, char* __restrict__ w2img,
+                                           char* __restrict__ w3img, char* __restrict__ w3timg,
+                                           char* __restrict__ w2timg) {
+    // (from L2: in a training loop the partials were written by other CTAs of the same launch)
+    float g = 0.0f;
+    for (int c = 0; c < nparts; ++c) g += __ldcg(partial + (size_t)c * PART_STRIDE + p);
+    if (grad_out) grad_out[p] = g;
+    if (!apply) return;
+    const float b1c = 0.9f, b2c = 0.999f;
+    const float mm = __fmaf_rn(b1c, m[p], __fmul_rn(1.0f - b1c, g));
+    const float vn = __fmaf_rn(b2c, vv[p], __fmul_rn(__fmul_rn(1.0f - b2c, g), g));
+    m[p] = mm;
+    vv[p] = vn;
+    const float step = __fdiv_rn(__fdiv_rn(mm, bc1), __fadd_rn(__fsqrt_rn(__fdiv_rn(vn, bc2)), 1e-8f));
+    const float w = __fsub_rn(params[p], __fmul_rn(lr, step));
+    params[p] = w;
+    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
+    if (p < OFF_B1) {
+        const int o = (p - OFF_W1) / NIN, i = (p - OFF_W1) % NIN;
+        *reinterpret_cast<__nv_bfloat16*>(w1img + elem_off(o, i, KIN)) = wb;
+    } else if (p >= OFF_W2 && p < OFF_B2) {
+        const int o = (p - OFF_W2) / HID, i = (p - OFF_W2) % HID;
+        *reinterpret_cast<__nv_bfloat16*>(w2img + elem_off(o, i, HID)) = wb;
+        *reinterpret_cast<__nv_bfloat16*>(w2timg + elem_off(i, o, HID)) = wb;
+    } else if (p >= OFF_W3 && p < OFF_B3) {
+        const int j = (p - OFF_W3) / HID, h = (p - OFF_W3) % HID;
+        *reinterpret_cast<__nv_bfloat16*>(w3img + elem_off(j, h, HID)) = wb;
+        *reinterpret_cast<__nv_bfloat16*>(w3timg + elem_off(h, j, NOUTP)) = wb;
+    }
+}
+
+// A bounded barrier of all CTAs of a cooperative launch (bar[0] counts arrivals, bar[1] is the
+// generation): false if it was not reached by all within the wait limit.
+__device__ __forceinline__ bool grid_barrier(unsigned* bar, int* shared_ok) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned gen;
+        asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(gen) : "l"(bar + 1) : "memory");
+        __threadfence();  // this CTA's writes before its arrival
+        if (atomicAdd(bar, 1u) + 1u == gridDim.x) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(bar + 1), "r"(gen + 1u) : "memory");
+        } else {
+            const uint64_t t0 = tc::globaltimer_ns();
+            for (;;) {
+                unsigned g;
+                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(g) : "l"(bar + 1) : "memory");
+                if (g != gen) break;
+                if (tc::globaltimer_ns() - t0 > WAIT_LIMIT) {
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *shared_ok = ok;
+    }
+    __syncthreads();
+    return *shared_ok != 0;
+}
+
+// Per-batch arguments of an in-kernel training loop (kLoop): the batches' Adam bias corrections
+// (bc[2 b], bc[2 b + 1]), the master parameters and moments, the operand images and the grid
+// barrier's two words.
+struct TrainLoop {
+    const float* bc;
+    float* params;
+    float* m;
+    float* v;
+    char* img[5];
+    float lr;
+    unsigned* bar;
+};
+
+// One 128-sample tile per CTA and batch: forward, loss, backward; writes this CTA's
+// parameter-gradient partial (packed like the parameters) and adds its loss sum to *loss_acc. Two
+// warpgroups: thread q of either owns sample q (TMEM lane q); each epilogue's 128 columns are
+// split between them (columns 64 wg .. 64 wg + 63), and the per-sample work (inputs, loss) is
+// warpgroup 0's. kLoop: a cooperative launch that trains on nbatch consecutive batches of the
+// permutation, all CTAs together: after each batch a grid barrier, the Adam step with the
+// parameters spread over all threads, a second barrier, and the next batch reloads the weights
+// and biases. Otherwise one batch (nbatch = 1) whose Adam step is a separate kernel.
 //   raw = 1: a = pre deviations, b = post deviations (normalised inside);
 //   raw = 0: a = normalised inputs, b = normalised targets.
+template <bool kLoop>
 __global__ void __launch_bounds__(2 * TILE, 1)
 mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restrict__ b,
-                 const int* __restrict__ perm, long long base, float inv_count, int raw,
-                 float* __restrict__ partial, double* __restrict__ loss_acc, int* __restrict__ flag) {
+                 const int* __restrict__ perm, long long base, int nbatch, float inv_count, int raw,
+                 float* __restrict__ partial, double* __restrict__ loss_acc, int* __restrict__ flag, TrainLoop L) {
     extern __shared__ __align__(1024) char sm[];
     const int tid = threadIdx.x, warp = tid >> 5, q = tid & (TILE - 1), wg = tid >> 7, c0 = 64 * wg;
     float* gb = reinterpret_cast<float*>(sm + TR_GB);
     uint64_t* bar = reinterpret_cast<uint64_t*>(sm + TR_MISC);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + TR_MISC + 8);
-    int* abort_flag = reinterpret_cast<int*>(sm + TR_MISC + 12);
+    int* shared_ok = reinterpret_cast<int*>(sm + TR_MISC + 12);
     float* loss_sm = reinterpret_cast<float*>(sm + TR_MISC + 16);
-
     uint64_t* wbar = reinterpret_cast<uint64_t*>(sm + TR_MISC + 24);
+    float* bias = reinterpret_cast<float*>(sm + TR_BIAS);
+    float* gbw = gb + warp * TR_GBN;  // this warp's slots: each written once per tile, no atomics
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        tc::mbar_init(wbar, 1);
+    }
+    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tm = *tslot;
+    uint32_t ph = 0;
+    bool ok = true, weights_ok = true;
+    const int batch = (int)gridDim.x * TILE;
+    for (int bi = 0; bi < nbatch && ok; ++bi) {
     if (tid == 0) {
         // the five weight images (100 KB) by bulk copies, arriving on wbar while the threads
-        // gather and normalise their samples (one copy loop of 16-byte loads per thread waited for
-        // the L2 round trip ~50 times)
-        tc::mbar_init(wbar, 1);
+        // gather and normalise their samples (a copy loop of 16-byte loads per thread waited for
+        // the L2 round trip ~50 times); in a training loop they were just rewritten by the
+        // previous batch's Adam step (generic stores): the proxy fence orders those before the
+        // asynchronous copy's reads
+        if (kLoop) asm volatile("fence.proxy.async.global;" ::: "memory");
         tc::mbar_expect_tx(wbar, BYTES_W1 + BYTES_W2 + BYTES_W3 + BYTES_W3T + BYTES_W2T);
         tc::bulk_g2s(sm + TR_W1, net.w1img, BYTES_W1, wbar);
         tc::bulk_g2s(sm + TR_W2, net.w2img, BYTES_W2, wbar);
         tc::bulk_g2s(sm + TR_W3, net.w3img, BYTES_W3, wbar);
         tc::bulk_g2s(sm + TR_W3T, net.w3timg, BYTES_W3T, wbar);
         tc::bulk_g2s(sm + TR_W2T, net.w2timg, BYTES_W2T, wbar);
-    }
-    for (int k = tid; k < TR_WARPS * TR_GBN; k += blockDim.x) gb[k] = 0.0f;
-    float* gbw = gb + warp * TR_GBN;  // this warp's slots: each written once per tile, no atomics
-    if (tid == 0) {
-        tc::mbar_init(bar, 1);
-        *abort_flag = 0;
         *loss_sm = 0.0f;
     }
-    if (warp == 0) tc::tmem_alloc(tslot, 512);
+    for (int k = tid; k < TR_WARPS * TR_GBN; k += blockDim.x) gb[k] = 0.0f;
+    // this batch's biases (from L2: in a training loop another CTA's Adam step may have just
+    // rewritten them)
+    for (int k = tid; k < 2 * HID + NOUT; k += blockDim.x) {
+        const int off = k < HID ? OFF_B1 + k : k < 2 * HID ? OFF_B2 + (k - HID) : OFF_B3 + (k - 2 * HID);
+        bias[k] = __ldcg(net.params + off);
+    }
+    const long long tile0 = base + (long long)bi * batch + (long long)blockIdx.x * TILE;
 
     // ---- this thread's sample ----
-    const long long row = perm ? (long long)perm[base + (long long)blockIdx.x * TILE + q]
-                               : base + (long long)blockIdx.x * TILE + q;
+    const long long row = perm ? (long long)perm[tile0 + q] : tile0 + q;
     float xn[KIN], tn[NIN];
     if (wg == 0) {
         const float* norm = net.norm;
@@ -215,11 +320,9 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    const uint32_t tm = *tslot;
-    uint32_t ph = 0;
     // the weights have arrived (the products read them)
-    bool ok = !__syncthreads_or(!tc::mbar_wait_bounded(wbar, 0, WAIT_LIMIT));
-    const bool weights_ok = ok;
+    ok = !__syncthreads_or(!tc::mbar_wait_bounded(wbar, (uint32_t)(bi & 1), WAIT_LIMIT));
+    weights_ok = ok;
 
     auto issue_and_wait = [&](int which) {
         if (tid == 0) {
@@ -254,9 +357,9 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         tc::fence_after_sync();
     };
 
-    const float* b1 = net.params + OFF_B1;
-    const float* b2 = net.params + OFF_B2;
-    const float* b3 = net.params + OFF_B3;
+    const float* b1 = bias;
+    const float* b2 = bias + HID;
+    const float* b3 = bias + 2 * HID;
     float v[32];
     do {
         if (!ok) break;
@@ -386,9 +489,22 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         }
         for (int k = tid; k < NOUT; k += blockDim.x) out[OFF_B3 + k] = col(2 * HID + k);
         if (tid == 0) atomicAdd(loss_acc, (double)*loss_sm);
-    } else if (tid == 0) {
-        atomicOr(flag, ERR_TIMEOUT);
     }
+    if (kLoop && ok) {
+        // all partials written -> the Adam step, the parameters spread over the grid's threads ->
+        // the new weights written before any CTA reloads them
+        ok = grid_barrier(L.bar, shared_ok);
+        if (ok) {
+            const float* bcb = L.bc + 2 * bi;
+            for (int p = blockIdx.x * blockDim.x + tid; p < NPARAM; p += gridDim.x * blockDim.x)
+                adam_param(p, L.params, L.m, L.v, partial, gridDim.x, L.lr, bcb[0], bcb[1], 1, nullptr, L.img[0],
+                           L.img[1], L.img[2], L.img[3], L.img[4]);
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            ok = grid_barrier(L.bar, shared_ok);
+        }
+    }
+    }  // batches
+    if (!ok && tid == 0) atomicOr(flag, ERR_TIMEOUT);
     tc::fence_before_sync();
     __syncthreads();
     // TMEM must be released before the block exits; the barrier is invalidated only when no
@@ -398,39 +514,16 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     if (tid == 0 && weights_ok) tc::mbar_inval(wbar);
 }
 
-// Sum the per-tile gradient partials, take an Adam step on the FP32 master parameters and
-// re-pack the BF16 operand images. One thread per parameter.
+// One thread per parameter (the training batches launched one by one).
 __global__ void adam_kernel(float* __restrict__ params, float* __restrict__ m, float* __restrict__ vv,
                             const float* __restrict__ partial, int nparts, float lr, float bc1, float bc2,
                             int apply, float* __restrict__ grad_out, char* __restrict__ w1img,
                             char* __restrict__ w2img, char* __restrict__ w3img, char* __restrict__ w3timg,
                             char* __restrict__ w2timg) {
     const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= NPARAM) return;
-    float g = 0.0f;
-    for (int c = 0; c < nparts; ++c) g += partial[(size_t)c * PART_STRIDE + p];
-    if (grad_out) grad_out[p] = g;
-    if (!apply) return;
-    const float b1c = 0.9f, b2c = 0.999f;
-    const float mm = b1c * m[p] + (1.0f - b1c) * g;
-    const float vn = b2c * vv[p] + (1.0f - b2c) * g * g;
-    m[p] = mm;
-    vv[p] = vn;
-    const float w = params[p] - lr * (mm / bc1) / (sqrtf(vn / bc2) + 1e-8f);
-    params[p] = w;
-    const __nv_bfloat16 wb = __float2bfloat16_rn(w);
-    if (p < OFF_B1) {
-        const int o = (p - OFF_W1) / NIN, i = (p - OFF_W1) % NIN;
-        *reinterpret_cast<__nv_bfloat16*>(w1img + elem_off(o, i, KIN)) = wb;
-    } else if (p >= OFF_W2 && p < OFF_B2) {
-        const int o = (p - OFF_W2) / HID, i = (p - OFF_W2) % HID;
-        *reinterpret_cast<__nv_bfloat16*>(w2img + elem_off(o, i, HID)) = wb;
-        *reinterpret_cast<__nv_bfloat16*>(w2timg + elem_off(i, o, HID)) = wb;
-    } else if (p >= OFF_W3 && p < OFF_B3) {
-        const int j = (p - OFF_W3) / HID, h = (p - OFF_W3) % HID;
-        *reinterpret_cast<__nv_bfloat16*>(w3img + elem_off(j, h, HID)) = wb;
-        *reinterpret_cast<__nv_bfloat16*>(w3timg + elem_off(h, j, NOUTP)) = wb;
-    }
+    if (p < NPARAM)
+        adam_param(p, params, m, vv, partial, nparts, lr, bc1, bc2, apply, grad_out, w1img, w2img, w3img,
+                   w3timg, w2timg);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -1045,7 +1138,8 @@ lb_status set_smem_limits() {
     int dev = 0;
     L_CUDA(cudaGetDevice(&dev));
     if (dev >= 0 && dev < MAXDEV && done[dev].load()) return LB_OK;
-    L_CUDA(cudaFuncSetAttribute(mlp_train_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES));
+    L_CUDA(cudaFuncSetAttribute(mlp_train_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES));
+    L_CUDA(cudaFuncSetAttribute(mlp_train_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, TR_BYTES));
     L_CUDA(cudaFuncSetAttribute(mlp_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, FW_BYTES));
     L_CUDA(cudaFuncSetAttribute(step_learned_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ws::BYTES));
     if (dev >= 0 && dev < MAXDEV) done[dev].store(true);
@@ -1058,8 +1152,8 @@ lb_status train_batch(lb_mlp* net, const float* a, const float* b, const int* pe
                       int ntiles, int raw, float lr, int apply, float* partial, double* loss_acc,
                       int* flag, float* grad_out, cudaStream_t s) {
     const float inv_count = 1.0f / ((float)ntiles * TILE * NOUT);
-    mlp_train_kernel<<<ntiles, 2 * TILE, TR_BYTES, s>>>(net->dev(), a, b, perm, base, inv_count, raw, partial,
-                                                        loss_acc, flag);
+    mlp_train_kernel<false><<<ntiles, 2 * TILE, TR_BYTES, s>>>(net->dev(), a, b, perm, base, 1, inv_count, raw,
+                                                               partial, loss_acc, flag, TrainLoop{});
     L_CUDA(cudaGetLastError());
     float bc1 = 1.0f, bc2 = 1.0f;
     if (apply) {
@@ -1072,6 +1166,39 @@ lb_status train_batch(lb_mlp* net, const float* a, const float* b, const int* pe
                                                      net->img[3], net->img[4]);
     L_CUDA(cudaGetLastError());
     return LB_OK;
+}
+
+// All batches of one epoch in one cooperative launch (mlp_train_kernel<true>); bc holds the
+// batches' Adam bias corrections, gbar two words for the grid barrier (zeroed here).
+lb_status train_epoch_loop(lb_mlp* net, const float* a, const float* b, const int* perm, int nbatch, int ntiles,
+                           float lr, const float* bc, float* partial, double* loss_acc, int* flag, unsigned* gbar,
+                           cudaStream_t s) {
+    L_CUDA(cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), s));
+    NetDev nd = net->dev();
+    long long base = 0;
+    int raw = 1;
+    float inv_count = 1.0f / ((float)ntiles * TILE * NOUT);
+    TrainLoop L{bc, net->params, net->m, net->v, {net->img[0], net->img[1], net->img[2], net->img[3], net->img[4]},
+                lr, gbar};
+    void* args[] = {&nd, (void*)&a, (void*)&b, (void*)&perm, &base, &nbatch, &inv_count, &raw, &partial,
+                    &loss_acc, &flag, &L};
+    L_CUDA(cudaLaunchCooperativeKernel((const void*)mlp_train_kernel<true>, dim3(ntiles), dim3(2 * TILE), args,
+                                       (size_t)TR_BYTES, s));
+    net->adam_steps += nbatch;
+    return LB_OK;
+}
+
+// Whether ntiles training CTAs can all be resident at once (the cooperative launch's condition).
+bool train_loop_fits(int ntiles) {
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return false;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_train_kernel<true>, 2 * TILE, TR_BYTES) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return (long long)per_sm * sm_count() >= ntiles;
 }
 
 struct Scratch {
@@ -1122,6 +1249,8 @@ struct TrainBuffers {
     int* dperm[2] = {nullptr, nullptr};
     cudaEvent_t copied[2] = {nullptr, nullptr};
     double* loss = nullptr;
+    float* bc = nullptr;       // Adam bias corrections of every batch of the run (training loop)
+    unsigned* gbar = nullptr;  // grid barrier words (training loop)
     ~TrainBuffers() {
         for (int b = 0; b < 2; ++b) {
             if (hperm[b]) cudaFreeHost(hperm[b]);
@@ -1129,8 +1258,10 @@ struct TrainBuffers {
             if (copied[b]) cudaEventDestroy(copied[b]);
         }
         if (loss) cudaFree(loss);
+        if (bc) cudaFree(bc);
+        if (gbar) cudaFree(gbar);
     }
-    lb_status alloc(long long n, int epochs) {
+    lb_status alloc(long long n, int epochs, long long nbatches) {
         for (int b = 0; b < 2; ++b) {
             cudaError_t e = cudaMallocHost((void**)&hperm[b], (size_t)n * sizeof(int));
             if (e == cudaSuccess) e = cudaMalloc((void**)&dperm[b], (size_t)n * sizeof(int));
@@ -1141,7 +1272,9 @@ struct TrainBuffers {
                 return LB_ERR_ALLOC;
             }
         }
-        if (cudaMalloc((void**)&loss, (size_t)epochs * sizeof(double)) != cudaSuccess) {
+        if (cudaMalloc((void**)&loss, (size_t)epochs * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void**)&bc, (size_t)nbatches * 2 * sizeof(float)) != cudaSuccess ||
+            cudaMalloc((void**)&gbar, 2 * sizeof(unsigned)) != cudaSuccess) {
             cudaGetLastError();
             set_last_error("MLP training buffers allocation failed");
             return LB_ERR_ALLOC;
@@ -1335,9 +1468,22 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
     // pinned host buffers, two device buffers); the epochs' losses are summed into their own slots
     // and read at the end, so the host waits for the GPU only before reusing a host buffer.
     TrainBuffers tb;
-    st = tb.alloc(n, epochs);
-    if (st != LB_OK) return st;
     const long long nb = n / batch;
+    st = tb.alloc(n, epochs, (long long)epochs * nb);
+    if (st != LB_OK) return st;
+    // one cooperative launch per epoch when the batch's CTAs can all be resident, else one launch
+    // per batch and one for its Adam step (the same arithmetic)
+    const bool loop = train_loop_fits(ntiles);
+    if (loop) {
+        std::vector<float> bc((size_t)epochs * nb * 2);
+        for (long long k = 0; k < (long long)epochs * nb; ++k) {
+            const float t = (float)(net->adam_steps + k + 1);
+            bc[2 * k] = 1.0f - std::pow(0.9f, t);
+            bc[2 * k + 1] = 1.0f - std::pow(0.999f, t);
+        }
+        L_CUDA(cudaMemcpyAsync(tb.bc, bc.data(), bc.size() * sizeof(float), cudaMemcpyHostToDevice, s));
+        L_CUDA(cudaStreamSynchronize(s));  // bc is a local vector
+    }
     uint64_t rs = seed;
     auto shuffle = [&](int* perm) {
         for (long long k = 0; k < n; ++k) perm[k] = (int)k;
@@ -1357,9 +1503,13 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
             st = fail_l(e, "epoch setup");
             break;
         }
-        for (long long bi = 0; bi < nb && st == LB_OK; ++bi)
-            st = train_batch(net, pre, post, tb.dperm[b], bi * batch, ntiles, 1, lr, 1, sc.partial, tb.loss + ep,
-                             sc.flag, nullptr, s);
+        if (loop)
+            st = train_epoch_loop(net, pre, post, tb.dperm[b], (int)nb, ntiles, lr, tb.bc + 2 * (long long)ep * nb,
+                                  sc.partial, tb.loss + ep, sc.flag, tb.gbar, s);
+        else
+            for (long long bi = 0; bi < nb && st == LB_OK; ++bi)
+                st = train_batch(net, pre, post, tb.dperm[b], bi * batch, ntiles, 1, lr, 1, sc.partial,
+                                 tb.loss + ep, sc.flag, nullptr, s);
         if (st != LB_OK || ep + 1 == epochs) break;
         // the next epoch's permutation, into the host buffer whose copy (two epochs back) is done
         e = cudaEventSynchronize(tb.copied[b ^ 1]);
