@@ -663,9 +663,9 @@ def main():
             net.close()
         if not args.no_ensemble:
             forms["ensemble"] = measure_ensemble(lb, torch, np, inputs, value / world)
-            forms["ensemble_persistent"] = measure_ensemble(lb, torch, np, inputs, value / world,
-                                                            persistent=True,
-                                                            tile=tuple(forms["ensemble"]["tile"]))
+            forms["ensemble_per_item"] = measure_ensemble(lb, torch, np, inputs, value / world,
+                                                          per_item=True,
+                                                          tile=tuple(forms["ensemble"]["tile"]))
         forms["table1_1024x8192"] = measure_table1(lb, torch, np, inputs)
 
     line = {"metric": metric_name(args.precision),
@@ -912,13 +912,13 @@ def measure_table1(lb, torch, np, inputs, reps=20):
                            "collide_GFs": 2253, "collide_MLUPS": 340, "global_MLUPS": 232}}
 
 
-def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300, persistent=False,
+def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300, per_item=False,
                      tile=None):
     """Batched ensemble: n seed-drawn Rayleigh-Taylor lattices (Lx uniform over multiples of 32 in
     [128, 1024], Ly = 4 Lx, Atwood in [0.05, 0.5], tau in [tau_min(A), 1.2]), FP32 storage (exact-split
     accumulation), autotuned tile shape (or the given one), 100-step CUDA graphs; MLUPS = sum of
-    sites x steps / s. persistent: a grid of the co-resident blocks walking the work list instead
-    of one block per work item."""
+    sites x steps / s. The launch: one persistent grid per step whose co-resident blocks claim
+    the work items in list order (default), or per_item: one block per work item."""
     descs = inputs.ensemble_members(n, seed=seed)
     specs = []
     for d in descs:
@@ -928,7 +928,7 @@ def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300,
                       "uy": st.uy, "T": st.T})
     stream = torch.cuda.Stream()
     ens = lb.Ensemble(specs, precision="fp32split", graph_steps=100, stream=stream,
-                      persistent=persistent, tile=tile or (0, 0))
+                      per_item=per_item, tile=tile or (0, 0))
     specs = None
     if tile is None:
         tx, ty, tune_mlups = ens.autotune(steps=3)
@@ -954,8 +954,8 @@ def measure_ensemble(lb, torch, np, inputs, fp64_mlups, n=64, seed=0, steps=300,
             "hbm_frac": round(gbs / hbm, 4), "tile": [tx, ty], "work_items": info["items"],
             "autotune_best_mlups": None if tune_mlups is None else round(tune_mlups, 1),
             "graph_steps": 100, "precision": "fp32split",
-            "launch": "persistent grid (co-resident blocks walk the work list)" if persistent
-                      else "one block per work item"}
+            "launch": "one block per work item" if per_item
+                      else "persistent grid (co-resident blocks claim the work items in order)"}
 
 
 if __name__ == "__main__":

@@ -36,9 +36,10 @@ typedef struct {
     void* stream;        /* cudaStream_t or NULL (library-owned non-blocking stream) */
     void* workspace;     /* caller-owned device memory or NULL */
     size_t workspace_bytes;
-    int persistent;      /* 0: one block per work item (default, the faster launch); 1: a
-                            persistent grid of the co-resident blocks (occupancy x SMs), each
-                            walking the work list with stride grid. Same results either way. */
+    int per_item;        /* 0 (default): one persistent launch per step, a grid of the
+                            co-resident blocks (occupancy x SMs) that take the work items in
+                            list order from a counter; 1: one block per work item. Same results
+                            either way. */
 } lb_ensemble_opts;
 
 /* Device bytes needed by n members (members[k].Lx, .Ly used). */

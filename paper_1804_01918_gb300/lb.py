@@ -47,7 +47,7 @@ class lb_params(C.Structure):
 class lb_ensemble_opts(C.Structure):
     _fields_ = [("tile_x", C.c_int), ("tile_y", C.c_int), ("graph_steps", C.c_int),
                 ("precision", C.c_int), ("stream", C.c_void_p), ("workspace", C.c_void_p),
-                ("workspace_bytes", C.c_size_t), ("persistent", C.c_int)]
+                ("workspace_bytes", C.c_size_t), ("per_item", C.c_int)]
 
 
 _lib = None
@@ -540,7 +540,7 @@ class Ensemble:
     member, a temperature ratio R and a seed instead of fields (lb_ensemble_init_rt)."""
 
     def __init__(self, members, precision="fp32split", tile=(0, 0), graph_steps=0, stream=None,
-                 persistent=False):
+                 per_item=False):
         import torch
         self._ctx = C.c_void_p()
         n = len(members)
@@ -563,7 +563,7 @@ class Ensemble:
         self.stream = torch.cuda.Stream() if stream is None else stream
         sh = self.stream.cuda_stream if hasattr(self.stream, "cuda_stream") else self.stream
         opts = lb_ensemble_opts(int(tile[0]), int(tile[1]), int(graph_steps),
-                                _precision_code(precision), sh, None, 0, int(bool(persistent)))
+                                _precision_code(precision), sh, None, 0, int(bool(per_item)))
         nbytes = C.c_size_t()
         check(lib().lb_ensemble_workspace_bytes(n, params, C.byref(opts), C.byref(nbytes)),
               "lb_ensemble_workspace_bytes")

@@ -44,13 +44,13 @@ def single_runs(L, specs, steps, precision):
     return out
 
 
-@pytest.mark.parametrize("persistent", [False, True])
+@pytest.mark.parametrize("per_item", [False, True])
 @pytest.mark.parametrize("precision", ["fp32split", "fp32dev"])
-def test_ensemble_members_equal_single_lattice_runs(L, precision, persistent):
-    """Both launch shapes (one block per work item; a persistent grid walking the list) give
+def test_ensemble_members_equal_single_lattice_runs(L, precision, per_item):
+    """Both launch shapes (a persistent grid claiming the work items; one block per item) give
     every member the single-lattice result bit for bit."""
     specs = member_specs()
-    ens = L.Ensemble(specs, precision=precision, graph_steps=10, persistent=persistent)
+    ens = L.Ensemble(specs, precision=precision, graph_steps=10, per_item=per_item)
     ens.step(25)                      # two 10-step graph replays + 5 single launches
     ens.sync()
     want = single_runs(L, specs, 25, precision)
