@@ -145,6 +145,21 @@ def test_training_is_deterministic(L):
         net.close()
 
 
+def test_training_with_batches_beyond_one_launch(L):
+    """Batches of 20 480 samples (160 tiles: more CTAs than a 152-SM GPU holds at once) are trained
+    with one launch per batch and a separate Adam kernel instead of the per-epoch cooperative
+    loop; the same per-parameter Adam arithmetic, so that path too is deterministic and reduces
+    the loss."""
+    pre, post = collect_pairs(L)
+    nets = [L.MLP(seed=2) for _ in range(2)]
+    losses = [net.train(pre, post, epochs=3, batch=20480, lr=1e-3, seed=5) for net in nets]
+    assert np.all(np.isfinite(losses[0])) and losses[0][-1] < losses[0][0], losses[0]
+    (pa, na), (pb, nb) = nets[0].get_params(), nets[1].get_params()
+    assert np.array_equal(pa, pb) and np.array_equal(na, nb)
+    for net in nets:
+        net.close()
+
+
 def test_bound_zero_falls_back_everywhere_and_equals_plain(L):
     st = inputs.rayleigh_taylor(64, 128, R=2.0, seed=2)
     net = L.MLP(seed=2)
