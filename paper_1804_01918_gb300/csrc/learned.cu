@@ -4,15 +4,16 @@
 // Training data are (pre, post) pairs of FP32 deviations produced by the plain collide of this
 // library (pairs_kernel). The network (mlp_core.cuh) predicts the normalised collision change
 // (post - pre); its forward and backward passes run as tcgen05 BF16 x BF16 -> FP32 products with
-// hand-written epilogues (bias, GELU, GELU derivative, loss gradient), one 128-sample tile per CTA,
-// and Adam updates FP32 master weights and re-packs the BF16 operand images.
+// hand-written epilogues (bias, GELU, GELU derivative, loss gradient), one 128-sample tile per CTA
+// and batch, and Adam updates FP32 master weights and re-packs the BF16 operand images; a training
+// run takes one cooperative launch per epoch (mlp_train_kernel<true>).
 //
 // The learned LB step (step_learned_kernel) is persistent over 32 x 32-site tiles: per tile it
 // pulls the populations, runs the MLP on 8 sub-tiles of 128 sites, adds the predicted change,
 // projects onto the exact post-collision moments, stores, and on check steps also evaluates the
 // plain collide of the same sites: if max |f_learned - f_plain| exceeds bound x max |f_plain| over
-// the tile, the tile is rewritten with the plain collide (the source copy is never modified, so
-// the plain result can always be recomputed) and stays on the plain collide until the next check.
+// the tile, the plain result (kept in a scratch tile) is copied over the tile, which stays on the
+// plain collide until the next check.
 #include <cuda_runtime.h>
 
 #include <algorithm>
