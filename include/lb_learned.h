@@ -60,6 +60,8 @@ lb_status lb_mlp_loss_grad_fp32(lb_mlp* net, const float* x, const float* t, int
 
 /* Train on n (pre, post) pairs: sets the normalisation from the data, then `epochs` passes of
  * shuffled mini-batches (batch a multiple of 128) with Adam (beta 0.9 / 0.999, eps 1e-8, rate lr).
+ * One cooperative launch per epoch when a batch's CTAs (batch / 128) fit on the GPU at once, else
+ * one launch per batch and its Adam step; the same arithmetic either way, and bit-reproducible.
  * epoch_loss (host, may be NULL) receives each epoch's mean loss. Synchronous. */
 lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long long n, int epochs,
                        int batch, float lr, uint64_t seed, float* epoch_loss, void* stream);
@@ -86,7 +88,9 @@ lb_status lb_collide_train(lb_ctx* c, const float* pre, const float* post, size_
 lb_status lb_collide_save(lb_ctx* c, const char* path);
 lb_status lb_collide_load(lb_ctx* c, const char* path);
 
-/* Switch the context's collide to the learned one (net must outlive the setting), or back. */
+/* Switch the context's collide to the learned one (net must outlive the setting), or back.
+ * Setting it allocates the tile decisions, the statistics and a scratch area for the plain result
+ * of the tiles in flight (three 32 x 32 tiles per SM, ~150 KB each). */
 lb_status lb_set_collide_learned(lb_ctx* c, const lb_mlp* net, double bound, int check_every);
 lb_status lb_set_collide_plain(lb_ctx* c);
 
