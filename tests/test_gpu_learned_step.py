@@ -171,3 +171,67 @@ def test_learned_step_with_constant_network_output_is_fp32_exact(L, orc, bound):
     _, _, w, _ = orc.velocity_set()
     assert np.max(np.abs(want["y"])) > 0.01          # the bias is there to be dropped
     check_case(got, modes, stats, want, FP32_BAR * w, tp)
+
+
+def test_learned_step_full_size_sampled_tiles_match_oracle(L, orc):
+    """The bench workload's size (2304 x 8192 Rayleigh-Taylor, FP32 split storage) in the bench's
+    launch configuration (one CTA per SM, each warpgroup stepping ~40 tiles one after another):
+    sampled tiles -- at both walls, at the x wrap, across the interface and at random -- against
+    the oracle's learned step evaluated on a window around each (a tile pulls from at most 3 sites
+    beyond its edges; the window wraps in x and stops at the real walls). Bound 1e-2: tiles across
+    the interface fall back, the rest keep the network."""
+    Lx, Ly, tau, bound = 2304, 8192, 0.9, 1e-2
+    _, _, wg, _ = L.velocity_set()
+    st = inputs.rayleigh_taylor(Lx, Ly, R=2.0, seed=0)
+    params = inputs.mlp_params(5)
+    norm = inputs.mlp_norm(wg, seed=1, sd_t=1e-4, mu_t=2e-4)
+    net = L.MLP(seed=0)
+    net.set_params(params, norm)
+    lat = L.Lattice.from_fields(st, tau=tau, precision="fp32split")
+    lat.set_collide_learned(net, bound=bound)
+    lat.step(1)
+    lat.sync()
+    f1 = lat.get_populations()
+    modes = lat.learned_tiles()
+    stats = lat.learned_stats()
+    lat.close()
+    net.close()
+    ntx, nty = Lx // 32, Ly // 32
+    assert stats["tiles_checked"] == ntx * nty
+    cxg, cyg, _, _ = L.velocity_set()
+    perm = orc.order_map(cxg, cyg)
+    _, _, w, _ = orc.velocity_set()
+    nrm = np.empty((4, 37))
+    nrm[:, perm] = np.asarray(norm, np.float64)
+    predict = olr.network_change(params, norm, (cxg, cyg))
+    P = np.abs(projection_operator(orc))
+    rng = np.random.default_rng(7)
+    tiles = [(0, 0), (ntx - 1, 0), (0, nty - 1), (ntx - 1, nty - 1), (5, nty // 2 - 1), (6, nty // 2),
+             (ntx // 2, nty // 2 - 1), (ntx - 1, nty // 2)]
+    tiles += [(int(rng.integers(ntx)), int(rng.integers(nty))) for _ in range(8)]
+    kinds = set()
+    for tx, ty in tiles:
+        x0, y0 = 32 * tx, 32 * ty
+        xs = np.arange(x0 - 3, x0 + 35) % Lx
+        ylo, yhi = max(0, y0 - 3), min(Ly, y0 + 35)
+        sub = [a[ylo:yhi][:, xs] for a in (st.rho, st.ux, st.uy, st.T)]
+        fp = olr.pulled(orc.equilibrium(*sub), st.T_top, st.T_bottom)[y0 - ylo:y0 - ylo + 32, 3:35]
+        d = (fp - w).reshape(-1, 37)
+        y = predict(d)
+        dl = olr.project(olr.add_change(d, y, nrm), olr.targets(d, 0.0, st.gy))
+        f_learned = (dl + w).reshape(32, 32, 37)
+        f_plain = orc.collide(fp, tau, 0.0, st.gy)
+        res = olr.tile_residual(f_learned, f_plain)
+        got = orc.from_planes(f1[:, y0:y0 + 32, x0:x0 + 32], cxg, cyg)
+        tol_learned = P @ (nrm[3] * Y_BAR * np.max(np.abs(y))) + FP32_BAR * w
+        tol_plain = FP32_PLAIN_BAR * w
+        margin = 1.5 * np.max(tol_learned + tol_plain) / np.max(np.abs(f_plain))
+        if abs(res - bound) > margin * max(1.0, res):
+            assert bool(modes[ty, tx]) == olr.falls_back(res, bound), (tx, ty, res)
+        if modes[ty, tx]:
+            err = np.abs(got - f_plain) / tol_plain
+        else:
+            err = np.abs(got - f_learned) / tol_learned
+        kinds.add(bool(modes[ty, tx]))
+        assert err.max() <= 1.0, (tx, ty, bool(modes[ty, tx]), float(err.max()))
+    assert kinds == {False, True}, "the sampled tiles should include kept and fallback ones"
