@@ -188,6 +188,32 @@ __device__ __forceinline__ void adam_param(int p, float* __restrict__ params, fl
     }
 }
 
+// One epoch's training data in permutation order, ready for mlp_train_kernel (raw = 2): sample p
+// (p < count) is pair perm[p], normalised -- x = (pre - mu_x) / sd_x, t = (post - pre - mu_t) /
+// sd_t, the same arithmetic as the kernel's raw = 1 gather -- with x written as row p mod 128 of
+// tile p / 128's BF16 X image (the shared-memory operand layout, so the kernel copies it in one
+// bulk copy) and t as t[tile][i][p mod 128]. One thread per sample, all SMs: the random rows of
+// pre and post are gathered with the whole GPU's memory parallelism instead of 32 SMs'.
+__global__ void prep_epoch_kernel(const float* __restrict__ pre, const float* __restrict__ post,
+                                  const int* __restrict__ perm, long long count, const float* __restrict__ norm,
+                                  char* __restrict__ ximg, float* __restrict__ timg) {
+    const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= count) return;
+    const long long row = perm[p], tile = p / TILE;
+    const int r = (int)(p % TILE);
+    float xn[KIN];
+#pragma unroll
+    for (int i = 0; i < NIN; ++i) {
+        const float av = pre[row * NIN + i], bv = post[row * NIN + i];
+        xn[i] = (av - norm[i]) / norm[NIN + i];
+        timg[(tile * NIN + i) * TILE + r] = ((bv - av) - norm[2 * NIN + i]) / norm[3 * NIN + i];
+    }
+#pragma unroll
+    for (int i = NIN; i < KIN; ++i) xn[i] = 0.0f;
+#pragma unroll
+    for (int k0 = 0; k0 < KIN; k0 += 8) store_row8(ximg + tile * BYTES_X, r, k0, KIN, xn + k0);
+}
+
 // A bounded barrier of all CTAs of a cooperative launch (bar[0] counts arrivals, bar[1] is the
 // generation): false if it was not reached by all within the wait limit.
 __device__ __forceinline__ bool grid_barrier(unsigned* bar, int* shared_ok) {
@@ -243,7 +269,9 @@ struct TrainLoop {
 // parameters spread over all threads, a second barrier, and the next batch reloads the weights
 // and biases. Otherwise one batch (nbatch = 1) whose Adam step is a separate kernel.
 //   raw = 1: a = pre deviations, b = post deviations (normalised inside);
-//   raw = 0: a = normalised inputs, b = normalised targets.
+//   raw = 0: a = normalised inputs, b = normalised targets;
+//   raw = 2: a = the tiles' X images, b = their normalised targets, as prep_epoch_kernel writes
+//            them for the permutation's sample order (perm unused).
 template <bool kLoop>
 __global__ void __launch_bounds__(2 * TILE, 1)
 mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restrict__ b,
@@ -272,6 +300,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     bool ok = true, weights_ok = true;
     const int batch = (int)gridDim.x * TILE;
     for (int bi = 0; bi < nbatch && ok; ++bi) {
+    const long long tile0 = base + (long long)bi * batch + (long long)blockIdx.x * TILE;
     if (tid == 0) {
         // the five weight images (100 KB) by bulk copies, arriving on wbar while the threads
         // gather and normalise their samples (a copy loop of 16-byte loads per thread waited for
@@ -279,7 +308,9 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         // previous batch's Adam step (generic stores): the proxy fence orders those before the
         // asynchronous copy's reads
         if (kLoop) asm volatile("fence.proxy.async.global;" ::: "memory");
-        tc::mbar_expect_tx(wbar, BYTES_W1 + BYTES_W2 + BYTES_W3 + BYTES_W3T + BYTES_W2T);
+        tc::mbar_expect_tx(wbar, BYTES_W1 + BYTES_W2 + BYTES_W3 + BYTES_W3T + BYTES_W2T + (raw == 2 ? BYTES_X : 0));
+        if (raw == 2)  // the tile's prepared X image
+            tc::bulk_g2s(sm + TR_X, reinterpret_cast<const char*>(a) + (tile0 / TILE) * BYTES_X, BYTES_X, wbar);
         tc::bulk_g2s(sm + TR_W1, net.w1img, BYTES_W1, wbar);
         tc::bulk_g2s(sm + TR_W2, net.w2img, BYTES_W2, wbar);
         tc::bulk_g2s(sm + TR_W3, net.w3img, BYTES_W3, wbar);
@@ -294,12 +325,17 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         const int off = k < HID ? OFF_B1 + k : k < 2 * HID ? OFF_B2 + (k - HID) : OFF_B3 + (k - 2 * HID);
         bias[k] = __ldcg(net.params + off);
     }
-    const long long tile0 = base + (long long)bi * batch + (long long)blockIdx.x * TILE;
 
     // ---- this thread's sample ----
-    const long long row = perm ? (long long)perm[tile0 + q] : tile0 + q;
     float xn[KIN], tn[NIN];
-    if (wg == 0) {
+    if (raw == 2) {
+        // prepared by prep_epoch_kernel: the X image arrives with the weights, the normalised
+        // targets are [tile][37][128]
+        if (wg == 0)
+#pragma unroll
+            for (int i = 0; i < NIN; ++i) tn[i] = b[((tile0 / TILE) * NIN + i) * TILE + q];
+    } else if (wg == 0) {
+        const long long row = perm ? (long long)perm[tile0 + q] : tile0 + q;
         const float* norm = net.norm;
 #pragma unroll
         for (int i = 0; i < NIN; ++i) {
@@ -1169,15 +1205,17 @@ lb_status train_batch(lb_mlp* net, const float* a, const float* b, const int* pe
     return LB_OK;
 }
 
-// All batches of one epoch in one cooperative launch (mlp_train_kernel<true>); bc holds the
-// batches' Adam bias corrections, gbar two words for the grid barrier (zeroed here).
-lb_status train_epoch_loop(lb_mlp* net, const float* a, const float* b, const int* perm, int nbatch, int ntiles,
-                           float lr, const float* bc, float* partial, double* loss_acc, int* flag, unsigned* gbar,
+// All batches of one epoch in one cooperative launch (mlp_train_kernel<true>) on the data that
+// prep_epoch_kernel laid out (raw = 2: a = X images, b = targets); bc holds the batches' Adam bias
+// corrections, gbar two words for the grid barrier (zeroed here).
+lb_status train_epoch_loop(lb_mlp* net, const float* a, const float* b, int nbatch, int ntiles, float lr,
+                           const float* bc, float* partial, double* loss_acc, int* flag, unsigned* gbar,
                            cudaStream_t s) {
     L_CUDA(cudaMemsetAsync(gbar, 0, 2 * sizeof(unsigned), s));
     NetDev nd = net->dev();
     long long base = 0;
-    int raw = 1;
+    const int* perm = nullptr;
+    int raw = 2;
     float inv_count = 1.0f / ((float)ntiles * TILE * NOUT);
     TrainLoop L{bc, net->params, net->m, net->v, {net->img[0], net->img[1], net->img[2], net->img[3], net->img[4]},
                 lr, gbar};
@@ -1252,6 +1290,8 @@ struct TrainBuffers {
     double* loss = nullptr;
     float* bc = nullptr;       // Adam bias corrections of every batch of the run (training loop)
     unsigned* gbar = nullptr;  // grid barrier words (training loop)
+    char* ximg = nullptr;      // an epoch's X images and targets in batch order (training loop)
+    float* timg = nullptr;
     ~TrainBuffers() {
         for (int b = 0; b < 2; ++b) {
             if (hperm[b]) cudaFreeHost(hperm[b]);
@@ -1261,6 +1301,18 @@ struct TrainBuffers {
         if (loss) cudaFree(loss);
         if (bc) cudaFree(bc);
         if (gbar) cudaFree(gbar);
+        if (ximg) cudaFree(ximg);
+        if (timg) cudaFree(timg);
+    }
+    // the training loop's prepared data: count samples (a multiple of 128)
+    lb_status alloc_prepared(long long count) {
+        if (cudaMalloc((void**)&ximg, (size_t)(count / TILE) * BYTES_X) != cudaSuccess ||
+            cudaMalloc((void**)&timg, (size_t)count * NIN * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            set_last_error("MLP training buffers allocation failed");
+            return LB_ERR_ALLOC;
+        }
+        return LB_OK;
     }
     lb_status alloc(long long n, int epochs, long long nbatches) {
         for (int b = 0; b < 2; ++b) {
@@ -1476,6 +1528,8 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
     // per batch and one for its Adam step (the same arithmetic)
     const bool loop = train_loop_fits(ntiles);
     if (loop) {
+        st = tb.alloc_prepared(nb * batch);
+        if (st != LB_OK) return st;
         std::vector<float> bc((size_t)epochs * nb * 2);
         for (long long k = 0; k < (long long)epochs * nb; ++k) {
             const float t = (float)(net->adam_steps + k + 1);
@@ -1504,9 +1558,16 @@ lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long lo
             st = fail_l(e, "epoch setup");
             break;
         }
-        if (loop)
-            st = train_epoch_loop(net, pre, post, tb.dperm[b], (int)nb, ntiles, lr, tb.bc + 2 * (long long)ep * nb,
-                                  sc.partial, tb.loss + ep, sc.flag, tb.gbar, s);
+        if (loop) {
+            const long long count = nb * batch;
+            prep_epoch_kernel<<<(unsigned)((count + 255) / 256), 256, 0, s>>>(pre, post, tb.dperm[b], count, net->norm,
+                                                                             tb.ximg, tb.timg);
+            e = cudaGetLastError();
+            st = e != cudaSuccess ? fail_l(e, "epoch data")
+                                  : train_epoch_loop(net, reinterpret_cast<const float*>(tb.ximg), tb.timg, (int)nb,
+                                                     ntiles, lr, tb.bc + 2 * (long long)ep * nb, sc.partial,
+                                                     tb.loss + ep, sc.flag, tb.gbar, s);
+        }
         else
             for (long long bi = 0; bi < nb && st == LB_OK; ++bi)
                 st = train_batch(net, pre, post, tb.dperm[b], bi * batch, ntiles, 1, lr, 1, sc.partial,
