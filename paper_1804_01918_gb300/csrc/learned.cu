@@ -258,16 +258,18 @@ struct TrainLoop {
     char* img[5];
     float lr;
     unsigned* bar;
+    int tiles;  // the batch's tiles: CTAs 0 .. tiles - 1 take one each, the rest join the Adam step
 };
 
 // One 128-sample tile per CTA and batch: forward, loss, backward; writes this CTA's
 // parameter-gradient partial (packed like the parameters) and adds its loss sum to *loss_acc. Two
 // warpgroups: thread q of either owns sample q (TMEM lane q); each epilogue's 128 columns are
 // split between them (columns 64 wg .. 64 wg + 63), and the per-sample work (inputs, loss) is
-// warpgroup 0's. kLoop: a cooperative launch that trains on nbatch consecutive batches of the
-// permutation, all CTAs together: after each batch a grid barrier, the Adam step with the
-// parameters spread over all threads, a second barrier, and the next batch reloads the weights
-// and biases. Otherwise one batch (nbatch = 1) whose Adam step is a separate kernel.
+// warpgroup 0's. kLoop: a cooperative launch of one CTA per SM that trains on nbatch consecutive
+// batches of the permutation: CTAs 0 .. L.tiles - 1 take a tile each; after each batch a grid
+// barrier, the Adam step with the parameters spread over all CTAs' threads, a second barrier, and
+// the next batch reloads the weights and biases. Otherwise one batch (nbatch = 1, one CTA per
+// tile) whose Adam step is a separate kernel.
 //   raw = 1: a = pre deviations, b = post deviations (normalised inside);
 //   raw = 0: a = normalised inputs, b = normalised targets;
 //   raw = 2: a = the tiles' X images, b = their normalised targets, as prep_epoch_kernel writes
@@ -298,8 +300,11 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
     const uint32_t tm = *tslot;
     uint32_t ph = 0;
     bool ok = true, weights_ok = true;
-    const int batch = (int)gridDim.x * TILE;
+    const int tiles = kLoop ? L.tiles : (int)gridDim.x;
+    const int batch = tiles * TILE;
+    const bool worker = (int)blockIdx.x < tiles;
     for (int bi = 0; bi < nbatch && ok; ++bi) {
+    if (worker) {
     const long long tile0 = base + (long long)bi * batch + (long long)blockIdx.x * TILE;
     if (tid == 0) {
         // the five weight images (100 KB) by bulk copies, arriving on wbar while the threads
@@ -527,6 +532,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         for (int k = tid; k < NOUT; k += blockDim.x) out[OFF_B3 + k] = col(2 * HID + k);
         if (tid == 0) atomicAdd(loss_acc, (double)*loss_sm);
     }
+    }  // worker
     if (kLoop && ok) {
         // all partials written -> the Adam step, the parameters spread over the grid's threads ->
         // the new weights written before any CTA reloads them
@@ -534,7 +540,7 @@ mlp_train_kernel(NetDev net, const float* __restrict__ a, const float* __restric
         if (ok) {
             const float* bcb = L.bc + 2 * bi;
             for (int p = blockIdx.x * blockDim.x + tid; p < NPARAM; p += gridDim.x * blockDim.x)
-                adam_param(p, L.params, L.m, L.v, partial, gridDim.x, L.lr, bcb[0], bcb[1], 1, nullptr, L.img[0],
+                adam_param(p, L.params, L.m, L.v, partial, tiles, L.lr, bcb[0], bcb[1], 1, nullptr, L.img[0],
                            L.img[1], L.img[2], L.img[3], L.img[4]);
             asm volatile("fence.proxy.async.global;" ::: "memory");
             ok = grid_barrier(L.bar, shared_ok);
@@ -1205,6 +1211,22 @@ lb_status train_batch(lb_mlp* net, const float* a, const float* b, const int* pe
     return LB_OK;
 }
 
+// The training loop's CTAs that can be resident at once (0 without cooperative launches).
+int train_loop_ctas() {
+    int dev = 0, coop = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_train_kernel<true>, 2 * TILE, TR_BYTES) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return per_sm * sm_count();
+}
+
+// Whether ntiles training CTAs can all be resident at once (the cooperative launch's condition).
+bool train_loop_fits(int ntiles) { return train_loop_ctas() >= ntiles; }
+
 // All batches of one epoch in one cooperative launch (mlp_train_kernel<true>) on the data that
 // prep_epoch_kernel laid out (raw = 2: a = X images, b = targets); bc holds the batches' Adam bias
 // corrections, gbar two words for the grid barrier (zeroed here).
@@ -1218,27 +1240,17 @@ lb_status train_epoch_loop(lb_mlp* net, const float* a, const float* b, int nbat
     int raw = 2;
     float inv_count = 1.0f / ((float)ntiles * TILE * NOUT);
     TrainLoop L{bc, net->params, net->m, net->v, {net->img[0], net->img[1], net->img[2], net->img[3], net->img[4]},
-                lr, gbar};
+                lr, gbar, ntiles};
+    // every SM takes part: the batch's tiles on ntiles of them, the Adam step on all
+    const int grid = std::max(ntiles, train_loop_ctas());
     void* args[] = {&nd, (void*)&a, (void*)&b, (void*)&perm, &base, &nbatch, &inv_count, &raw, &partial,
                     &loss_acc, &flag, &L};
-    L_CUDA(cudaLaunchCooperativeKernel((const void*)mlp_train_kernel<true>, dim3(ntiles), dim3(2 * TILE), args,
+    L_CUDA(cudaLaunchCooperativeKernel((const void*)mlp_train_kernel<true>, dim3(grid), dim3(2 * TILE), args,
                                        (size_t)TR_BYTES, s));
     net->adam_steps += nbatch;
     return LB_OK;
 }
 
-// Whether ntiles training CTAs can all be resident at once (the cooperative launch's condition).
-bool train_loop_fits(int ntiles) {
-    int dev = 0, coop = 0, per_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return false;
-    if (cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop) return false;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, mlp_train_kernel<true>, 2 * TILE, TR_BYTES) !=
-        cudaSuccess) {
-        cudaGetLastError();
-        return false;
-    }
-    return (long long)per_sm * sm_count() >= ntiles;
-}
 
 struct Scratch {
     char* mem = nullptr;
