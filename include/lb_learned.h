@@ -62,6 +62,8 @@ lb_status lb_mlp_loss_grad_fp32(lb_mlp* net, const float* x, const float* t, int
  * shuffled mini-batches (batch a multiple of 128) with Adam (beta 0.9 / 0.999, eps 1e-8, rate lr).
  * One cooperative launch per epoch when a batch's CTAs (batch / 128) fit on the GPU at once, else
  * one launch per batch and its Adam step; the same arithmetic either way, and bit-reproducible.
+ * The per-epoch launch works on the epoch's samples laid out in batch order in temporary device
+ * memory (244 bytes per sample: the BF16 inputs and the FP32 targets, normalised).
  * epoch_loss (host, may be NULL) receives each epoch's mean loss. Synchronous. */
 lb_status lb_mlp_train(lb_mlp* net, const float* pre, const float* post, long long n, int epochs,
                        int batch, float lr, uint64_t seed, float* epoch_loss, void* stream);
