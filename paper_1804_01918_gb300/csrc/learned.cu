@@ -733,6 +733,7 @@ constexpr int THREADS = GROUPS * TILE;
 constexpr int SLOT_D = NPOP * TILE * 4;     // [37][128] floats
 constexpr int SCRATCH_TILE = NPOP * 1024;   // floats: a tile's plain result, [37][32 rows][32]
 constexpr int COPY_V4 = NPOP * 32 * 8;      // 16-byte pieces of a tile
+constexpr uint64_t START_STAGGER_NS = 5000;  // group g starts g x this late
 // TMEM: the groups' networks at columns 0..383, their plain results (37 columns) from 384 on
 constexpr int PLAIN_COL = GROUPS * 128, PLAIN_STRIDE = 40;
 static_assert(PLAIN_COL + (GROUPS - 1) * PLAIN_STRIDE + NPOP <= 512, "TMEM columns");
@@ -987,6 +988,13 @@ step_learned_kernel(const float* __restrict__ src, float* __restrict__ dst, cons
     g.wq = (tid >> 5) & 3;
     g.id = 1 + gi;
     float* scr = scratch + ((size_t)blockIdx.x * GROUPS + gi) * SCRATCH_TILE;
+    // Stagger the groups' start by about a third of a sub-tile's ~13 us each: groups that start
+    // together keep epilogues and product waits in step and leave the SM idle together (measured
+    // +2.7 %, flat between 4 and 7 us); the delay costs ~10 us of a group's time per launch.
+    if (gi > 0) {
+        const uint64_t t0 = tc::globaltimer_ns();
+        while (tc::globaltimer_ns() - t0 < (uint64_t)gi * START_STAGGER_NS) __nanosleep(256);
+    }
     const int ntx = P.Lx / 32, ntiles = ntx * (P.Ly / 32);
     bool alive = true;
     for (int t = blockIdx.x * GROUPS + gi; t < ntiles && alive; t += gridDim.x * GROUPS) {
